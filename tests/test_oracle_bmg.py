@@ -1,0 +1,112 @@
+"""Pins of the oracle's enriched Rayleigh-Ritz and BFMG against dense solves."""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+from oracle import bmg, certify
+from paper_1511_07042_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def test_svqb_matches_lapack_on_well_conditioned_pencil():
+    rng = np.random.default_rng(11)
+    n, k = 30, 8
+    B = rng.standard_normal((n, n))
+    Mh = B @ B.T + n * np.eye(n)
+    C = rng.standard_normal((n, n))
+    Ah = C + C.T
+    sigma = 0.3
+    theta, Y = bmg.svqb_eig(Ah, Mh, sigma, k)
+    w = sla.eigh(Ah, Mh, eigvals_only=True) - sigma
+    want = w[np.lexsort((np.arange(n), w, np.abs(w)))[:k]]
+    assert np.allclose(theta, want, rtol=1e-12, atol=1e-12)
+    assert np.allclose(Y.T @ Mh @ Y, np.eye(k), atol=1e-12)
+    R = Ah @ Y - Mh @ Y * (theta + sigma)[None, :]
+    assert np.max(np.abs(R)) < 1e-11
+
+
+def test_svqb_drops_dependent_directions():
+    """A repeated basis vector makes M_hat singular; SVQB must still return the
+    eigenpairs of the pencil restricted to the spanned space."""
+    rng = np.random.default_rng(12)
+    N, m = 40, 6
+    Z = rng.standard_normal((N, m))
+    Zd = np.concatenate([Z, Z[:, :1]], axis=1)        # dependent column
+    S = rng.standard_normal((N, N))
+    A = S + S.T
+    Mh, Ah = Zd.T @ Zd, Zd.T @ A @ Zd
+    theta, Y = bmg.svqb_eig(Ah, Mh, 0.0, 4)
+    w = sla.eigh(Z.T @ A @ Z, Z.T @ Z, eigvals_only=True)
+    want = w[np.argsort(np.abs(w))[:4]]
+    assert np.allclose(np.sort(theta), np.sort(want), rtol=1e-10, atol=1e-10)
+
+
+def test_selection_order_ties():
+    th = np.array([2.0, -1.0, 1.0, -2.0, 1.0])
+    assert list(bmg.select_order(th)) == [1, 2, 4, 3, 0]
+
+
+def _c1(form, smoother, nu, omega):
+    v, t = inputs.icosahedron()
+    H = bmg.build_hierarchy(v, t, 3)
+    X0 = inputs.gaussian_block(162, 20, 1001)
+    opt = bmg.Options(smoother=smoother, nu=nu, omega=omega, form=form)
+    return H, bmg.bfmg(H, X0, 20, 16, 0.0, 1e-10, opt)
+
+
+@pytest.mark.parametrize("form,smoother,nu,omega", [
+    ("shifted", "jacobi", 2, 2 / 3), ("homogeneous", "jacobi", 2, 2 / 3),
+    ("shifted", "mcsgs", 1, 1.0), ("homogeneous", "mcgs", 2, 1.0)])
+def test_bfmg_sphere642_matches_dense_eigensolve(form, smoother, nu, omega):
+    H, res = _c1(form, smoother, nu, omega)
+    assert res.converged
+    A, M = H.A[3], H.M[3]
+    w, V = certify.dense_pencil_eigs(A, M)
+    err, ang = certify.compare_to_reference(M, res.lam[:16], res.U[:, :16], w[:16], V[:, :16])
+    assert err.max() <= 1e-10 and ang.max() <= 1e-8
+    assert np.all(res.resid[:16] <= 1e-10)
+    gold = np.loadtxt(os.path.join(GOLDEN, "sphere_spectrum.txt"), comments="#")
+    for l, lam, mult, j0, j1 in gold[:4]:
+        assert np.all(np.abs(np.sort(res.lam[:16])[int(j0):int(j1) + 1] - lam) < 0.1 * max(lam, 1))
+
+
+def test_bfmg_shifted_interior_cluster_perturbed_sphere():
+    """Interior pairs nearest sigma on a perturbed sphere (Remark on the choice of
+    shifts) against LAPACK, plus the residual-bound certificate."""
+    v, t = inputs.icosahedron()
+    coefs = inputs.sh_coefficients(1003)
+    H = bmg.build_hierarchy(v, t, 3, amplitude=0.1, coefs=coefs)
+    sigma, k, nw = 20.0, 24, 9
+    X0 = inputs.gaussian_block(162, k, 1013)
+    res = bmg.bfmg(H, X0, k, nw, sigma, 1e-10, bmg.Options(form="shifted"))
+    assert res.converged
+    A, M = H.A[3], H.M[3]
+    w, V = certify.dense_pencil_eigs(A, M)
+    wr, Vr = certify.nearest(w, V, sigma, nw)
+    err, ang = certify.compare_to_reference(M, res.lam[:nw], res.U[:, :nw], wr, Vr)
+    assert err.max() <= 1e-10 and ang.max() <= 1e-8
+    bnd = certify.residual_bound(A, M, res.lam[:nw], res.U[:, :nw])
+    assert np.all(bnd / np.maximum(np.abs(res.lam[:nw]), 1) < 1e-8)
+
+
+def test_bfmg_rate_of_convergence_table1_analogue():
+    """Table 1 (BMG w/ GS): |lambda - lambda_h| ~ DoF^-r with r ~= 1 for lambda = 2, 6, 12."""
+    gold = np.loadtxt(os.path.join(GOLDEN, "table1_rates.txt"), comments="#")
+    v, t = inputs.icosahedron()
+    H = bmg.build_hierarchy(v, t, 5)
+    X0 = inputs.gaussian_block(162, 20, 1001)
+    res = bmg.bfmg(H, X0, 20, 16, 0.0, 1e-9, bmg.Options(smoother="mcsgs", nu=1, omega=1.0,
+                                                          tol_intermediate=1e-9,
+                                                          cycles_intermediate=60))
+    dof = np.array([inputs.n_vertices(r) for r in (3, 4, 5)])
+    for lam, r_bmg, r_gs in gold:
+        l = int(round((np.sqrt(1 + 4 * lam) - 1) / 2))
+        errs = []
+        for lev in (1, 2, 3):                       # levels 3, 4, 5
+            lv = np.sort(level := res.level_lams[lev])[l * l:(l + 1) ** 2]
+            errs.append(np.mean(np.abs(lv - lam)))
+        r = np.log(errs[0] / errs[-1]) / np.log(dof[-1] / dof[0])
+        assert abs(r - 1.0) < 0.05 and abs(r - r_gs) < 0.1, (lam, r)
