@@ -62,6 +62,7 @@ def sh_basis(n: np.ndarray) -> np.ndarray:
     c42 = (3.0 / 8.0) * math.sqrt(5.0 / pi)
     c44 = (3.0 / 16.0) * math.sqrt(35.0 / pi)
     one = np.ones_like(x)
+    z4 = z * z * z * z
     cols = [
         c00 * one,
         c1 * y, c1 * z, c1 * x,
@@ -73,7 +74,7 @@ def sh_basis(n: np.ndarray) -> np.ndarray:
         c3a * x * (x * x - 3.0 * y * y),
         c4a * x * y * (x * x - y * y), c4b * y * z * (3.0 * x * x - y * y),
         c4c * x * y * (7.0 * z * z - 1.0), c4d * y * z * (7.0 * z * z - 3.0),
-        c40 * (35.0 * z ** 4 - 30.0 * z * z + 3.0),
+        c40 * (35.0 * z4 - 30.0 * z * z + 3.0),
         c4d * x * z * (7.0 * z * z - 3.0), c42 * (x * x - y * y) * (7.0 * z * z - 1.0),
         c4b * x * z * (x * x - 3.0 * y * y),
         c44 * (x * x * (x * x - 3.0 * y * y) - y * y * (3.0 * x * x - y * y)),
@@ -82,10 +83,20 @@ def sh_basis(n: np.ndarray) -> np.ndarray:
 
 
 def radius(n: np.ndarray, amplitude: float, coefs) -> np.ndarray:
-    """r(n) = 1 + a * sum c_lm Y_lm(n) for unit vectors n."""
+    """r(n) = 1 + a * sum c_lm Y_lm(n) for unit vectors n.
+
+    The sum runs in the column order of sh_basis, one term at a time, so that its
+    rounding is fixed (products and sums evaluated left to right, no fused
+    multiply-add).
+    """
     if amplitude == 0.0:
         return np.ones(n.shape[0])
-    return 1.0 + amplitude * (sh_basis(n) @ np.asarray(coefs, dtype=np.float64))
+    Y = sh_basis(n)
+    c = np.asarray(coefs, dtype=np.float64)
+    acc = Y[:, 0] * c[0]
+    for q in range(1, 25):
+        acc = acc + Y[:, q] * c[q]
+    return 1.0 + amplitude * acc
 
 
 def project(m: np.ndarray, amplitude: float = 0.0, coefs=None) -> np.ndarray:
