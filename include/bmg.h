@@ -1,0 +1,211 @@
+/*
+ * bmg.h -- C ABI of libbmg, a GB300 (sm_103a) implementation of the bootstrap
+ * multigrid (BMG) eigensolver for the P1 surface finite-element Laplace-Beltrami
+ * pencil  A x = lambda M x  (Brannick & Cao, "A Bootstrap Multigrid Eigensolver").
+ *
+ * The paper states the problem as: given a coarse mesh, a shift mu and a tolerance,
+ * compute the eigenpairs (u_{h,i}, lambda_{h,i}) near mu on a uniformly refined mesh
+ * (Sec. 4.1, the paragraph after Alg. 2).  The three top-level calls follow it:
+ *   bmg_assemble   coarse mesh -> refined meshes, P1 stiffness A and mass M
+ *   bmg_hierarchy  prolongations P_l, Galerkin coarse operators, colourings
+ *   bmg_solve      BFMG (Alg. 4) with BMG cycles (Alg. 3) -> Ritz pairs near sigma
+ * The remaining calls expose the individual steps of the cycle on device buffers;
+ * they exist so that each step can be checked on its own.
+ *
+ * Conventions
+ *   - Indices are int32, 0-based.  Matrices are CSR with ascending columns; the
+ *     diagonal is stored.  Dense blocks are row-major.  A block of k vectors on a
+ *     level with N vertices is "k-interleaved": row-major [N][ld] with ld >= k, the
+ *     k values of one vertex contiguous (ld is a multiple of 2 for 16-byte loads;
+ *     columns k..ld-1 are padding that every kernel keeps at zero).
+ *   - Pointers documented as "device" must be device memory of the current CUDA
+ *     device; "host" pointers are ordinary host memory.  Calls that take a
+ *     `stream` (a cudaStream_t passed as void*; NULL = legacy default stream)
+ *     enqueue their work on it and may return before it completes, unless stated.
+ *   - Ownership: a bmg_problem owns every device buffer it allocates and frees it
+ *     in bmg_destroy.  Buffers passed in by the caller are never freed.
+ *   - Errors: every call returns a bmg_status and never aborts the process.  On an
+ *     error the outputs are unspecified (except BMG_ERR_NOT_CONVERGED, see
+ *     bmg_solve), and bmg_last_error() returns a message for the calling thread.
+ *   - Threads: a bmg_problem must not be used by two threads at once.
+ */
+#ifndef BMG_H
+#define BMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  BMG_OK = 0,
+  BMG_ERR_INVALID_ARG = 1,   /* bad size, null pointer, unsupported option        */
+  BMG_ERR_CUDA = 2,          /* a CUDA runtime call failed (message has details) */
+  BMG_ERR_OOM = 3,           /* device allocation failed                         */
+  BMG_ERR_SINGULAR = 4,      /* enriched mass matrix rank below k                */
+  BMG_ERR_NOT_CONVERGED = 5, /* cycle cap reached; best pairs are returned       */
+  BMG_ERR_NONFINITE = 6,     /* NaN/Inf met in the iteration                     */
+  BMG_ERR_MESH = 7,          /* input mesh not a closed manifold triangulation   */
+  BMG_ERR_STATE = 8          /* call order violated (e.g. solve before hierarchy)*/
+} bmg_status;
+
+typedef enum { BMG_SMOOTH_JACOBI = 0, BMG_SMOOTH_MCGS = 1, BMG_SMOOTH_MCSGS = 2 } bmg_smoother;
+
+/* Source problem smoothed for each Ritz pair (theta_i, u_i), lambda_i = theta_i + sigma:
+ *   BMG_FORM_SHIFTED:     (A - sigma M) x_i = theta_i M u_i   (Eq. pb-m-s, Alg. 3 step 3)
+ *   BMG_FORM_HOMOGENEOUS: (A - lambda_i M) x_i = 0
+ * Both start from x_i = u_i and have the same residual there.                       */
+typedef enum { BMG_FORM_SHIFTED = 0, BMG_FORM_HOMOGENEOUS = 1 } bmg_form;
+
+typedef struct {
+  int smoother;              /* bmg_smoother                                      */
+  int nu;                    /* sweeps per level (SGS: forward+backward = 1)       */
+  double omega;              /* Jacobi damping (ignored by Gauss-Seidel)           */
+  int form;                  /* bmg_form                                          */
+  int vcycle_depth;          /* max coarse levels visited after the fine sweeps   */
+  int cycles_intermediate;   /* cycle cap on levels 2..L-1                         */
+  double tol_intermediate;   /* early stop on levels 2..L-1 (<0: none)             */
+  int max_cycles;            /* cycle cap on the finest level                      */
+} bmg_options;
+
+/* Fills the defaults: Jacobi, nu=2, omega=2/3, shifted form, full depth,
+ * 6 intermediate cycles, no intermediate tolerance, 200 finest cycles.            */
+void bmg_default_options(bmg_options* opt);
+
+typedef struct bmg_problem bmg_problem;
+
+typedef struct {
+  int levels;                /* hierarchy levels (finest = levels)                 */
+  int cycles[32];            /* cycles run on level l+2 (levels 2..L)              */
+  int total_cycles;
+  int converged;             /* 1 if every wanted pair met tol                    */
+  double max_resid;          /* largest wanted relative residual at exit          */
+} bmg_solve_info;
+
+/* ---------------------------------------------------------------- set-up ----- */
+
+/* Builds the surface hierarchy from a coarse input mesh (Sec. 3; Sec. 2.1).
+ *   verts [n_verts][3] host, float64: coarse vertex positions.  They are first
+ *         projected onto the surface, as are all new vertices.
+ *   tris  [n_tris][3]  host, int32: outward-oriented triangles of a closed
+ *         two-manifold (every edge shared by exactly two triangles).
+ *   refinements: number of uniform refinements R (0 <= R <= 10).
+ *   amplitude, sh_coefs: surface = star-shaped sphere r(n) n with
+ *         r(n) = 1 + amplitude * sum_{l<=4} c_lm Y_lm(n); sh_coefs [25] host
+ *         (l = 0..4, m = -l..l), ignored when amplitude == 0 (unit sphere).
+ *   stream: stream for all set-up work.  Returns after the work completes.
+ * Refinement r numbers old vertices first and the midpoint of edge (i<j) as
+ * N_{r-1} + rank of (i,j) among the lexicographically sorted edges; the children
+ * of triangle t=(a,b,c) are (a,m_ab,m_ca), (b,m_bc,m_ab), (c,m_ca,m_bc),
+ * (m_ab,m_bc,m_ca) at 4t..4t+3.  P1 stiffness and mass (Eq. bl-dis, sp-fe) are
+ * assembled on every refinement >= 1.
+ * Errors: BMG_ERR_INVALID_ARG, BMG_ERR_MESH, BMG_ERR_OOM, BMG_ERR_CUDA.          */
+bmg_status bmg_assemble(const double* verts, int n_verts, const int* tris, int n_tris,
+                        int refinements, double amplitude, const double* sh_coefs,
+                        void* stream, bmg_problem** out);
+
+/* Builds the multilevel structures on levels 1..L, level l = refinement
+ * R-L+l (so `levels` = R makes refinement 1 the coarsest level): prolongations
+ * P_l (Eq. proj-1: 1 at old vertices, 1/2 at both parents of a midpoint), the
+ * restriction P_l^T (Sec. 3), the Galerkin operators P^T A P and P^T M P of every
+ * finest level f on every coarser level (Sec. 1.1, Eq. evalapprox), and a greedy
+ * colouring per level in descending (splitmix64(v), v) priority.  Synchronous.
+ * Errors: BMG_ERR_INVALID_ARG (levels < 2 or > R), BMG_ERR_STATE, BMG_ERR_OOM.   */
+bmg_status bmg_hierarchy(bmg_problem* p, int levels);
+
+void bmg_destroy(bmg_problem* p);
+
+/* Thread-local text of the last error (never NULL). */
+const char* bmg_last_error(void);
+
+/* ------------------------------------------------------------------ solve ---- */
+
+/* BFMG (Alg. 4) on levels 2..L with BMG cycles (Alg. 3): enriched Rayleigh-Ritz
+ * in V_{h_1} + span(X) (Sec. 4.1 block matrices), source-problem smoothing from
+ * the finest level down (Alg. 3 step 3), prolongation of the Ritz vectors to the
+ * next level.  Returns the n_wanted Ritz pairs nearest sigma on level L.
+ *   k: block size (n_wanted <= k <= N_2, k <= 160, N_1 + k <= 320); sigma: shift; tol: the
+ *      finest level stops when every wanted pair has
+ *      ||A u - lambda M u||_2 / (||A||_1 ||u||_2) <= tol.
+ *   opt: options (NULL = defaults).
+ *   X0 [N_2][k] row-major float64: initial block on level 2, host memory if
+ *      x0_on_device == 0, else device memory.
+ *   evals [n_wanted] host: Ritz values, in selection order (|lambda - sigma|
+ *      ascending, ties by value then index).
+ *   evecs [N_L][n_wanted] row-major float64, host (evecs_on_device == 0) or
+ *      device (== 1), or NULL: Ritz vectors, M-orthonormal.
+ *   resid [n_wanted] host or NULL: relative residuals.
+ *   info: optional host struct.
+ * Synchronous.  Errors: BMG_ERR_INVALID_ARG, BMG_ERR_STATE, BMG_ERR_SINGULAR,
+ * BMG_ERR_NONFINITE, BMG_ERR_CUDA; BMG_ERR_NOT_CONVERGED fills all outputs with the
+ * last Ritz pairs.                                                               */
+bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigma, double tol,
+                     const bmg_options* opt, const double* X0, int x0_on_device,
+                     double* evals, double* evecs, int evecs_on_device, double* resid,
+                     bmg_solve_info* info);
+
+/* ---------------------------------------------- inspection (host outputs) --- */
+
+/* Sizes of refinement r (0..R): vertices, triangles, CSR nonzeros.             */
+bmg_status bmg_get_sizes(const bmg_problem* p, int refinement, int* n, int* n_tris,
+                         int* nnz);
+/* Mesh of refinement r: verts [n][3], tris [n_tris][3], parents [n][2] (parents
+ * of refinement 0 are (v,v)).  Any output may be NULL.  Host memory.            */
+bmg_status bmg_get_mesh(const bmg_problem* p, int refinement, double* verts, int* tris,
+                        int* parents);
+/* CSR of refinement r >= 1: row_ptr [n+1], col [nnz], a [nnz], m [nnz] (host,
+ * any may be NULL).                                                             */
+bmg_status bmg_get_csr(const bmg_problem* p, int refinement, int* row_ptr, int* col,
+                       double* a, double* m);
+/* Galerkin values of finest level f on level j < f (pattern of level j; levels
+ * in 1..L as in bmg_hierarchy), host.                                           */
+bmg_status bmg_get_galerkin(const bmg_problem* p, int f, int j, double* a, double* m);
+/* Colouring of level l (1..L): colour [n] host; returns the colour count.        */
+bmg_status bmg_get_colouring(const bmg_problem* p, int level, int* colour,
+                             int* n_colours);
+
+/* ------------------------------------- individual cycle steps (device data) -- */
+/* All pointers below are device memory; all calls are asynchronous on `stream`.
+ * `level` is a hierarchy level (1..L); `f` selects the operator set: f == level
+ * means the assembled A_l, M_l; f > level the Galerkin operators of finest level
+ * f on `level`.  Blocks are k-interleaved with leading dimension ld.            */
+
+/* [AX | MX] = [A X | M X] in one pass over the shared pattern (matrix form of
+ * Eq. pb-f-aux-mat; blocks of Sec. 4.1).                                        */
+bmg_status bmg_spmm(const bmg_problem* p, int f, int level, const double* X, int k,
+                    int ld, double* AX, double* MX, void* stream);
+
+/* nu sweeps of the smoother on (A - s_i M) x_i = b_i, in place on X
+ * (Remark after Alg. 1; Sec. 5.3).  s [k] device shifts; B [N][ld] device right-
+ * hand side or NULL for b = 0.  smoother: bmg_smoother; omega used by Jacobi.
+ * Jacobi needs a work block: work [N][ld] device (caller-owned).                */
+bmg_status bmg_smooth(const bmg_problem* p, int f, int level, double* X, const double* B,
+                      const double* s, int k, int ld, int smoother, int nu, double omega,
+                      double* work, void* stream);
+
+/* Y = P_l Xc (level l-1 -> l, Eq. proj-1); with add != 0: Y += P_l Xc.          */
+bmg_status bmg_prolong(const bmg_problem* p, int level, const double* Xc, double* Y,
+                       int k, int ld, int add, void* stream);
+/* Zc = P_l^T R (level l -> l-1).                                                 */
+bmg_status bmg_restrict(const bmg_problem* p, int level, const double* R, double* Zc,
+                        int k, int ld, void* stream);
+
+/* G[i][j] = sum_r X[r][i] Y[r][j] (k x k, row-major, float64) for X, Y [n][ld],
+ * 1 <= k <= 160.  Synchronous.                                                   */
+bmg_status bmg_gram(const double* X, const double* Y, int n, int k, int ld, double* G,
+                    void* stream);
+
+/* Smallest-|theta| k eigenpairs of the symmetric-semidefinite pencil
+ * (Ahat - sigma Mhat) y = theta Mhat y, n x n row-major device matrices (n <= 320):
+ * Mhat is scaled to unit diagonal, reduced by a Cholesky factorisation with
+ * diagonal pivoting that drops pivots below 1e-12 (rank-deficient enriched
+ * spaces), and the reduced standard problem is solved (Alg. 2 step 4).
+ * theta [k], Y [n][k] device; Y^T Mhat Y = I.  rank_out (device int or NULL)
+ * receives the kept rank.  Errors: BMG_ERR_INVALID_ARG; a rank below k is
+ * reported through bmg_solve as BMG_ERR_SINGULAR.                               */
+bmg_status bmg_dense_eig(const double* Ahat, const double* Mhat, int n, double sigma,
+                         int k, double* theta, double* Y, int* rank_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BMG_H */

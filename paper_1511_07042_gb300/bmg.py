@@ -1,0 +1,234 @@
+"""Thin ctypes binding of libbmg (include/bmg.h): argument marshalling only.
+
+Every computation runs inside libbmg's CUDA kernels.  Device buffers are torch CUDA
+tensors (float64, contiguous) passed by pointer together with the current torch
+stream; host outputs are numpy arrays.  Importing this module loads libbmg.so and
+raises if it is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbmg.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "bmg.h")
+
+SMOOTHERS = {"jacobi": 0, "mcgs": 1, "mcsgs": 2}
+FORMS = {"shifted": 0, "homogeneous": 1}
+STATUS = {0: "BMG_OK", 1: "BMG_ERR_INVALID_ARG", 2: "BMG_ERR_CUDA", 3: "BMG_ERR_OOM",
+          4: "BMG_ERR_SINGULAR", 5: "BMG_ERR_NOT_CONVERGED", 6: "BMG_ERR_NONFINITE",
+          7: "BMG_ERR_MESH", 8: "BMG_ERR_STATE"}
+
+
+class BmgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("smoother", C.c_int), ("nu", C.c_int), ("omega", C.c_double), ("form", C.c_int),
+                ("vcycle_depth", C.c_int), ("cycles_intermediate", C.c_int),
+                ("tol_intermediate", C.c_double), ("max_cycles", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("levels", C.c_int), ("cycles", C.c_int * 32), ("total_cycles", C.c_int),
+                ("converged", C.c_int), ("max_resid", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libbmg.so not built: run `python -c 'import __graft_entry__ as g; g.build()'` "
+                          "(expected at %s)" % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    vp, ip, dp, i, d = C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_double
+    P = C.POINTER
+    sig = {
+        "bmg_default_options": (None, [P(Options)]),
+        "bmg_last_error": (C.c_char_p, []),
+        "bmg_destroy": (None, [vp]),
+        "bmg_assemble": (i, [vp, i, vp, i, i, d, vp, vp, P(vp)]),
+        "bmg_hierarchy": (i, [vp, i]),
+        "bmg_solve": (i, [vp, i, i, d, d, P(Options), vp, i, vp, vp, i, vp, P(SolveInfo)]),
+        "bmg_get_sizes": (i, [vp, i, P(C.c_int), P(C.c_int), P(C.c_int)]),
+        "bmg_get_mesh": (i, [vp, i, vp, vp, vp]),
+        "bmg_get_csr": (i, [vp, i, vp, vp, vp, vp]),
+        "bmg_get_galerkin": (i, [vp, i, i, vp, vp]),
+        "bmg_get_colouring": (i, [vp, i, vp, P(C.c_int)]),
+        "bmg_spmm": (i, [vp, i, i, vp, i, i, vp, vp, vp]),
+        "bmg_smooth": (i, [vp, i, i, vp, vp, vp, i, i, i, i, d, vp, vp]),
+        "bmg_prolong": (i, [vp, i, vp, vp, i, i, i, vp]),
+        "bmg_restrict": (i, [vp, i, vp, vp, i, i, vp]),
+        "bmg_gram": (i, [vp, vp, i, i, i, vp, vp]),
+        "bmg_dense_eig": (i, [vp, vp, i, d, i, vp, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def header_symbols():
+    """Function names declared in include/bmg.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(bmg_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(code):
+    if code != 0:
+        raise BmgError(code, LIB.bmg_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_depth=99,
+            cycles_intermediate=6, tol_intermediate=-1.0, max_cycles=200) -> Options:
+    o = Options()
+    LIB.bmg_default_options(C.byref(o))
+    o.smoother = SMOOTHERS[smoother]
+    o.nu = nu
+    o.omega = omega
+    o.form = FORMS[form]
+    o.vcycle_depth = vcycle_depth
+    o.cycles_intermediate = cycles_intermediate
+    o.tol_intermediate = tol_intermediate
+    o.max_cycles = max_cycles
+    return o
+
+
+class Problem:
+    """A surface hierarchy and its operators, owned by libbmg on the GPU."""
+
+    def __init__(self, verts, tris, refinements, amplitude=0.0, coefs=None, stream=None):
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        t = np.ascontiguousarray(tris, dtype=np.int32)
+        cf = None if coefs is None else np.ascontiguousarray(coefs, dtype=np.float64)
+        h = C.c_void_p()
+        s = _stream() if stream is None else stream
+        _check(LIB.bmg_assemble(_ptr(v), v.shape[0], _ptr(t), t.shape[0], refinements, float(amplitude),
+                                _ptr(cf), s, C.byref(h)))
+        self.h = h
+        self.refinements = refinements
+        self.levels = 0
+
+    def close(self):
+        if getattr(self, "h", None):
+            LIB.bmg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def hierarchy(self, levels):
+        _check(LIB.bmg_hierarchy(self.h, levels))
+        self.levels = levels
+
+    def level_refinement(self, level):
+        return self.refinements - self.levels + level
+
+    def sizes(self, refinement):
+        n, nt, nnz = C.c_int(), C.c_int(), C.c_int()
+        _check(LIB.bmg_get_sizes(self.h, refinement, C.byref(n), C.byref(nt), C.byref(nnz)))
+        return n.value, nt.value, nnz.value
+
+    def mesh(self, refinement):
+        n, nt, _ = self.sizes(refinement)
+        v = np.empty((n, 3)); t = np.empty((nt, 3), np.int32); p = np.empty((n, 2), np.int32)
+        _check(LIB.bmg_get_mesh(self.h, refinement, _ptr(v), _ptr(t), _ptr(p)))
+        return v, t, p
+
+    def csr(self, refinement, values=True):
+        n, _, nnz = self.sizes(refinement)
+        rp = np.empty(n + 1, np.int32); col = np.empty(nnz, np.int32)
+        a = np.empty(nnz) if values else None
+        m = np.empty(nnz) if values else None
+        _check(LIB.bmg_get_csr(self.h, refinement, _ptr(rp), _ptr(col), _ptr(a), _ptr(m)))
+        return rp, col, a, m
+
+    def galerkin(self, f, j):
+        _, _, nnz = self.sizes(self.level_refinement(j))
+        a = np.empty(nnz); m = np.empty(nnz)
+        _check(LIB.bmg_get_galerkin(self.h, f, j, _ptr(a), _ptr(m)))
+        return a, m
+
+    def colouring(self, level):
+        n, _, _ = self.sizes(self.level_refinement(level))
+        c = np.empty(n, np.int32)
+        nc = C.c_int()
+        _check(LIB.bmg_get_colouring(self.h, level, _ptr(c), C.byref(nc)))
+        return c, nc.value
+
+    # ---- individual cycle steps on torch CUDA tensors ([N][ld] float64) -------
+    def spmm(self, f, level, X, k, AX, MX):
+        _check(LIB.bmg_spmm(self.h, f, level, _ptr(X), k, X.shape[1], _ptr(AX), _ptr(MX), _stream()))
+
+    def smooth(self, f, level, X, B, shift, k, smoother, nu, omega, work):
+        _check(LIB.bmg_smooth(self.h, f, level, _ptr(X), _ptr(B), _ptr(shift), k, X.shape[1],
+                              SMOOTHERS[smoother], nu, omega, _ptr(work), _stream()))
+
+    def prolong(self, level, Xc, Y, k, add=False):
+        _check(LIB.bmg_prolong(self.h, level, _ptr(Xc), _ptr(Y), k, Y.shape[1], int(add), _stream()))
+
+    def restrict(self, level, R, Zc, k):
+        _check(LIB.bmg_restrict(self.h, level, _ptr(R), _ptr(Zc), k, R.shape[1], _stream()))
+
+    def solve(self, X0, k, n_wanted, sigma, tol, opt=None, evecs=True, evecs_device=None):
+        """BFMG solve.  X0: numpy [N_2, k] (host) or torch CUDA tensor (device).
+
+        Returns (evals, evecs, resid, info) with evecs a numpy array, or the
+        caller's torch tensor `evecs_device` when given.
+        """
+        on_dev = not isinstance(X0, np.ndarray)
+        X0c = X0 if on_dev else np.ascontiguousarray(X0, dtype=np.float64)
+        nL = self.sizes(self.refinements)[0]
+        ev = np.empty(n_wanted)
+        rs = np.empty(n_wanted)
+        if evecs_device is not None:
+            U, udev = evecs_device, 1
+        elif evecs:
+            U, udev = np.empty((nL, n_wanted)), 0
+        else:
+            U, udev = None, 0
+        info = SolveInfo()
+        o = opt if opt is not None else options()
+        code = LIB.bmg_solve(self.h, k, n_wanted, float(sigma), float(tol), C.byref(o), _ptr(X0c),
+                             int(on_dev), _ptr(ev), _ptr(U), udev, _ptr(rs), C.byref(info))
+        if code not in (0, 5):
+            _check(code)
+        return ev, U, rs, info
+
+
+def gram(X, Y, k, G):
+    _check(LIB.bmg_gram(_ptr(X), _ptr(Y), X.shape[0], k, X.shape[1], _ptr(G), _stream()))
+
+
+def dense_eig(Ahat, Mhat, sigma, k, theta, Y, rank=None):
+    _check(LIB.bmg_dense_eig(_ptr(Ahat), _ptr(Mhat), Ahat.shape[0], float(sigma), k, _ptr(theta),
+                             _ptr(Y), _ptr(rank), _stream()))

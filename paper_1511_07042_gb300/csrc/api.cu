@@ -1,0 +1,642 @@
+// C ABI of libbmg: set-up, hierarchy, the BFMG solve and the per-step entry points.
+//
+// The solve is Alg. 4 (BFMG) over levels 2..L with the BMG cycle of Alg. 3 on each
+// level f:
+//   1. [AX | MX] on the k-block X                       (matrix form, Eq. pb-f-aux-mat)
+//   2. Grams X^T AX, X^T MX and the couplings Q^T AX, Q^T MX by the restriction chain
+//      (block matrices of Sec. 4.1; Q = P_2 ... P_f)
+//   3. eigensolve in V_{h_1} + span X, k pairs nearest sigma        (Alg. 2 step 4)
+//   4. Ritz vectors U = Q Y_c + X Y_x, their residuals; stop when all wanted pairs
+//      meet tol (finest level) or after the intermediate cycle cap
+//   5. source problems from U smoothed on level f, then corrections on coarser
+//      levels (Galerkin operators) prolonged back        (Alg. 3 step 3, Eq. pb-m-s)
+// Between levels the Ritz vectors are prolongated (Alg. 4 step 3, Eq. proj-1).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace bmg {
+
+static thread_local std::string g_last_error = "no error";
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+struct BmgException {
+  bmg_status code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(bmg_status code, const std::string& msg) { throw BmgException{code, msg}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(e == cudaErrorMemoryAllocation ? BMG_ERR_OOM : BMG_ERR_CUDA,
+         std::string(what) + ": " + cudaGetErrorString(e));
+  }
+}
+
+void check_launch(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) fail(BMG_ERR_CUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e));
+}
+
+namespace {
+
+template <typename F>
+bmg_status guarded(F&& f) {
+  try {
+    f();
+    return BMG_OK;
+  } catch (const BmgException& e) {
+    set_error(e.msg);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return BMG_ERR_OOM;
+  } catch (...) {
+    set_error("unknown error");
+    return BMG_ERR_CUDA;
+  }
+}
+
+__global__ void csr_to_dense_kernel(const int* row_ptr, const int* col, const double* v, int n,
+                                    double* D) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int j = 0; j < n; ++j) D[i * n + j] = 0.0;
+  for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) D[i * n + col[p]] = v[p];
+}
+
+__global__ void row_abs_max_kernel(const int* row_ptr, const double* v, int n,
+                                   unsigned long long* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) s += fabs(v[p]);
+  atomicMax(out, (unsigned long long)__double_as_longlong(s));
+}
+
+__global__ void ratio_max_kernel(const double* da, const double* dm, int n, unsigned long long* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double r = dm[i] / da[i];
+  if (!(r >= 0.0)) r = 1e300;
+  atomicMax(out, (unsigned long long)__double_as_longlong(r));
+}
+
+// Ahat = [[AQ, CA], [CA^T, GA]] (n = n1 + k), CA read from a [n1][ld] block.
+__global__ void assemble_hat_kernel(const double* AQ, const double* CA, const double* GA, int n1,
+                                    int k, int ld, double* H) {
+  const int n = n1 + k;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * n) return;
+  const int i = q / n, j = q % n;
+  double v;
+  if (i < n1 && j < n1) v = AQ[i * n1 + j];
+  else if (i < n1) v = CA[(size_t)i * ld + (j - n1)];
+  else if (j < n1) v = CA[(size_t)j * ld + (i - n1)];
+  else v = GA[(i - n1) * k + (j - n1)];
+  H[q] = v;
+}
+
+// Coarse coefficients Y[0:n1][0:k] into a [n1][ld] block (zero padding).
+__global__ void pack_coarse_kernel(const double* Y, int n1, int k, int ld, double* Z) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n1 * ld) return;
+  const int i = q / ld, c = q % ld;
+  Z[q] = (c < k) ? Y[i * k + c] : 0.0;
+}
+
+// lam = theta + sigma; shift per column (form), zero in the padding.
+__global__ void shifts_kernel(const double* theta, int k, int ld, double sigma, int form,
+                              double* lam, double* shift) {
+  const int c = threadIdx.x + blockIdx.x * blockDim.x;
+  if (c >= ld) return;
+  if (c < k) {
+    lam[c] = theta[c] + sigma;
+    shift[c] = (form == BMG_FORM_SHIFTED) ? sigma : theta[c] + sigma;
+  } else {
+    lam[c] = 0.0;
+    shift[c] = 0.0;
+  }
+}
+
+int grid_of(size_t n, int b) { return (int)std::max<size_t>(1, (n + b - 1) / b); }
+
+}  // namespace
+}  // namespace bmg
+
+using namespace bmg;
+
+// ------------------------------------------------------------------------------
+extern "C" void bmg_default_options(bmg_options* o) {
+  if (!o) return;
+  o->smoother = BMG_SMOOTH_JACOBI;
+  o->nu = 2;
+  o->omega = 2.0 / 3.0;
+  o->form = BMG_FORM_SHIFTED;
+  o->vcycle_depth = 99;
+  o->cycles_intermediate = 6;
+  o->tol_intermediate = -1.0;
+  o->max_cycles = 200;
+}
+
+extern "C" const char* bmg_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" void bmg_destroy(bmg_problem* p) {
+  if (!p) return;
+  try { delete p; } catch (...) {}
+}
+
+extern "C" bmg_status bmg_assemble(const double* verts, int n_verts, const int* tris, int n_tris,
+                                   int refinements, double amplitude, const double* sh_coefs,
+                                   void* stream, bmg_problem** out) {
+  return guarded([&] {
+    if (!out) fail(BMG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!verts || !tris || n_verts < 4 || n_tris < 4) fail(BMG_ERR_INVALID_ARG, "empty or null mesh");
+    if (refinements < 0 || refinements > 10) fail(BMG_ERR_INVALID_ARG, "refinements must be in 0..10");
+    if (amplitude != 0.0 && !sh_coefs) fail(BMG_ERR_INVALID_ARG, "sh_coefs is NULL");
+    if (!std::isfinite(amplitude)) fail(BMG_ERR_INVALID_ARG, "amplitude not finite");
+    for (int i = 0; i < 3 * n_tris; ++i)
+      if (tris[i] < 0 || tris[i] >= n_verts) fail(BMG_ERR_MESH, "triangle index out of range");
+    std::unique_ptr<bmg_problem> p(new bmg_problem());
+    p->stream = (cudaStream_t)stream;
+    cudaStream_t s = p->stream;
+    p->R = refinements;
+    p->amplitude = amplitude;
+    p->mesh.resize(refinements + 1);
+    double C[17];
+    fill_sh_constants(C);
+    DBuf<double> dC(17), dcf(25);
+    double cf[25] = {0};
+    if (amplitude != 0.0) std::memcpy(cf, sh_coefs, sizeof(cf));
+    BMG_CUDA(cudaMemcpyAsync(dC.get(), C, sizeof(C), cudaMemcpyHostToDevice, s));
+    BMG_CUDA(cudaMemcpyAsync(dcf.get(), cf, sizeof(cf), cudaMemcpyHostToDevice, s));
+    Mesh& m0 = p->mesh[0];
+    m0.n = n_verts;
+    m0.n_tris = n_tris;
+    m0.verts.alloc(3 * (size_t)n_verts);
+    m0.tris.alloc(3 * (size_t)n_tris);
+    m0.parents.alloc(2 * (size_t)n_verts);
+    BMG_CUDA(cudaMemcpyAsync(m0.verts.get(), verts, sizeof(double) * 3 * n_verts, cudaMemcpyHostToDevice, s));
+    BMG_CUDA(cudaMemcpyAsync(m0.tris.get(), tris, sizeof(int) * 3 * n_tris, cudaMemcpyHostToDevice, s));
+    {
+      std::vector<int> par(2 * (size_t)n_verts);
+      for (int i = 0; i < n_verts; ++i) { par[2 * i] = i; par[2 * i + 1] = i; }
+      BMG_CUDA(cudaMemcpyAsync(m0.parents.get(), par.data(), sizeof(int) * par.size(), cudaMemcpyHostToDevice, s));
+      BMG_CUDA(cudaStreamSynchronize(s));
+    }
+    project_input(m0, amplitude, dC.get(), dcf.get(), s);
+    build_mesh_pattern(m0, s);
+    for (int r = 1; r <= refinements; ++r) {
+      refine_mesh(p->mesh[r - 1], p->mesh[r], amplitude, dC.get(), dcf.get(), s);
+      assemble_p1(p->mesh[r], s);
+    }
+    BMG_CUDA(cudaStreamSynchronize(s));
+    *out = p.release();
+  });
+}
+
+extern "C" bmg_status bmg_hierarchy(bmg_problem* p, int levels) {
+  return guarded([&] {
+    if (!p) fail(BMG_ERR_INVALID_ARG, "null problem");
+    if (levels < 2 || levels > p->R) fail(BMG_ERR_INVALID_ARG, "levels must be in 2..refinements");
+    if (p->L) fail(BMG_ERR_STATE, "hierarchy already built");
+    cudaStream_t s = p->stream;
+    const int L = levels;
+    p->r0 = p->R - L + 1;
+    if (p->r0 < 1) fail(BMG_ERR_INVALID_ARG, "coarsest level must be refinement >= 1");
+    p->lev.clear();
+    p->lev.resize(L + 1);
+    for (int l = 1; l <= L; ++l) {
+      p->lev[l].refinement = p->r0 + l - 1;
+      colour_level(p->meshOf(l), p->lev[l], s);
+    }
+    p->ops.clear();
+    p->ops.resize(L + 1);
+    p->norm1.assign(L + 1, 0.0);
+    p->coarseA.assign(L + 1, {});
+    p->coarseM.assign(L + 1, {});
+    DBuf<unsigned long long> um(1);
+    for (int f = 2; f <= L; ++f) {
+      p->ops[f].resize(f + 1);
+      for (int j = f; j >= 1; --j) {
+        const Mesh& mj = p->meshOf(j);
+        OpSet& o = p->ops[f][j];
+        if (j < f) {
+          o.a.alloc(mj.nnz);
+          o.m.alloc(mj.nnz);
+          galerkin(p->meshOf(j + 1), mj, p->opA(f, j + 1), p->opM(f, j + 1), o.a.get(), o.m.get(), s);
+        }
+        o.da.alloc(mj.n);
+        o.dm.alloc(mj.n);
+        extract_diag(mj, p->opA(f, j), p->opM(f, j), o.da.get(), o.dm.get(), s);
+      }
+      const Mesh& mf = p->meshOf(f);
+      BMG_CUDA(cudaMemsetAsync(um.get(), 0, sizeof(unsigned long long), s));
+      row_abs_max_kernel<<<grid_of(mf.n, 256), 256, 0, s>>>(mf.row_ptr.get(), mf.valA.get(), mf.n, um.get());
+      check_launch("row_abs_max_kernel");
+      unsigned long long h = 0;
+      BMG_CUDA(cudaMemcpyAsync(&h, um.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+      BMG_CUDA(cudaStreamSynchronize(s));
+      double nrm;
+      std::memcpy(&nrm, &h, sizeof(nrm));
+      p->norm1[f] = nrm;
+    }
+    p->L = L;
+  });
+}
+
+// ----------------------------------------------------------------- inspection -
+static const Mesh& mesh_at(const bmg_problem* p, int r) {
+  if (!p) fail(BMG_ERR_INVALID_ARG, "null problem");
+  if (r < 0 || r > p->R) fail(BMG_ERR_INVALID_ARG, "refinement out of range");
+  return p->mesh[r];
+}
+
+extern "C" bmg_status bmg_get_sizes(const bmg_problem* p, int r, int* n, int* nt, int* nnz) {
+  return guarded([&] {
+    const Mesh& m = mesh_at(p, r);
+    if (n) *n = m.n;
+    if (nt) *nt = m.n_tris;
+    if (nnz) *nnz = m.nnz;
+  });
+}
+
+extern "C" bmg_status bmg_get_mesh(const bmg_problem* p, int r, double* verts, int* tris, int* parents) {
+  return guarded([&] {
+    const Mesh& m = mesh_at(p, r);
+    if (verts) BMG_CUDA(cudaMemcpy(verts, m.verts.get(), sizeof(double) * 3 * m.n, cudaMemcpyDeviceToHost));
+    if (tris) BMG_CUDA(cudaMemcpy(tris, m.tris.get(), sizeof(int) * 3 * m.n_tris, cudaMemcpyDeviceToHost));
+    if (parents) BMG_CUDA(cudaMemcpy(parents, m.parents.get(), sizeof(int) * 2 * m.n, cudaMemcpyDeviceToHost));
+  });
+}
+
+extern "C" bmg_status bmg_get_csr(const bmg_problem* p, int r, int* row_ptr, int* col, double* a, double* mm) {
+  return guarded([&] {
+    const Mesh& m = mesh_at(p, r);
+    if (row_ptr) BMG_CUDA(cudaMemcpy(row_ptr, m.row_ptr.get(), sizeof(int) * (m.n + 1), cudaMemcpyDeviceToHost));
+    if (col) BMG_CUDA(cudaMemcpy(col, m.col.get(), sizeof(int) * m.nnz, cudaMemcpyDeviceToHost));
+    if ((a || mm) && r < 1) fail(BMG_ERR_INVALID_ARG, "no matrices on refinement 0");
+    if (a) BMG_CUDA(cudaMemcpy(a, m.valA.get(), sizeof(double) * m.nnz, cudaMemcpyDeviceToHost));
+    if (mm) BMG_CUDA(cudaMemcpy(mm, m.valM.get(), sizeof(double) * m.nnz, cudaMemcpyDeviceToHost));
+  });
+}
+
+static void check_levels(const bmg_problem* p, int f, int j) {
+  if (!p) fail(BMG_ERR_INVALID_ARG, "null problem");
+  if (!p->L) fail(BMG_ERR_STATE, "bmg_hierarchy not called");
+  if (f < 1 || f > p->L || j < 1 || j > f) fail(BMG_ERR_INVALID_ARG, "level out of range");
+}
+
+extern "C" bmg_status bmg_get_galerkin(const bmg_problem* p, int f, int j, double* a, double* mm) {
+  return guarded([&] {
+    check_levels(p, f, j);
+    if (f < 2) fail(BMG_ERR_INVALID_ARG, "f must be >= 2");
+    const Mesh& m = p->meshOf(j);
+    if (a) BMG_CUDA(cudaMemcpy(a, p->opA(f, j), sizeof(double) * m.nnz, cudaMemcpyDeviceToHost));
+    if (mm) BMG_CUDA(cudaMemcpy(mm, p->opM(f, j), sizeof(double) * m.nnz, cudaMemcpyDeviceToHost));
+  });
+}
+
+extern "C" bmg_status bmg_get_colouring(const bmg_problem* p, int level, int* colour, int* n_colours) {
+  return guarded([&] {
+    check_levels(p, level, level);
+    if (colour) BMG_CUDA(cudaMemcpy(colour, p->lev[level].colour.get(), sizeof(int) * p->meshOf(level).n, cudaMemcpyDeviceToHost));
+    if (n_colours) *n_colours = p->lev[level].n_colours;
+  });
+}
+
+// ------------------------------------------------------------- step entries ---
+static const double* opDA_or_compute(const bmg_problem* p, int f, int j) {
+  if (f >= 2) return p->opDA(f, j);
+  return nullptr;
+}
+
+extern "C" bmg_status bmg_spmm(const bmg_problem* p, int f, int level, const double* X, int k, int ld,
+                               double* AX, double* MX, void* stream) {
+  return guarded([&] {
+    check_levels(p, f, level);
+    if (!X || !AX || !MX || k < 1 || ld < k || (ld & 1)) fail(BMG_ERR_INVALID_ARG, "bad block arguments");
+    spmm_am(p->meshOf(level), p->opA(f, level), p->opM(f, level), X, ld, AX, MX, (cudaStream_t)stream);
+  });
+}
+
+extern "C" bmg_status bmg_smooth(const bmg_problem* p, int f, int level, double* X, const double* B,
+                                 const double* sft, int k, int ld, int smoother, int nu, double omega,
+                                 double* work, void* stream) {
+  return guarded([&] {
+    check_levels(p, f, level);
+    if (f < 2) fail(BMG_ERR_INVALID_ARG, "f must be >= 2");
+    if (!X || !sft || k < 1 || ld < k || (ld & 1) || nu < 0) fail(BMG_ERR_INVALID_ARG, "bad block arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    const Mesh& m = p->meshOf(level);
+    const double *a = p->opA(f, level), *mm = p->opM(f, level);
+    const double *da = p->opDA(f, level), *dm = p->opDM(f, level);
+    (void)opDA_or_compute;
+    if (smoother == BMG_SMOOTH_JACOBI) {
+      if (!work) fail(BMG_ERR_INVALID_ARG, "Jacobi needs a work block");
+      for (int it = 0; it < nu; ++it) {
+        jacobi_sweep(m, a, mm, da, dm, X, work, B, sft, ld, omega, s);
+        BMG_CUDA(cudaMemcpyAsync(X, work, sizeof(double) * (size_t)m.n * ld, cudaMemcpyDeviceToDevice, s));
+      }
+    } else if (smoother == BMG_SMOOTH_MCGS || smoother == BMG_SMOOTH_MCSGS) {
+      const Level& lv = p->lev[level];
+      for (int it = 0; it < nu; ++it) {
+        for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
+        if (smoother == BMG_SMOOTH_MCSGS)
+          for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
+      }
+    } else {
+      fail(BMG_ERR_INVALID_ARG, "unknown smoother");
+    }
+  });
+}
+
+extern "C" bmg_status bmg_prolong(const bmg_problem* p, int level, const double* Xc, double* Y, int k, int ld,
+                                  int add, void* stream) {
+  return guarded([&] {
+    check_levels(p, level, level);
+    if (level < 2) fail(BMG_ERR_INVALID_ARG, "level must be >= 2");
+    if (!Xc || !Y || k < 1 || ld < k || (ld & 1)) fail(BMG_ERR_INVALID_ARG, "bad block arguments");
+    prolong(p->meshOf(level), Xc, Y, ld, add != 0, (cudaStream_t)stream);
+  });
+}
+
+extern "C" bmg_status bmg_restrict(const bmg_problem* p, int level, const double* R, double* Zc, int k, int ld,
+                                   void* stream) {
+  return guarded([&] {
+    check_levels(p, level, level);
+    if (level < 2) fail(BMG_ERR_INVALID_ARG, "level must be >= 2");
+    if (!R || !Zc || k < 1 || ld < k || (ld & 1)) fail(BMG_ERR_INVALID_ARG, "bad block arguments");
+    restrict_(p->meshOf(level - 1), R, Zc, ld, (cudaStream_t)stream);
+  });
+}
+
+extern "C" bmg_status bmg_gram(const double* X, const double* Y, int n, int k, int ld, double* G, void* stream) {
+  return guarded([&] {
+    if (!X || !Y || !G || n < 1 || k < 1 || k > 160 || ld < k) fail(BMG_ERR_INVALID_ARG, "bad gram arguments (1 <= k <= 160)");
+    const int parts = gram_parts(n);
+    DBuf<double> partial((size_t)parts * k * k);
+    gram(X, Y, n, k, ld, G, partial.get(), parts, (cudaStream_t)stream);
+    BMG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  });
+}
+
+extern "C" bmg_status bmg_dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k,
+                                    double* theta, double* Y, int* rank_out, void* stream) {
+  return guarded([&] {
+    if (!Ahat || !Mhat || !theta || !Y) fail(BMG_ERR_INVALID_ARG, "null pointer");
+    if (n < 1 || n > 320 || k < 1 || k > n) fail(BMG_ERR_INVALID_ARG, "need 1 <= k <= n <= 320");
+    DBuf<double> work(dense_work_doubles(n));
+    DBuf<int> rk(1);
+    dense_eig(Ahat, Mhat, n, sigma, k, theta, Y, rank_out ? rank_out : rk.get(), work.get(), (cudaStream_t)stream);
+    BMG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  });
+}
+
+// ------------------------------------------------------------------- solve ----
+namespace {
+
+struct SolveWork {
+  int ld = 0, k = 0, n1 = 0, nh = 0, L = 0, parts = 0;
+  DBuf<double> X, AX, MX, U, AU, MU, B, W, Zf;
+  std::vector<DBuf<double>> cA, cB, cC, cD;  // per coarse level j < L: [N_j][ld]
+  DBuf<double> Ahat, Mhat, Y, theta, lam, shift, GA, GM, dense, partial, res;
+  DBuf<int> rank;
+  std::vector<DBuf<double>> AQ, MQ;        // per f: dense n1 x n1 coarse blocks
+};
+
+void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, double* X,
+                  const double* B, const double* shift, int ld, double* work, cudaStream_t s) {
+  const Mesh& m = p->meshOf(j);
+  const double *a = p->opA(f, j), *mm = p->opM(f, j), *da = p->opDA(f, j), *dm = p->opDM(f, j);
+  if (o.smoother == BMG_SMOOTH_JACOBI) {
+    for (int it = 0; it < o.nu; ++it) {
+      jacobi_sweep(m, a, mm, da, dm, X, work, B, shift, ld, o.omega, s);
+      BMG_CUDA(cudaMemcpyAsync(X, work, sizeof(double) * (size_t)m.n * ld, cudaMemcpyDeviceToDevice, s));
+    }
+  } else {
+    const Level& lv = p->lev[j];
+    for (int it = 0; it < o.nu; ++it) {
+      for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep(m, lv, c, a, mm, da, dm, X, B, shift, ld, s);
+      if (o.smoother == BMG_SMOOTH_MCSGS)
+        for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep(m, lv, c, a, mm, da, dm, X, B, shift, ld, s);
+    }
+  }
+}
+
+}  // namespace
+
+extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigma, double tol,
+                                const bmg_options* opt_in, const double* X0, int x0_on_device,
+                                double* evals, double* evecs, int evecs_on_device, double* resid,
+                                bmg_solve_info* info) {
+  bmg_status final_status = BMG_OK;
+  bmg_status st = guarded([&] {
+    if (!p) fail(BMG_ERR_INVALID_ARG, "null problem");
+    if (!p->L) fail(BMG_ERR_STATE, "bmg_hierarchy not called");
+    bmg_options o;
+    bmg_default_options(&o);
+    if (opt_in) o = *opt_in;
+    const int L = p->L;
+    const int n1 = p->meshOf(1).n, n2 = p->meshOf(2).n, nL = p->meshOf(L).n;
+    if (k < 1 || k > 160 || n_wanted < 1 || n_wanted > k || k > n2 || n1 + k > 320)
+      fail(BMG_ERR_INVALID_ARG, "need 1 <= n_wanted <= k <= min(N_2, 160) and N_1 + k <= 320");
+    if (!X0 || !evals) fail(BMG_ERR_INVALID_ARG, "X0 and evals are required");
+    if (!(tol > 0.0) || !std::isfinite(sigma)) fail(BMG_ERR_INVALID_ARG, "bad tol or sigma");
+    if (o.nu < 1 || o.nu > 64 || o.smoother < 0 || o.smoother > 2 || o.form < 0 || o.form > 1 ||
+        o.max_cycles < 1 || o.cycles_intermediate < 1)
+      fail(BMG_ERR_INVALID_ARG, "bad options");
+    cudaStream_t s = p->stream;
+    SolveWork w;
+    w.k = k;
+    w.ld = (k + 1) & ~1;
+    w.n1 = n1;
+    w.nh = n1 + k;
+    w.L = L;
+    const int ld = w.ld;
+    const size_t big = (size_t)nL * ld;
+    for (DBuf<double>* b : {&w.X, &w.AX, &w.MX, &w.U, &w.AU, &w.MU, &w.B, &w.W, &w.Zf}) {
+      b->alloc(big);
+      BMG_CUDA(cudaMemsetAsync(b->get(), 0, sizeof(double) * big, s));
+    }
+    w.cA.resize(L); w.cB.resize(L); w.cC.resize(L); w.cD.resize(L);
+    for (int j = 1; j < L; ++j) {
+      const size_t sz = (size_t)p->meshOf(j).n * ld;
+      for (auto* v : {&w.cA, &w.cB, &w.cC, &w.cD}) {
+        (*v)[j].alloc(sz);
+        BMG_CUDA(cudaMemsetAsync((*v)[j].get(), 0, sizeof(double) * sz, s));
+      }
+    }
+    w.Ahat.alloc((size_t)w.nh * w.nh);
+    w.Mhat.alloc((size_t)w.nh * w.nh);
+    w.Y.alloc((size_t)w.nh * k);
+    w.theta.alloc(k);
+    w.lam.alloc(ld);
+    w.shift.alloc(ld);
+    w.GA.alloc((size_t)k * k);
+    w.GM.alloc((size_t)k * k);
+    w.dense.alloc(dense_work_doubles(w.nh));
+    w.parts = gram_parts(nL);
+    w.partial.alloc((size_t)w.parts * std::max(k * k, 2 * k));
+    w.res.alloc(2 * k);
+    w.rank.alloc(1);
+    w.AQ.resize(L + 1);
+    w.MQ.resize(L + 1);
+    for (int f = 2; f <= L; ++f) {
+      w.AQ[f].alloc((size_t)n1 * n1);
+      w.MQ[f].alloc((size_t)n1 * n1);
+      const Mesh& m1 = p->meshOf(1);
+      csr_to_dense_kernel<<<grid_of(n1, 64), 64, 0, s>>>(m1.row_ptr.get(), m1.col.get(), p->opA(f, 1), n1, w.AQ[f].get());
+      csr_to_dense_kernel<<<grid_of(n1, 64), 64, 0, s>>>(m1.row_ptr.get(), m1.col.get(), p->opM(f, 1), n1, w.MQ[f].get());
+      check_launch("csr_to_dense_kernel");
+    }
+    // max over rows of dM/dA per (f, j), for the admissible depth of the down-leg
+    std::vector<std::vector<double>> ratio(L + 1, std::vector<double>(L + 1, 0.0));
+    {
+      DBuf<unsigned long long> um(1);
+      for (int f = 2; f <= L; ++f)
+        for (int j = 1; j < f; ++j) {
+          BMG_CUDA(cudaMemsetAsync(um.get(), 0, sizeof(unsigned long long), s));
+          ratio_max_kernel<<<grid_of(p->meshOf(j).n, 256), 256, 0, s>>>(p->opDA(f, j), p->opDM(f, j), p->meshOf(j).n, um.get());
+          unsigned long long h = 0;
+          BMG_CUDA(cudaMemcpyAsync(&h, um.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+          BMG_CUDA(cudaStreamSynchronize(s));
+          std::memcpy(&ratio[f][j], &h, sizeof(double));
+        }
+    }
+    // X0 -> X on level 2 (ld-strided)
+    BMG_CUDA(cudaMemcpy2DAsync(w.X.get(), sizeof(double) * ld, X0, sizeof(double) * k, sizeof(double) * k, n2,
+                               x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+
+    std::vector<double> hres(2 * k), htheta(k), hlam(k), rho(k);
+    int total_cycles = 0;
+    bool converged = false;
+    std::vector<int> cyc(L + 1, 0);
+    for (int f = 2; f <= L; ++f) {
+      const Mesh& mf = p->meshOf(f);
+      const int nf = mf.n;
+      if (f > 2) prolong(mf, w.U.get(), w.X.get(), ld, false, s);
+      const int budget = (f == L) ? o.max_cycles : o.cycles_intermediate;
+      const double ftol = (f == L) ? tol : o.tol_intermediate;
+      for (int c = 0; c < budget; ++c) {
+        // 1-2: products, Grams, couplings
+        spmm_am(mf, mf.valA.get(), mf.valM.get(), w.X.get(), ld, w.AX.get(), w.MX.get(), s);
+        gram(w.X.get(), w.AX.get(), nf, k, ld, w.GA.get(), w.partial.get(), gram_parts(nf), s);
+        gram(w.X.get(), w.MX.get(), nf, k, ld, w.GM.get(), w.partial.get(), gram_parts(nf), s);
+        const double* ca = w.AX.get();
+        const double* cm = w.MX.get();
+        for (int j = f; j >= 2; --j) {
+          restrict_(p->meshOf(j - 1), ca, w.cA[j - 1].get(), ld, s);
+          restrict_(p->meshOf(j - 1), cm, w.cB[j - 1].get(), ld, s);
+          ca = w.cA[j - 1].get();
+          cm = w.cB[j - 1].get();
+        }
+        const int nh = w.nh;
+        assemble_hat_kernel<<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.AQ[f].get(), ca, w.GA.get(), n1, k, ld, w.Ahat.get());
+        assemble_hat_kernel<<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.MQ[f].get(), cm, w.GM.get(), n1, k, ld, w.Mhat.get());
+        check_launch("assemble_hat_kernel");
+        // 3: enriched eigensolve
+        dense_eig(w.Ahat.get(), w.Mhat.get(), nh, sigma, k, w.theta.get(), w.Y.get(), w.rank.get(), w.dense.get(), s);
+        shifts_kernel<<<grid_of(ld, 128), 128, 0, s>>>(w.theta.get(), k, ld, sigma, o.form, w.lam.get(), w.shift.get());
+        check_launch("shifts_kernel");
+        // 4: Ritz vectors U = Q Y_c + X Y_x
+        pack_coarse_kernel<<<grid_of((size_t)n1 * ld, 256), 256, 0, s>>>(w.Y.get(), n1, k, ld, w.cC[1].get());
+        check_launch("pack_coarse_kernel");
+        const double* z = w.cC[1].get();
+        for (int j = 2; j < f; ++j) {
+          prolong(p->meshOf(j), z, w.cC[j].get(), ld, false, s);
+          z = w.cC[j].get();
+        }
+        prolong(mf, z, w.Zf.get(), ld, false, s);
+        expand(w.Zf.get(), w.X.get(), w.Y.get() + (size_t)n1 * k, nf, k, ld, k, w.U.get(), s);
+        spmm_am(mf, mf.valA.get(), mf.valM.get(), w.U.get(), ld, w.AU.get(), w.MU.get(), s);
+        eig_residuals(w.AU.get(), w.MU.get(), w.U.get(), w.lam.get(), nf, k, ld, w.partial.get(), gram_parts(nf), w.res.get(), s);
+        int hrank = 0;
+        BMG_CUDA(cudaMemcpyAsync(hres.data(), w.res.get(), sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
+        BMG_CUDA(cudaMemcpyAsync(hlam.data(), w.lam.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+        BMG_CUDA(cudaMemcpyAsync(&hrank, w.rank.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        BMG_CUDA(cudaStreamSynchronize(s));
+        ++total_cycles;
+        cyc[f] = c + 1;
+        if (hrank < k) fail(BMG_ERR_SINGULAR, "enriched space rank " + std::to_string(hrank) + " < k");
+        bool conv = true, finite = true;
+        for (int i = 0; i < k; ++i) {
+          rho[i] = std::sqrt(hres[i]) / (p->norm1[f] * std::sqrt(hres[k + i]));
+          if (!std::isfinite(rho[i]) || !std::isfinite(hlam[i])) finite = false;
+          if (i < n_wanted && !(rho[i] <= ftol)) conv = false;
+        }
+        if (!finite) fail(BMG_ERR_NONFINITE, "non-finite Ritz pair on level " + std::to_string(f));
+        if (f == L) converged = conv;
+        if (conv || c + 1 == budget) break;
+        // 5: smoothing of the source problems from U, then the down-leg
+        const double* Bp = nullptr;
+        if (o.form == BMG_FORM_SHIFTED) {
+          scale_rhs(w.MU.get(), w.theta.get(), nf, k, ld, w.B.get(), s);
+          Bp = w.B.get();
+        }
+        BMG_CUDA(cudaMemcpyAsync(w.X.get(), w.U.get(), sizeof(double) * (size_t)nf * ld, cudaMemcpyDeviceToDevice, s));
+        smooth_level(p, f, f, o, w.X.get(), Bp, w.shift.get(), ld, w.W.get(), s);
+        double smax = (o.form == BMG_FORM_SHIFTED) ? sigma : -1e300;
+        if (o.form != BMG_FORM_SHIFTED) for (int i = 0; i < k; ++i) smax = std::max(smax, hlam[i]);
+        std::vector<int> legs;
+        for (int j = f - 1; j >= 1 && (int)legs.size() < o.vcycle_depth; --j) {
+          if (!(smax * ratio[f][j] < 1.0 - 0.25)) break;
+          legs.push_back(j);
+        }
+        if (!legs.empty()) {
+          residual(mf, mf.valA.get(), mf.valM.get(), w.X.get(), Bp, w.shift.get(), ld, w.W.get(), s);
+          const double* rprev = w.W.get();
+          for (size_t t = 0; t < legs.size(); ++t) {
+            const int j = legs[t];
+            const Mesh& mj = p->meshOf(j);
+            restrict_(mj, rprev, w.cA[j].get(), ld, s);
+            BMG_CUDA(cudaMemsetAsync(w.cB[j].get(), 0, sizeof(double) * (size_t)mj.n * ld, s));
+            smooth_level(p, f, j, o, w.cB[j].get(), w.cA[j].get(), w.shift.get(), ld, w.cD[j].get(), s);
+            if (t + 1 < legs.size()) {
+              residual(mj, p->opA(f, j), p->opM(f, j), w.cB[j].get(), w.cA[j].get(), w.shift.get(), ld, w.cC[j].get(), s);
+              rprev = w.cC[j].get();
+            }
+          }
+          for (size_t t = legs.size() - 1; t >= 1; --t) {
+            const int j = legs[t];  // coarser; add into level j+1
+            prolong(p->meshOf(j + 1), w.cB[j].get(), w.cB[j + 1].get(), ld, true, s);
+          }
+          prolong(mf, w.cB[f - 1].get(), w.X.get(), ld, true, s);
+        }
+      }
+    }
+    // outputs: the last Ritz pairs on level L
+    for (int i = 0; i < n_wanted; ++i) evals[i] = hlam[i];
+    if (resid) for (int i = 0; i < n_wanted; ++i) resid[i] = rho[i];
+    if (evecs) {
+      BMG_CUDA(cudaMemcpy2DAsync(evecs, sizeof(double) * n_wanted, w.U.get(), sizeof(double) * ld,
+                                 sizeof(double) * n_wanted, nL,
+                                 evecs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+      BMG_CUDA(cudaStreamSynchronize(s));
+    }
+    if (info) {
+      std::memset(info, 0, sizeof(*info));
+      info->levels = L;
+      for (int f = 2; f <= L && f - 2 < 32; ++f) info->cycles[f - 2] = cyc[f];
+      info->total_cycles = total_cycles;
+      info->converged = converged ? 1 : 0;
+      double mx = 0.0;
+      for (int i = 0; i < n_wanted; ++i) mx = std::max(mx, rho[i]);
+      info->max_resid = mx;
+    }
+    if (!converged) {
+      final_status = BMG_ERR_NOT_CONVERGED;
+      set_error("cycle cap reached before every wanted pair met tol");
+    }
+  });
+  return st != BMG_OK ? st : final_status;
+}

@@ -1,0 +1,168 @@
+// Internal definitions shared by the libbmg translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bmg.h"
+
+namespace bmg {
+
+// ---------------------------------------------------------------- errors ----
+void set_error(const std::string& msg);
+struct Error {
+  bmg_status code;
+  std::string msg;
+};
+// Throwing is confined to the library; every extern "C" entry catches.
+[[noreturn]] void fail(bmg_status code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define BMG_CUDA(call) ::bmg::check_cuda((call), #call)
+void check_launch(const char* what);
+
+// ------------------------------------------------------- device buffers ----
+// Owning device buffer (cudaMalloc / cudaFree), move-only.
+template <typename T>
+struct DBuf {
+  T* ptr = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  explicit DBuf(size_t count) { alloc(count); }
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept : ptr(o.ptr), n(o.n) { o.ptr = nullptr; o.n = 0; }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) { release(); ptr = o.ptr; n = o.n; o.ptr = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  void alloc(size_t count);
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    n = 0;
+  }
+  T* get() const { return ptr; }
+};
+
+template <typename T>
+void DBuf<T>::alloc(size_t count) {
+  release();
+  if (count == 0) return;
+  cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    cudaGetLastError();
+    fail(BMG_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: " +
+                          cudaGetErrorString(e));
+  }
+  n = count;
+}
+
+// ----------------------------------------------------------- structures ----
+// One refinement of the surface mesh (refinement 0 = the input mesh).
+struct Mesh {
+  int n = 0, n_tris = 0, nnz = 0;
+  DBuf<double> verts;    // [n][3]
+  DBuf<int> tris;        // [n_tris][3]
+  DBuf<int> parents;     // [n][2]
+  DBuf<int> row_ptr;     // [n+1] vertex adjacency incl. self, ascending columns
+  DBuf<int> col;         // [nnz]
+  DBuf<int> diag_pos;    // [n] position of the diagonal in each row
+  DBuf<int> inc_ptr;     // [n+1] incident triangles per vertex
+  DBuf<int> inc_tri;     // ascending triangle ids
+  DBuf<int> mid;         // [nnz] fine index of the midpoint of edge (i, col) (-1 on diag);
+                         //       filled when the next refinement exists
+  DBuf<double> valA, valM;  // [nnz] assembled P1 stiffness / mass (refinement >= 1)
+};
+
+// Operators of one level l of the hierarchy, for one finest level f.
+struct OpSet {
+  DBuf<double> a, m;     // [nnz_l] values on mesh l's pattern
+  DBuf<double> da, dm;   // [n_l] diagonals
+};
+
+struct Level {
+  int refinement = 0;
+  int n_colours = 0;
+  DBuf<int> colour;        // [n]
+  DBuf<int> colour_ptr;    // [n_colours+1]
+  DBuf<int> colour_rows;   // [n] rows grouped by colour, ascending within a colour
+  std::vector<int> colour_ptr_host;
+};
+
+}  // namespace bmg
+
+// Opaque handle.
+struct bmg_problem {
+  cudaStream_t stream = nullptr;
+  int R = 0;                        // finest refinement
+  double amplitude = 0.0;
+  std::vector<bmg::Mesh> mesh;      // refinements 0..R
+  int L = 0;                        // hierarchy levels (0 until bmg_hierarchy)
+  int r0 = 0;                       // refinement of level 1
+  std::vector<bmg::Level> lev;      // index 1..L
+  // ops[f][j]: operator set of finest level f on level j (j <= f); ops[f][f] aliases
+  // the assembled matrices through pointers below.
+  std::vector<std::vector<bmg::OpSet>> ops;
+  std::vector<double> norm1;        // ||A_f||_1 per level (host)
+  std::vector<std::vector<double>> coarseA, coarseM;   // [f] dense 42x42-type blocks (host copy)
+  bmg::Mesh& meshOf(int level) { return mesh[r0 + level - 1]; }
+  const bmg::Mesh& meshOf(int level) const { return mesh[r0 + level - 1]; }
+  const double* opA(int f, int j) const {
+    return f == j ? meshOf(j).valA.get() : ops[f][j].a.get();
+  }
+  const double* opM(int f, int j) const {
+    return f == j ? meshOf(j).valM.get() : ops[f][j].m.get();
+  }
+  const double* opDA(int f, int j) const { return ops[f][j].da.get(); }
+  const double* opDM(int f, int j) const { return ops[f][j].dm.get(); }
+};
+
+namespace bmg {
+// set-up (setup.cu)
+void exclusive_scan(const int* in, int* out, int n, int* total_host, cudaStream_t s);
+void build_mesh_pattern(Mesh& m, cudaStream_t s);
+void refine_mesh(const Mesh& c, Mesh& f, double amplitude, const double* sh_consts_dev,
+                 const double* coefs_dev, cudaStream_t s);
+void assemble_p1(Mesh& m, cudaStream_t s);
+void colour_level(const Mesh& m, Level& lv, cudaStream_t s);
+void galerkin(const Mesh& fine, const Mesh& coarse, const double* fa, const double* fm,
+              double* ca, double* cm, cudaStream_t s);
+void extract_diag(const Mesh& m, const double* a, const double* mm, double* da, double* dm,
+                  cudaStream_t s);
+void fill_sh_constants(double* c17);
+void project_input(Mesh& m, double amplitude, const double* sh_consts_dev,
+                   const double* coefs_dev, cudaStream_t s);
+
+// cycle steps (ops.cu)
+void spmm_am(const Mesh& m, const double* a, const double* mm, const double* X, int ld,
+             double* AX, double* MX, cudaStream_t s);
+void jacobi_sweep(const Mesh& m, const double* a, const double* mm, const double* da,
+                  const double* dm, const double* X, double* Xout, const double* B,
+                  const double* shift, int ld, double omega, cudaStream_t s);
+void gs_colour_sweep(const Mesh& m, const Level& lv, int colour, const double* a,
+                     const double* mm, const double* da, const double* dm, double* X,
+                     const double* B, const double* shift, int ld, cudaStream_t s);
+void residual(const Mesh& m, const double* a, const double* mm, const double* X,
+              const double* B, const double* shift, int ld, double* R, cudaStream_t s);
+void prolong(const Mesh& fine, const double* Xc, double* Y, int ld, bool add, cudaStream_t s);
+void restrict_(const Mesh& coarse, const double* R, double* Zc, int ld, cudaStream_t s);
+void gram(const double* X, const double* Y, int n, int k, int ld, double* G, double* partial,
+          int nparts, cudaStream_t s);
+int gram_parts(int n);
+void eig_residuals(const double* AU, const double* MU, const double* U, const double* lam, int n,
+                   int k, int ld, double* partial, int nparts, double* out, cudaStream_t s);
+void expand(const double* Zf, const double* X, const double* Yx, int n, int k, int ld,
+            int ldy, double* U, cudaStream_t s);
+void scale_rhs(const double* MU, const double* theta, int n, int k, int ld, double* B,
+               cudaStream_t s);
+void axpy_block(double* Y, const double* X, int n, int ld, cudaStream_t s);
+
+// dense (dense.cu)
+void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k,
+               double* theta, double* Y, int* rank, double* work, cudaStream_t s);
+size_t dense_work_doubles(int n);
+}  // namespace bmg

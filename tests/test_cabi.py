@@ -1,0 +1,46 @@
+"""Host-side checks of the C-ABI library: it loads, exports every declared symbol,
+and validates arguments before touching the GPU."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import __graft_entry__  # noqa: F401  (build helper)
+
+
+@pytest.fixture(scope="module")
+def bmg():
+    __graft_entry__.build_library()
+    from paper_1511_07042_gb300 import bmg as b
+    return b
+
+
+def test_every_declared_symbol_is_exported(bmg):
+    names = bmg.header_symbols()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(bmg.LIB, n)]
+    assert not missing, missing
+
+
+def test_default_options(bmg):
+    o = bmg.options()
+    assert (o.smoother, o.nu, o.form, o.cycles_intermediate, o.max_cycles) == (0, 2, 0, 6, 200)
+    assert abs(o.omega - 2.0 / 3.0) < 1e-16
+
+
+def test_argument_errors_are_reported_without_gpu(bmg):
+    h = C.c_void_p()
+    code = bmg.LIB.bmg_assemble(None, 12, None, 20, 2, 0.0, None, None, C.byref(h))
+    assert code == 1 and h.value is None
+    assert b"null mesh" in bmg.LIB.bmg_last_error() or b"empty" in bmg.LIB.bmg_last_error()
+    v = np.zeros((12, 3)); t = np.zeros((20, 3), np.int32)
+    code = bmg.LIB.bmg_assemble(v.ctypes.data, 12, t.ctypes.data, 20, 11, 0.0, None, None, C.byref(h))
+    assert code == 1
+    t[0, 0] = 99
+    code = bmg.LIB.bmg_assemble(v.ctypes.data, 12, t.ctypes.data, 20, 1, 0.0, None, None, C.byref(h))
+    assert code == 7                                  # BMG_ERR_MESH
+    assert bmg.LIB.bmg_hierarchy(None, 2) == 1
+    assert bmg.LIB.bmg_solve(None, 4, 2, 0.0, 1e-8, None, None, 0, None, None, 0, None, None) == 1
+    assert bmg.LIB.bmg_dense_eig(None, None, 4, 0.0, 2, None, None, None, None) == 1
+    assert bmg.LIB.bmg_gram(None, None, 4, 2, 2, None, None) == 1
+    bmg.LIB.bmg_destroy(None)

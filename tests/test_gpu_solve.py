@@ -1,0 +1,95 @@
+"""End-to-end GPU BFMG solves against the FP64 oracle and dense LAPACK solves."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import bmg as obmg, certify
+from paper_1511_07042_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def solve(bmg, R, k, nw, sigma, tol, amp=0.0, seed=None, x0seed=1001, colour=False, **kw):
+    v, t = inputs.icosahedron()
+    coefs = None if seed is None else inputs.sh_coefficients(seed)
+    prob = bmg.Problem(v, t, R, amp, coefs)
+    prob.hierarchy(R)
+    X0 = inputs.gaussian_block(inputs.n_vertices(2), k, x0seed)
+    ev, U, rs, info = prob.solve(X0, k, nw, sigma, tol, bmg.options(**kw))
+    H = obmg.build_hierarchy(v, t, R, amp, coefs, colour=colour)
+    return ev, U, rs, info, H
+
+
+@pytest.mark.parametrize("kw", [dict(smoother="jacobi", nu=2, omega=2 / 3),
+                                dict(smoother="jacobi", nu=2, omega=2 / 3, form="homogeneous"),
+                                dict(smoother="mcsgs", nu=1, omega=1.0),
+                                dict(smoother="mcgs", nu=2, omega=1.0, form="homogeneous")])
+def test_sphere642_k20_matches_dense(gpu_bmg, kw):
+    ev, U, rs, info, H = solve(gpu_bmg, 3, 20, 16, 0.0, 1e-10, **kw)
+    assert info.converged == 1
+    A, M = H.A[3], H.M[3]
+    w, V = certify.dense_pencil_eigs(A, M)
+    err, ang = certify.compare_to_reference(M, ev, U, w[:16], V[:, :16])
+    assert err.max() <= 1e-10 and ang.max() <= 1e-8
+    # residual recomputed on the host from the oracle's matrices
+    r = obmg.residuals(A, M, U, ev)
+    assert np.all(r <= 1e-9) and np.allclose(r, rs, rtol=1e-3, atol=1e-15)
+    assert np.allclose(U.T @ (M @ U), np.eye(16), atol=1e-10)
+
+
+def test_bumpy_interior_cluster_matches_dense(gpu_bmg):
+    ev, U, rs, info, H = solve(gpu_bmg, 3, 24, 9, 20.0, 1e-10, amp=0.1, seed=1003, x0seed=1013)
+    assert info.converged == 1
+    A, M = H.A[3], H.M[3]
+    w, V = certify.dense_pencil_eigs(A, M)
+    wr, Vr = certify.nearest(w, V, 20.0, 9)
+    err, ang = certify.compare_to_reference(M, ev, U, wr, Vr)
+    assert err.max() <= 1e-10 and ang.max() <= 1e-8
+
+
+def test_ragged_block_and_no_guard(gpu_bmg):
+    ev, U, rs, info, H = solve(gpu_bmg, 3, 17, 16, 0.0, 1e-10, smoother="jacobi")
+    assert info.converged == 1
+    w = certify.dense_pencil_eigs(H.A[3], H.M[3])[0]
+    assert np.max(np.abs(np.sort(ev) - w[:16]) / np.maximum(w[:16], 1)) <= 1e-10
+
+
+def test_sphere40962_k64_full_size(gpu_bmg):
+    """Full 6-level workload with multicolour SGS: eigenvalues against the oracle's
+    own BFMG run, residuals recomputed on the host, M-orthonormality, and Sylvester
+    inertia proving no eigenvalue below the wanted ones was missed."""
+    ev, U, rs, info, H = solve(gpu_bmg, 6, 64, 49, 0.0, 1e-10, colour=True, smoother="mcsgs", nu=1,
+                              omega=1.0)
+    assert info.converged == 1
+    A, M = H.A[6], H.M[6]
+    r = obmg.residuals(A, M, U, ev)
+    assert np.all(r <= 1e-9)
+    assert np.allclose(U.T @ (M @ U), np.eye(49), atol=1e-9)
+    lam = np.sort(ev)
+    cut = 0.5 * (lam[-1] + 56.0)           # between l=6 (42) and l=7 (56) clusters
+    assert certify.inertia_below(A, M, cut) == 49
+    gold = [(0, 0, 1), (1, 2, 3), (2, 6, 5), (3, 12, 7), (4, 20, 9), (5, 30, 11), (6, 42, 13)]
+    i = 0
+    for l, lv, mult in gold:
+        assert np.all(np.abs(lam[i:i + mult] - lv) < 0.01 * max(lv, 1)), l
+        i += mult
+    # the oracle's BFMG on the same input converges to the same pairs
+    X0 = inputs.gaussian_block(inputs.n_vertices(2), 64, 1001)
+    ref = obmg.bfmg(H, X0, 64, 49, 0.0, 1e-10, obmg.Options(smoother="mcsgs", nu=1, omega=1.0))
+    assert np.max(np.abs(lam - np.sort(ref.lam[:49])) / np.maximum(np.abs(lam), 1)) <= 1e-10
+
+
+def test_invalid_arguments_and_nonfinite(gpu_bmg):
+    v, t = inputs.icosahedron()
+    prob = gpu_bmg.Problem(v, t, 3)
+    X0 = inputs.gaussian_block(162, 20, 1)
+    with pytest.raises(gpu_bmg.BmgError) as e:
+        prob.solve(X0, 20, 16, 0.0, 1e-10)          # hierarchy missing
+    assert e.value.code == 8
+    prob.hierarchy(3)
+    with pytest.raises(gpu_bmg.BmgError):
+        prob.solve(X0, 200, 16, 0.0, 1e-10)         # k > N_2
+    X0[5, 3] = np.nan
+    with pytest.raises(gpu_bmg.BmgError) as e:
+        prob.solve(X0, 20, 16, 0.0, 1e-10)
+    assert e.value.code in (4, 6)                   # singular or non-finite, never a silent answer
