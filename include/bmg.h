@@ -205,6 +205,22 @@ bmg_status bmg_gram(const double* X, const double* Y, int n, int k, int ld, doub
 bmg_status bmg_dense_eig(const double* Ahat, const double* Mhat, int n, double sigma,
                          int k, double* theta, double* Y, int* rank_out, void* stream);
 
+/* ------------------------------------------------------------ measurement --- */
+/* Kernel-class timing for benchmarks (no counterpart in the paper).  When enabled,
+ * the launches of each class made by any call are bracketed by CUDA events on the
+ * stream that runs them; bmg_profile_read waits for them and returns the summed
+ * device time, the launch count and the algorithmic bytes and flops those launches
+ * had to move / execute (formulas in the library source).  Classes:
+ * 0 spmm_am, 1 smooth_sweep, 2 residual, 3 transfer, 4 gram, 5 dense_eig, 6 expand,
+ * 7 small.  Process-wide state; not thread-safe.                                 */
+bmg_status bmg_profile_enable(int enable);
+bmg_status bmg_profile_reset(void);
+bmg_status bmg_profile_read(int cls, double* total_ms, long long* launches, double* bytes,
+                            double* flops);
+const char* bmg_kernel_class_name(int cls);
+/* Number of kernels libbmg has launched in this process.                         */
+long long bmg_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,11 @@ def _load():
         "bmg_restrict": (i, [vp, i, vp, vp, i, i, vp]),
         "bmg_gram": (i, [vp, vp, i, i, i, vp, vp]),
         "bmg_dense_eig": (i, [vp, vp, i, d, i, vp, vp, vp, vp]),
+        "bmg_profile_enable": (i, [i]),
+        "bmg_profile_reset": (i, []),
+        "bmg_profile_read": (i, [i, P(C.c_double), P(C.c_longlong), P(C.c_double), P(C.c_double)]),
+        "bmg_kernel_class_name": (C.c_char_p, [i]),
+        "bmg_launch_count": (C.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -199,6 +204,12 @@ class Problem:
     def restrict(self, level, R, Zc, k):
         _check(LIB.bmg_restrict(self.h, level, _ptr(R), _ptr(Zc), k, R.shape[1], _stream()))
 
+    def solve_host(self, X0_host, U_host, k, n_wanted, sigma, tol, opt=None):
+        """BFMG solve with host buffers (e.g. pinned torch CPU tensors): X0 [N_2, k] in,
+        eigenvectors [N_L, n_wanted] out; copies happen inside the call."""
+        ev, rs, info = _solve_raw(self.h, _ptr(X0_host), 0, _ptr(U_host), 0, k, n_wanted, sigma, tol, opt)
+        return ev, U_host, rs, info
+
     def solve(self, X0, k, n_wanted, sigma, tol, opt=None, evecs=True, evecs_device=None):
         """BFMG solve.  X0: numpy [N_2, k] (host) or torch CUDA tensor (device).
 
@@ -223,6 +234,44 @@ class Problem:
         if code not in (0, 5):
             _check(code)
         return ev, U, rs, info
+
+
+KERNEL_CLASSES = 8
+
+
+def profile_enable(on=True):
+    _check(LIB.bmg_profile_enable(int(bool(on))))
+
+
+def profile_reset():
+    _check(LIB.bmg_profile_reset())
+
+
+def profile_read():
+    """{class name: dict(ms, launches, bytes, flops)} summed since the last reset."""
+    out = {}
+    for c in range(KERNEL_CLASSES):
+        ms, n, b, f = C.c_double(), C.c_longlong(), C.c_double(), C.c_double()
+        _check(LIB.bmg_profile_read(c, C.byref(ms), C.byref(n), C.byref(b), C.byref(f)))
+        out[LIB.bmg_kernel_class_name(c).decode()] = dict(ms=ms.value, launches=n.value,
+                                                          bytes=b.value, flops=f.value)
+    return out
+
+
+def launch_count():
+    return int(LIB.bmg_launch_count())
+
+
+def _solve_raw(h, X0_ptr, x0_dev, U_ptr, u_dev, k, n_wanted, sigma, tol, opt):
+    ev = np.empty(n_wanted)
+    rs = np.empty(n_wanted)
+    info = SolveInfo()
+    o = opt if opt is not None else options()
+    code = LIB.bmg_solve(h, k, n_wanted, float(sigma), float(tol), C.byref(o), X0_ptr, x0_dev,
+                         _ptr(ev), U_ptr, u_dev, _ptr(rs), C.byref(info))
+    if code not in (0, 5):
+        _check(code)
+    return ev, rs, info
 
 
 def gram(X, Y, k, G):

@@ -42,6 +42,7 @@ void check_cuda(cudaError_t e, const char* what) {
 }
 
 void check_launch(const char* what) {
+  count_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) fail(BMG_ERR_CUDA, std::string("launch of ") + what + ": " + cudaGetErrorString(e));
 }
@@ -222,8 +223,6 @@ extern "C" bmg_status bmg_hierarchy(bmg_problem* p, int levels) {
     p->ops.clear();
     p->ops.resize(L + 1);
     p->norm1.assign(L + 1, 0.0);
-    p->coarseA.assign(L + 1, {});
-    p->coarseM.assign(L + 1, {});
     DBuf<unsigned long long> um(1);
     for (int f = 2; f <= L; ++f) {
       p->ops[f].resize(f + 1);
@@ -397,7 +396,8 @@ extern "C" bmg_status bmg_dense_eig(const double* Ahat, const double* Mhat, int 
     if (n < 1 || n > 320 || k < 1 || k > n) fail(BMG_ERR_INVALID_ARG, "need 1 <= k <= n <= 320");
     DBuf<double> work(dense_work_doubles(n));
     DBuf<int> rk(1);
-    dense_eig(Ahat, Mhat, n, sigma, k, theta, Y, rank_out ? rank_out : rk.get(), work.get(), (cudaStream_t)stream);
+    dense_eig(Ahat, Mhat, n, sigma, k, theta, Y, rank_out ? rank_out : rk.get(), work.get(), nullptr,
+              (cudaStream_t)stream);
     BMG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   });
 }
@@ -405,32 +405,111 @@ extern "C" bmg_status bmg_dense_eig(const double* Ahat, const double* Mhat, int 
 // ------------------------------------------------------------------- solve ----
 namespace {
 
-struct SolveWork {
-  int ld = 0, k = 0, n1 = 0, nh = 0, L = 0, parts = 0;
-  DBuf<double> X, AX, MX, U, AU, MU, B, W, Zf;
-  std::vector<DBuf<double>> cA, cB, cC, cD;  // per coarse level j < L: [N_j][ld]
-  DBuf<double> Ahat, Mhat, Y, theta, lam, shift, GA, GM, dense, partial, res;
-  DBuf<int> rank;
-  std::vector<DBuf<double>> AQ, MQ;        // per f: dense n1 x n1 coarse blocks
-};
-
-void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, double* X,
-                  const double* B, const double* shift, int ld, double* work, cudaStream_t s) {
+// nu sweeps of the configured smoother on level j (operators of finest level f),
+// from Xin into Xout (Xin may equal Xout).  Jacobi alternates between Xout and work
+// so that the last sweep lands in Xout; Gauss-Seidel runs in place on Xout.
+void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, const double* Xin,
+                  double* Xout, const double* B, const double* shift, int ld, double* work,
+                  cudaStream_t s) {
   const Mesh& m = p->meshOf(j);
   const double *a = p->opA(f, j), *mm = p->opM(f, j), *da = p->opDA(f, j), *dm = p->opDM(f, j);
+  const size_t bytes = sizeof(double) * (size_t)m.n * ld;
   if (o.smoother == BMG_SMOOTH_JACOBI) {
-    for (int it = 0; it < o.nu; ++it) {
-      jacobi_sweep(m, a, mm, da, dm, X, work, B, shift, ld, o.omega, s);
-      BMG_CUDA(cudaMemcpyAsync(X, work, sizeof(double) * (size_t)m.n * ld, cudaMemcpyDeviceToDevice, s));
+    const double* src = Xin;
+    if (Xin == Xout && (o.nu % 2 == 1)) {
+      BMG_CUDA(cudaMemcpyAsync(work, Xin, bytes, cudaMemcpyDeviceToDevice, s));
+      src = work;
+      for (int it = 0; it < o.nu; ++it) {
+        double* dst = (it % 2 == 0) ? Xout : work;
+        jacobi_sweep(m, a, mm, da, dm, src, dst, B, shift, ld, o.omega, s);
+        src = dst;
+      }
+      return;
     }
-  } else {
-    const Level& lv = p->lev[j];
     for (int it = 0; it < o.nu; ++it) {
-      for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep(m, lv, c, a, mm, da, dm, X, B, shift, ld, s);
-      if (o.smoother == BMG_SMOOTH_MCSGS)
-        for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep(m, lv, c, a, mm, da, dm, X, B, shift, ld, s);
+      double* dst = ((o.nu - 1 - it) % 2 == 0) ? Xout : work;
+      jacobi_sweep(m, a, mm, da, dm, src, dst, B, shift, ld, o.omega, s);
+      src = dst;
+    }
+    return;
+  }
+  if (Xin != Xout) BMG_CUDA(cudaMemcpyAsync(Xout, Xin, bytes, cudaMemcpyDeviceToDevice, s));
+  const Level& lv = p->lev[j];
+  for (int it = 0; it < o.nu; ++it) {
+    for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s);
+    if (o.smoother == BMG_SMOOTH_MCSGS)
+      for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s);
+  }
+}
+
+// Allocates (or reuses) the solve workspace for block size k.
+SolveWork& workspace(bmg_problem* p, int k) {
+  if (p->ws && p->ws->k == k) return *p->ws;
+  p->ws.reset();
+  cudaStream_t s = p->stream;
+  const int L = p->L;
+  const int n1 = p->meshOf(1).n, nL = p->meshOf(L).n;
+  std::unique_ptr<SolveWork> wp(new SolveWork());
+  SolveWork& w = *wp;
+  w.k = k;
+  w.ld = (k + 1) & ~1;
+  w.n1 = n1;
+  w.nh = n1 + k;
+  w.L = L;
+  const int ld = w.ld;
+  const size_t big = (size_t)nL * ld;
+  for (DBuf<double>* b : {&w.X, &w.AX, &w.MX, &w.U, &w.AU, &w.MU, &w.B, &w.W, &w.Zf}) {
+    b->alloc(big);
+    BMG_CUDA(cudaMemsetAsync(b->get(), 0, sizeof(double) * big, s));
+  }
+  w.cA.resize(L); w.cB.resize(L); w.cC.resize(L); w.cD.resize(L);
+  for (int j = 1; j < L; ++j) {
+    const size_t sz = (size_t)p->meshOf(j).n * ld;
+    for (auto* v : {&w.cA, &w.cB, &w.cC, &w.cD}) {
+      (*v)[j].alloc(sz);
+      BMG_CUDA(cudaMemsetAsync((*v)[j].get(), 0, sizeof(double) * sz, s));
     }
   }
+  w.Ahat.alloc((size_t)w.nh * w.nh);
+  w.Mhat.alloc((size_t)w.nh * w.nh);
+  w.Y.alloc((size_t)w.nh * k);
+  w.theta.alloc(k);
+  w.lam.alloc(ld);
+  w.shift.alloc(ld);
+  w.GA.alloc((size_t)k * k);
+  w.GM.alloc((size_t)k * k);
+  w.dense.alloc(dense_work_doubles(w.nh));
+  w.parts = gram_parts(nL);
+  w.partial.alloc((size_t)w.parts * std::max(k * k, 2 * k));
+  w.res.alloc(2 * k);
+  w.rank.alloc(1);
+  w.dstats.alloc(2);
+  BMG_CUDA(cudaMallocHost(&w.hbuf, sizeof(double) * (3 * (size_t)k + 8)));
+  w.AQ.resize(L + 1);
+  w.MQ.resize(L + 1);
+  const Mesh& m1 = p->meshOf(1);
+  for (int f = 2; f <= L; ++f) {
+    w.AQ[f].alloc((size_t)n1 * n1);
+    w.MQ[f].alloc((size_t)n1 * n1);
+    csr_to_dense_kernel<<<grid_of(n1, 64), 64, 0, s>>>(m1.row_ptr.get(), m1.col.get(), p->opA(f, 1), n1, w.AQ[f].get());
+    csr_to_dense_kernel<<<grid_of(n1, 64), 64, 0, s>>>(m1.row_ptr.get(), m1.col.get(), p->opM(f, 1), n1, w.MQ[f].get());
+    check_launch("csr_to_dense_kernel");
+  }
+  // max over rows of dM/dA per (f, j): admissible depth of the down-leg
+  w.ratio.assign(L + 1, std::vector<double>(L + 1, 0.0));
+  DBuf<unsigned long long> um(1);
+  for (int f = 2; f <= L; ++f)
+    for (int j = 1; j < f; ++j) {
+      BMG_CUDA(cudaMemsetAsync(um.get(), 0, sizeof(unsigned long long), s));
+      ratio_max_kernel<<<grid_of(p->meshOf(j).n, 256), 256, 0, s>>>(p->opDA(f, j), p->opDM(f, j), p->meshOf(j).n, um.get());
+      check_launch("ratio_max_kernel");
+      unsigned long long h = 0;
+      BMG_CUDA(cudaMemcpyAsync(&h, um.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
+      BMG_CUDA(cudaStreamSynchronize(s));
+      std::memcpy(&w.ratio[f][j], &h, sizeof(double));
+    }
+  p->ws = std::move(wp);
+  return *p->ws;
 }
 
 }  // namespace
@@ -453,71 +532,20 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
     if (!X0 || !evals) fail(BMG_ERR_INVALID_ARG, "X0 and evals are required");
     if (!(tol > 0.0) || !std::isfinite(sigma)) fail(BMG_ERR_INVALID_ARG, "bad tol or sigma");
     if (o.nu < 1 || o.nu > 64 || o.smoother < 0 || o.smoother > 2 || o.form < 0 || o.form > 1 ||
-        o.max_cycles < 1 || o.cycles_intermediate < 1)
+        o.max_cycles < 1 || o.cycles_intermediate < 1 || !(o.omega > 0.0))
       fail(BMG_ERR_INVALID_ARG, "bad options");
     cudaStream_t s = p->stream;
-    SolveWork w;
-    w.k = k;
-    w.ld = (k + 1) & ~1;
-    w.n1 = n1;
-    w.nh = n1 + k;
-    w.L = L;
+    SolveWork& w = workspace(p, k);
     const int ld = w.ld;
-    const size_t big = (size_t)nL * ld;
-    for (DBuf<double>* b : {&w.X, &w.AX, &w.MX, &w.U, &w.AU, &w.MU, &w.B, &w.W, &w.Zf}) {
-      b->alloc(big);
-      BMG_CUDA(cudaMemsetAsync(b->get(), 0, sizeof(double) * big, s));
-    }
-    w.cA.resize(L); w.cB.resize(L); w.cC.resize(L); w.cD.resize(L);
-    for (int j = 1; j < L; ++j) {
-      const size_t sz = (size_t)p->meshOf(j).n * ld;
-      for (auto* v : {&w.cA, &w.cB, &w.cC, &w.cD}) {
-        (*v)[j].alloc(sz);
-        BMG_CUDA(cudaMemsetAsync((*v)[j].get(), 0, sizeof(double) * sz, s));
-      }
-    }
-    w.Ahat.alloc((size_t)w.nh * w.nh);
-    w.Mhat.alloc((size_t)w.nh * w.nh);
-    w.Y.alloc((size_t)w.nh * k);
-    w.theta.alloc(k);
-    w.lam.alloc(ld);
-    w.shift.alloc(ld);
-    w.GA.alloc((size_t)k * k);
-    w.GM.alloc((size_t)k * k);
-    w.dense.alloc(dense_work_doubles(w.nh));
-    w.parts = gram_parts(nL);
-    w.partial.alloc((size_t)w.parts * std::max(k * k, 2 * k));
-    w.res.alloc(2 * k);
-    w.rank.alloc(1);
-    w.AQ.resize(L + 1);
-    w.MQ.resize(L + 1);
-    for (int f = 2; f <= L; ++f) {
-      w.AQ[f].alloc((size_t)n1 * n1);
-      w.MQ[f].alloc((size_t)n1 * n1);
-      const Mesh& m1 = p->meshOf(1);
-      csr_to_dense_kernel<<<grid_of(n1, 64), 64, 0, s>>>(m1.row_ptr.get(), m1.col.get(), p->opA(f, 1), n1, w.AQ[f].get());
-      csr_to_dense_kernel<<<grid_of(n1, 64), 64, 0, s>>>(m1.row_ptr.get(), m1.col.get(), p->opM(f, 1), n1, w.MQ[f].get());
-      check_launch("csr_to_dense_kernel");
-    }
-    // max over rows of dM/dA per (f, j), for the admissible depth of the down-leg
-    std::vector<std::vector<double>> ratio(L + 1, std::vector<double>(L + 1, 0.0));
-    {
-      DBuf<unsigned long long> um(1);
-      for (int f = 2; f <= L; ++f)
-        for (int j = 1; j < f; ++j) {
-          BMG_CUDA(cudaMemsetAsync(um.get(), 0, sizeof(unsigned long long), s));
-          ratio_max_kernel<<<grid_of(p->meshOf(j).n, 256), 256, 0, s>>>(p->opDA(f, j), p->opDM(f, j), p->meshOf(j).n, um.get());
-          unsigned long long h = 0;
-          BMG_CUDA(cudaMemcpyAsync(&h, um.get(), sizeof(h), cudaMemcpyDeviceToHost, s));
-          BMG_CUDA(cudaStreamSynchronize(s));
-          std::memcpy(&ratio[f][j], &h, sizeof(double));
-        }
-    }
-    // X0 -> X on level 2 (ld-strided)
+    double* hres = w.hbuf;            // 2k residual sums
+    double* hlam = w.hbuf + 2 * k;    // k Ritz values
+    int* hint = reinterpret_cast<int*>(w.hbuf + 3 * k);  // rank, sweeps, rotations
+    // X0 -> X on level 2 (ld-strided; padding columns stay zero)
+    BMG_CUDA(cudaMemsetAsync(w.X.get(), 0, sizeof(double) * (size_t)n2 * ld, s));
     BMG_CUDA(cudaMemcpy2DAsync(w.X.get(), sizeof(double) * ld, X0, sizeof(double) * k, sizeof(double) * k, n2,
                                x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
 
-    std::vector<double> hres(2 * k), htheta(k), hlam(k), rho(k);
+    std::vector<double> rho(k, 0.0), lamv(k, 0.0);
     int total_cycles = 0;
     bool converged = false;
     std::vector<int> cyc(L + 1, 0);
@@ -528,7 +556,7 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
       const int budget = (f == L) ? o.max_cycles : o.cycles_intermediate;
       const double ftol = (f == L) ? tol : o.tol_intermediate;
       for (int c = 0; c < budget; ++c) {
-        // 1-2: products, Grams, couplings
+        // 1-2: products, Grams, couplings Q^T AX, Q^T MX by the restriction chain
         spmm_am(mf, mf.valA.get(), mf.valM.get(), w.X.get(), ld, w.AX.get(), w.MX.get(), s);
         gram(w.X.get(), w.AX.get(), nf, k, ld, w.GA.get(), w.partial.get(), gram_parts(nf), s);
         gram(w.X.get(), w.MX.get(), nf, k, ld, w.GM.get(), w.partial.get(), gram_parts(nf), s);
@@ -541,16 +569,22 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
           cm = w.cB[j - 1].get();
         }
         const int nh = w.nh;
+        prof_begin(KC_SMALL, s);
         assemble_hat_kernel<<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.AQ[f].get(), ca, w.GA.get(), n1, k, ld, w.Ahat.get());
+        check_launch("assemble_hat_kernel");
         assemble_hat_kernel<<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.MQ[f].get(), cm, w.GM.get(), n1, k, ld, w.Mhat.get());
         check_launch("assemble_hat_kernel");
+        prof_end(KC_SMALL, s, 32.0 * nh * nh, 0.0);
         // 3: enriched eigensolve
-        dense_eig(w.Ahat.get(), w.Mhat.get(), nh, sigma, k, w.theta.get(), w.Y.get(), w.rank.get(), w.dense.get(), s);
+        dense_eig(w.Ahat.get(), w.Mhat.get(), nh, sigma, k, w.theta.get(), w.Y.get(), w.rank.get(), w.dense.get(),
+                  w.dstats.get(), s);
+        prof_begin(KC_SMALL, s);
         shifts_kernel<<<grid_of(ld, 128), 128, 0, s>>>(w.theta.get(), k, ld, sigma, o.form, w.lam.get(), w.shift.get());
         check_launch("shifts_kernel");
         // 4: Ritz vectors U = Q Y_c + X Y_x
         pack_coarse_kernel<<<grid_of((size_t)n1 * ld, 256), 256, 0, s>>>(w.Y.get(), n1, k, ld, w.cC[1].get());
         check_launch("pack_coarse_kernel");
+        prof_end(KC_SMALL, s, 8.0 * n1 * ld, 0.0);
         const double* z = w.cC[1].get();
         for (int j = 2; j < f; ++j) {
           prolong(p->meshOf(j), z, w.cC[j].get(), ld, false, s);
@@ -560,16 +594,17 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
         expand(w.Zf.get(), w.X.get(), w.Y.get() + (size_t)n1 * k, nf, k, ld, k, w.U.get(), s);
         spmm_am(mf, mf.valA.get(), mf.valM.get(), w.U.get(), ld, w.AU.get(), w.MU.get(), s);
         eig_residuals(w.AU.get(), w.MU.get(), w.U.get(), w.lam.get(), nf, k, ld, w.partial.get(), gram_parts(nf), w.res.get(), s);
-        int hrank = 0;
-        BMG_CUDA(cudaMemcpyAsync(hres.data(), w.res.get(), sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
-        BMG_CUDA(cudaMemcpyAsync(hlam.data(), w.lam.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-        BMG_CUDA(cudaMemcpyAsync(&hrank, w.rank.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        BMG_CUDA(cudaMemcpyAsync(hres, w.res.get(), sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
+        BMG_CUDA(cudaMemcpyAsync(hlam, w.lam.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+        BMG_CUDA(cudaMemcpyAsync(hint, w.rank.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+        BMG_CUDA(cudaMemcpyAsync(hint + 1, w.dstats.get(), 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
         BMG_CUDA(cudaStreamSynchronize(s));
         ++total_cycles;
         cyc[f] = c + 1;
-        if (hrank < k) fail(BMG_ERR_SINGULAR, "enriched space rank " + std::to_string(hrank) + " < k");
+        if (hint[0] < k) fail(BMG_ERR_SINGULAR, "enriched space rank " + std::to_string(hint[0]) + " < k");
         bool conv = true, finite = true;
         for (int i = 0; i < k; ++i) {
+          lamv[i] = hlam[i];
           rho[i] = std::sqrt(hres[i]) / (p->norm1[f] * std::sqrt(hres[k + i]));
           if (!std::isfinite(rho[i]) || !std::isfinite(hlam[i])) finite = false;
           if (i < n_wanted && !(rho[i] <= ftol)) conv = false;
@@ -580,16 +615,17 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
         // 5: smoothing of the source problems from U, then the down-leg
         const double* Bp = nullptr;
         if (o.form == BMG_FORM_SHIFTED) {
+          prof_begin(KC_SMALL, s);
           scale_rhs(w.MU.get(), w.theta.get(), nf, k, ld, w.B.get(), s);
+          prof_end(KC_SMALL, s, 16.0 * nf * ld, 1.0 * nf * ld);
           Bp = w.B.get();
         }
-        BMG_CUDA(cudaMemcpyAsync(w.X.get(), w.U.get(), sizeof(double) * (size_t)nf * ld, cudaMemcpyDeviceToDevice, s));
-        smooth_level(p, f, f, o, w.X.get(), Bp, w.shift.get(), ld, w.W.get(), s);
+        smooth_level(p, f, f, o, w.U.get(), w.X.get(), Bp, w.shift.get(), ld, w.W.get(), s);
         double smax = (o.form == BMG_FORM_SHIFTED) ? sigma : -1e300;
-        if (o.form != BMG_FORM_SHIFTED) for (int i = 0; i < k; ++i) smax = std::max(smax, hlam[i]);
+        if (o.form != BMG_FORM_SHIFTED) for (int i = 0; i < k; ++i) smax = std::max(smax, lamv[i]);
         std::vector<int> legs;
         for (int j = f - 1; j >= 1 && (int)legs.size() < o.vcycle_depth; --j) {
-          if (!(smax * ratio[f][j] < 1.0 - 0.25)) break;
+          if (!(smax * w.ratio[f][j] < 1.0 - 0.25)) break;
           legs.push_back(j);
         }
         if (!legs.empty()) {
@@ -600,7 +636,7 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
             const Mesh& mj = p->meshOf(j);
             restrict_(mj, rprev, w.cA[j].get(), ld, s);
             BMG_CUDA(cudaMemsetAsync(w.cB[j].get(), 0, sizeof(double) * (size_t)mj.n * ld, s));
-            smooth_level(p, f, j, o, w.cB[j].get(), w.cA[j].get(), w.shift.get(), ld, w.cD[j].get(), s);
+            smooth_level(p, f, j, o, w.cB[j].get(), w.cB[j].get(), w.cA[j].get(), w.shift.get(), ld, w.cD[j].get(), s);
             if (t + 1 < legs.size()) {
               residual(mj, p->opA(f, j), p->opM(f, j), w.cB[j].get(), w.cA[j].get(), w.shift.get(), ld, w.cC[j].get(), s);
               rprev = w.cC[j].get();
@@ -615,14 +651,14 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
       }
     }
     // outputs: the last Ritz pairs on level L
-    for (int i = 0; i < n_wanted; ++i) evals[i] = hlam[i];
+    for (int i = 0; i < n_wanted; ++i) evals[i] = lamv[i];
     if (resid) for (int i = 0; i < n_wanted; ++i) resid[i] = rho[i];
     if (evecs) {
       BMG_CUDA(cudaMemcpy2DAsync(evecs, sizeof(double) * n_wanted, w.U.get(), sizeof(double) * ld,
                                  sizeof(double) * n_wanted, nL,
                                  evecs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-      BMG_CUDA(cudaStreamSynchronize(s));
     }
+    BMG_CUDA(cudaStreamSynchronize(s));
     if (info) {
       std::memset(info, 0, sizeof(*info));
       info->levels = L;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -91,8 +92,37 @@ struct Level {
   DBuf<int> colour_ptr;    // [n_colours+1]
   DBuf<int> colour_rows;   // [n] rows grouped by colour, ascending within a colour
   std::vector<int> colour_ptr_host;
+  std::vector<long long> colour_nnz_host;  // CSR nonzeros of the rows of each colour
 };
 
+}  // namespace bmg
+
+namespace bmg {
+// Kernel classes timed by the profiler (bmg_profile_*).
+enum KernelClass { KC_SPMM = 0, KC_SMOOTH, KC_RESID, KC_TRANSFER, KC_GRAM, KC_DENSE, KC_EXPAND,
+                   KC_SMALL, KC_COUNT };
+
+// Process-wide kernel profiler: when enabled, launches of each class are bracketed
+// by CUDA events on their stream; totals are folded in by prof_flush() once the
+// stream is idle.  Algorithmic bytes and flops per launch are accumulated with them.
+void prof_begin(int cls, cudaStream_t s);
+void prof_end(int cls, cudaStream_t s, double bytes, double flops);
+void prof_flush();
+long long launch_count();
+void count_launch();
+
+// Workspace of bmg_solve, kept in the problem between calls with the same k.
+struct SolveWork {
+  int ld = 0, k = 0, n1 = 0, nh = 0, L = 0, parts = 0;
+  DBuf<double> X, AX, MX, U, AU, MU, B, W, Zf;
+  std::vector<DBuf<double>> cA, cB, cC, cD;  // per coarse level j < L: [N_j][ld]
+  DBuf<double> Ahat, Mhat, Y, theta, lam, shift, GA, GM, dense, partial, res;
+  DBuf<int> rank, dstats;
+  std::vector<DBuf<double>> AQ, MQ;         // per f: dense n1 x n1 coarse blocks
+  std::vector<std::vector<double>> ratio;   // [f][j] max_i dM_i / dA_i
+  double* hbuf = nullptr;                   // pinned host staging (res, lam, rank, stats)
+  ~SolveWork() { if (hbuf) cudaFreeHost(hbuf); }
+};
 }  // namespace bmg
 
 // Opaque handle.
@@ -108,7 +138,7 @@ struct bmg_problem {
   // the assembled matrices through pointers below.
   std::vector<std::vector<bmg::OpSet>> ops;
   std::vector<double> norm1;        // ||A_f||_1 per level (host)
-  std::vector<std::vector<double>> coarseA, coarseM;   // [f] dense 42x42-type blocks (host copy)
+  std::unique_ptr<bmg::SolveWork> ws;  // cached solve workspace
   bmg::Mesh& meshOf(int level) { return mesh[r0 + level - 1]; }
   const bmg::Mesh& meshOf(int level) const { return mesh[r0 + level - 1]; }
   const double* opA(int f, int j) const {
@@ -163,6 +193,6 @@ void axpy_block(double* Y, const double* X, int n, int ld, cudaStream_t s);
 
 // dense (dense.cu)
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k,
-               double* theta, double* Y, int* rank, double* work, cudaStream_t s);
+               double* theta, double* Y, int* rank, double* work, int* stats, cudaStream_t s);
 size_t dense_work_doubles(int n);
 }  // namespace bmg

@@ -33,7 +33,7 @@ __device__ void block_sync() { __syncthreads(); }
 __global__ void __launch_bounds__(kThreads)
 dense_eig_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mhat, int n,
                  double sigma, int k, double* __restrict__ theta_out, double* __restrict__ Y,
-                 int* __restrict__ rank_out, Work w) {
+                 int* __restrict__ rank_out, int* __restrict__ stats, Work w) {
   __shared__ int perm[320];
   __shared__ double red_v[kThreads];
   __shared__ int red_i[kThreads];
@@ -42,7 +42,10 @@ dense_eig_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mha
   __shared__ double cs_c[160], cs_s[160];
   __shared__ int pr_p[160], pr_q[160];
   __shared__ int order[320];
+  __shared__ int s_sweeps;
+  __shared__ unsigned long long s_rot;
   const int tid = threadIdx.x;
+  if (tid == 0) { s_sweeps = 0; s_rot = 0ull; }
 
   // 1. scaling D = diag(Mhat)^(-1/2) and S = D Mhat D (symmetrised)
   for (int i = tid; i < n; i += kThreads) {
@@ -101,7 +104,10 @@ dense_eig_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mha
     block_sync();
   }
   const int r = s_rank;
-  if (tid == 0) *rank_out = r;
+  if (tid == 0) {
+    *rank_out = r;
+    if (stats) { stats[0] = 0; stats[1] = 0; }
+  }
   if (r < k) return;  // caller reports BMG_ERR_SINGULAR
 
   // 3. C = D (Ahat - sigma Mhat) D in pivot order, leading r x r block
@@ -167,6 +173,7 @@ dense_eig_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mha
     if (tid == 0) s_frob = red_v[0];
     block_sync();
     if (s_off <= 1e-32 * s_frob || s_frob == 0.0) break;
+    if (tid == 0) s_sweeps = sweep + 1;
     for (int step = 0; step < m - 1; ++step) {
       for (int i = tid; i < m / 2; i += kThreads) {
         auto player = [&](int t) { return t == 0 ? 0 : ((t - 1 + step) % (m - 1)) + 1; };
@@ -183,6 +190,7 @@ dense_eig_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mha
             else t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
             c = 1.0 / sqrt(1.0 + t * t);
             s = t * c;
+            atomicAdd(&s_rot, 1ull);
           }
         }
         cs_c[i] = c; cs_s[i] = s; pr_p[i] = p; pr_q[i] = (q < r) ? q : -1;
@@ -228,6 +236,7 @@ dense_eig_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mha
   }
   block_sync();
   for (int c = tid; c < k; c += kThreads) theta_out[c] = w.C[order[c] * r + order[c]];
+  if (tid == 0 && stats) { stats[0] = s_sweeps; stats[1] = (int)s_rot; }
   // 7. Y = D P L^{-T} V_sel  (back substitution, parallel over the k columns)
   for (int i = r - 1; i >= 0; --i) {
     const double lii = w.L[perm[i] * n + i];
@@ -249,7 +258,7 @@ dense_eig_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mha
 size_t dense_work_doubles(int n) { return 5 * (size_t)n * n + n; }
 
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k, double* theta,
-               double* Y, int* rank, double* work, cudaStream_t s) {
+               double* Y, int* rank, double* work, int* stats, cudaStream_t s) {
   if (n < 1 || n > 320 || k < 1 || k > n) fail(BMG_ERR_INVALID_ARG, "dense_eig: need 1 <= k <= n <= 320");
   Work w;
   w.S = work;
@@ -258,8 +267,12 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
   w.V = w.C + (size_t)n * n;
   w.Z = w.V + (size_t)n * n;
   w.d = w.Z + (size_t)n * n;
-  dense_eig_kernel<<<1, kThreads, 0, s>>>(Ahat, Mhat, n, sigma, k, theta, Y, rank, w);
+  prof_begin(KC_DENSE, s);
+  dense_eig_kernel<<<1, kThreads, 0, s>>>(Ahat, Mhat, n, sigma, k, theta, Y, rank, stats, w);
   check_launch("dense_eig_kernel");
+  // nominal count of a dense symmetric-definite eigensolve with vectors (9 n^3)
+  const double nn = n;
+  prof_end(KC_DENSE, s, 16.0 * nn * nn + 8.0 * nn * k, 9.0 * nn * nn * nn);
 }
 
 }  // namespace bmg

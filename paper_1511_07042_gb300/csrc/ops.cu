@@ -329,6 +329,7 @@ int cpl_for(int nch) { return nch <= 32 ? 1 : (nch <= 64 ? 2 : 4); }
 void spmm_am(const Mesh& m, const double* a, const double* mm, const double* X, int ld, double* AX,
              double* MX, cudaStream_t s) {
   const int nch = ld / 2;
+  prof_begin(KC_SPMM, s);
   const int grid = blocks_for(m.n, kWarpsPerBlock);
   switch (cpl_for(nch)) {
     case 1: spmm_am_kernel<1><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX); break;
@@ -336,55 +337,69 @@ void spmm_am(const Mesh& m, const double* a, const double* mm, const double* X, 
     default: spmm_am_kernel<4><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX); break;
   }
   check_launch("spmm_am_kernel");
+  prof_end(KC_SPMM, s, 20.0 * m.nnz + 4.0 * (m.n + 1) + 24.0 * m.n * ld, 4.0 * m.nnz * ld);
 }
 
 template <int MODE>
 static void row_update(const Mesh& m, const double* a, const double* mm, const double* da,
-                       const double* dm, const int* rows, int nrows, const double* X, double* Out,
-                       const double* B, const double* shift, int ld, double omega, cudaStream_t s) {
+                       const double* dm, const int* rows, int nrows, long long nnz_rows,
+                       const double* X, double* Out, const double* B, const double* shift, int ld,
+                       double omega, cudaStream_t s) {
   const int nch = ld / 2;
   const int grid = blocks_for(nrows, kWarpsPerBlock);
   if (nrows == 0) return;
+  const int cls = (MODE == 2) ? KC_RESID : KC_SMOOTH;
+  prof_begin(cls, s);
   switch (cpl_for(nch)) {
     case 1: row_update_kernel<1, MODE><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega); break;
     case 2: row_update_kernel<2, MODE><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega); break;
     default: row_update_kernel<4, MODE><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega); break;
   }
   check_launch("row_update_kernel");
+  // matrix rows, diagonals, own-row read + write, one share of the gathered block, B
+  const double bytes = 20.0 * nnz_rows + 24.0 * nrows + 8.0 * nrows * ld * (B ? 4.0 : 3.0);
+  prof_end(cls, s, bytes, 4.0 * nnz_rows * ld + 6.0 * nrows * ld);
 }
 
 void jacobi_sweep(const Mesh& m, const double* a, const double* mm, const double* da,
                   const double* dm, const double* X, double* Xout, const double* B,
                   const double* shift, int ld, double omega, cudaStream_t s) {
-  row_update<0>(m, a, mm, da, dm, nullptr, m.n, X, Xout, B, shift, ld, omega, s);
+  row_update<0>(m, a, mm, da, dm, nullptr, m.n, m.nnz, X, Xout, B, shift, ld, omega, s);
 }
 
 void gs_colour_sweep(const Mesh& m, const Level& lv, int c, const double* a, const double* mm,
                      const double* da, const double* dm, double* X, const double* B,
                      const double* shift, int ld, cudaStream_t s) {
   const int b = lv.colour_ptr_host[c], e = lv.colour_ptr_host[c + 1];
-  row_update<1>(m, a, mm, da, dm, lv.colour_rows.get() + b, e - b, X, X, B, shift, ld, 1.0, s);
+  row_update<1>(m, a, mm, da, dm, lv.colour_rows.get() + b, e - b, lv.colour_nnz_host[c], X, X, B,
+                shift, ld, 1.0, s);
 }
 
 void residual(const Mesh& m, const double* a, const double* mm, const double* X, const double* B,
               const double* shift, int ld, double* R, cudaStream_t s) {
   // the diagonal is not used in residual mode; pass the matrix values as placeholders
-  row_update<2>(m, a, mm, a, mm, nullptr, m.n, X, R, B, shift, ld, 0.0, s);
+  row_update<2>(m, a, mm, a, mm, nullptr, m.n, m.nnz, X, R, B, shift, ld, 0.0, s);
 }
 
 void prolong(const Mesh& fine, const double* Xc, double* Y, int ld, bool add, cudaStream_t s) {
   const int nch = ld / 2;
   const size_t total = (size_t)fine.n * nch;
+  prof_begin(KC_TRANSFER, s);
   prolong_kernel<<<blocks_for(total, 256), 256, 0, s>>>(fine.parents.get(), fine.n, Xc, Y, nch, add ? 1 : 0);
   check_launch("prolong_kernel");
+  const double nc = (fine.n + 6) / 4.0;  // vertices of the coarse level of a refined sphere
+  prof_end(KC_TRANSFER, s, 8.0 * fine.n + 8.0 * ld * (nc + fine.n * (add ? 2.0 : 1.0)), 1.0 * fine.n * ld);
 }
 
 void restrict_(const Mesh& coarse, const double* R, double* Zc, int ld, cudaStream_t s) {
   const int nch = ld / 2;
   const size_t total = (size_t)coarse.n * nch;
+  prof_begin(KC_TRANSFER, s);
   restrict_kernel<<<blocks_for(total, 256), 256, 0, s>>>(coarse.row_ptr.get(), coarse.col.get(), coarse.mid.get(),
                                                           coarse.n, R, Zc, nch);
   check_launch("restrict_kernel");
+  const double nf = 4.0 * coarse.n - 6.0;
+  prof_end(KC_TRANSFER, s, 8.0 * coarse.nnz + 8.0 * ld * (nf + coarse.n), 2.0 * nf * ld);
 }
 
 int gram_parts(int n) { return std::max(1, std::min(304, (n + 63) / 64)); }
@@ -395,6 +410,7 @@ void gram(const double* X, const double* Y, int n, int k, int ld, double* G, dou
   const int tk = (k + 3) / 4;
   const int ntiles = tk * tk;
   const size_t smem = 2 * kGramRows * ld * sizeof(double);
+  prof_begin(KC_GRAM, s);
   if (ntiles <= kGramThreads) gram_kernel<1><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial);
   else if (ntiles <= 2 * kGramThreads) gram_kernel<2><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial);
   else if (ntiles <= 4 * kGramThreads) gram_kernel<4><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial);
@@ -403,17 +419,20 @@ void gram(const double* X, const double* Y, int n, int k, int ld, double* G, dou
   check_launch("gram_kernel");
   gram_reduce_kernel<<<blocks_for(k * k, 256), 256, 0, s>>>(partial, nparts, k * k, G);
   check_launch("gram_reduce_kernel");
+  prof_end(KC_GRAM, s, 16.0 * n * ld + 16.0 * nparts * k * k + 8.0 * k * k, 2.0 * n * k * k);
 }
 
 void eig_residuals(const double* AU, const double* MU, const double* U, const double* lam, int n,
                    int k, int ld, double* partial, int nparts, double* out, cudaStream_t s) {
   const int rows_per_part = (n + nparts - 1) / nparts;
   const int threads = std::max(k, (256 / k) * k);
+  prof_begin(KC_SMALL, s);
   eigres_kernel<<<nparts, threads, 2 * threads * sizeof(double), s>>>(AU, MU, U, lam, n, k, ld,
                                                                       rows_per_part, partial);
   check_launch("eigres_kernel");
   gram_reduce_kernel<<<blocks_for(2 * k, 256), 256, 0, s>>>(partial, nparts, 2 * k, out);
   check_launch("gram_reduce_kernel");
+  prof_end(KC_SMALL, s, 24.0 * n * ld, 5.0 * n * k);
 }
 
 void expand(const double* Zf, const double* X, const double* Yx, int n, int k, int ld, int ldy,
@@ -421,6 +440,7 @@ void expand(const double* Zf, const double* X, const double* Yx, int n, int k, i
   const int nch = ld / 2;
   const size_t smem = (size_t)k * ld * sizeof(double);
   const int grid = std::max(1, std::min(blocks_for(n, kWarpsPerBlock), 4 * 152));
+  prof_begin(KC_EXPAND, s);
   switch (cpl_for(nch)) {
     case 1:
       cudaFuncSetAttribute(expand_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -433,6 +453,7 @@ void expand(const double* Zf, const double* X, const double* Yx, int n, int k, i
       expand_kernel<4><<<grid, kWarpsPerBlock * 32, smem, s>>>(Zf, X, Yx, n, k, ld, ldy, U); break;
   }
   check_launch("expand_kernel");
+  prof_end(KC_EXPAND, s, 24.0 * n * ld + 8.0 * k * k, 2.0 * n * k * k);
 }
 
 void scale_rhs(const double* MU, const double* theta, int n, int k, int ld, double* B, cudaStream_t s) {

@@ -8,6 +8,7 @@
 // closest point on the unit sphere), times r(n) on a star-shaped perturbed sphere.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "common.cuh"
 
@@ -544,7 +545,14 @@ void colour_level(const Mesh& m, Level& lv, cudaStream_t s) {
   lv.colour_ptr_host[lv.n_colours] = base;
   BMG_CUDA(cudaMemcpyAsync(lv.colour_ptr.get(), lv.colour_ptr_host.data(),
                            sizeof(int) * (lv.n_colours + 1), cudaMemcpyHostToDevice, s));
+  std::vector<int> hrp(n + 1), hrows(n);
+  BMG_CUDA(cudaMemcpyAsync(hrp.data(), m.row_ptr.get(), sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaMemcpyAsync(hrows.data(), lv.colour_rows.get(), sizeof(int) * n, cudaMemcpyDeviceToHost, s));
   BMG_CUDA(cudaStreamSynchronize(s));
+  lv.colour_nnz_host.assign(lv.n_colours, 0);
+  for (int c = 0; c < lv.n_colours; ++c)
+    for (int q = lv.colour_ptr_host[c]; q < lv.colour_ptr_host[c + 1]; ++q)
+      lv.colour_nnz_host[c] += hrp[hrows[q] + 1] - hrp[hrows[q]];
 }
 
 // ------------------------------------------------------------- Galerkin ----
