@@ -79,6 +79,7 @@ typedef struct {
   int total_cycles;
   int converged;             /* 1 if every wanted pair met tol                    */
   double max_resid;          /* largest wanted relative residual at exit          */
+  double max_dense_err;      /* largest error estimate of the enriched eigensolve */
 } bmg_solve_info;
 
 /* ---------------------------------------------------------------- set-up ----- */

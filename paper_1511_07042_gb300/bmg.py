@@ -38,7 +38,7 @@ class Options(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("levels", C.c_int), ("cycles", C.c_int * 32), ("total_cycles", C.c_int),
-                ("converged", C.c_int), ("max_resid", C.c_double)]
+                ("converged", C.c_int), ("max_resid", C.c_double), ("max_dense_err", C.c_double)]
 
 
 def _load():

@@ -483,8 +483,8 @@ SolveWork& workspace(bmg_problem* p, int k) {
   w.partial.alloc((size_t)w.parts * std::max(k * k, 2 * k));
   w.res.alloc(2 * k);
   w.rank.alloc(1);
-  w.dstats.alloc(2);
-  BMG_CUDA(cudaMallocHost(&w.hbuf, sizeof(double) * (3 * (size_t)k + 8)));
+  w.dquality.alloc(1);
+  BMG_CUDA(cudaMallocHost(&w.hbuf, sizeof(double) * (3 * (size_t)k + 8)));  // res, lam, quality, rank
   w.AQ.resize(L + 1);
   w.MQ.resize(L + 1);
   const Mesh& m1 = p->meshOf(1);
@@ -539,7 +539,8 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
     const int ld = w.ld;
     double* hres = w.hbuf;            // 2k residual sums
     double* hlam = w.hbuf + 2 * k;    // k Ritz values
-    int* hint = reinterpret_cast<int*>(w.hbuf + 3 * k);  // rank, sweeps, rotations
+    double* hqual = w.hbuf + 3 * k;   // error estimate of the enriched eigensolve
+    int* hint = reinterpret_cast<int*>(w.hbuf + 3 * k + 1);  // rank
     // X0 -> X on level 2 (ld-strided; padding columns stay zero)
     BMG_CUDA(cudaMemsetAsync(w.X.get(), 0, sizeof(double) * (size_t)n2 * ld, s));
     BMG_CUDA(cudaMemcpy2DAsync(w.X.get(), sizeof(double) * ld, X0, sizeof(double) * k, sizeof(double) * k, n2,
@@ -547,6 +548,7 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
 
     std::vector<double> rho(k, 0.0), lamv(k, 0.0);
     int total_cycles = 0;
+    double max_dense_err = 0.0;
     bool converged = false;
     std::vector<int> cyc(L + 1, 0);
     for (int f = 2; f <= L; ++f) {
@@ -577,7 +579,7 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
         prof_end(KC_SMALL, s, 32.0 * nh * nh, 0.0);
         // 3: enriched eigensolve
         dense_eig(w.Ahat.get(), w.Mhat.get(), nh, sigma, k, w.theta.get(), w.Y.get(), w.rank.get(), w.dense.get(),
-                  w.dstats.get(), s);
+                  w.dquality.get(), s);
         prof_begin(KC_SMALL, s);
         shifts_kernel<<<grid_of(ld, 128), 128, 0, s>>>(w.theta.get(), k, ld, sigma, o.form, w.lam.get(), w.shift.get());
         check_launch("shifts_kernel");
@@ -597,11 +599,14 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
         BMG_CUDA(cudaMemcpyAsync(hres, w.res.get(), sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
         BMG_CUDA(cudaMemcpyAsync(hlam, w.lam.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
         BMG_CUDA(cudaMemcpyAsync(hint, w.rank.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
-        BMG_CUDA(cudaMemcpyAsync(hint + 1, w.dstats.get(), 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        BMG_CUDA(cudaMemcpyAsync(hqual, w.dquality.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
         BMG_CUDA(cudaStreamSynchronize(s));
         ++total_cycles;
         cyc[f] = c + 1;
         if (hint[0] < k) fail(BMG_ERR_SINGULAR, "enriched space rank " + std::to_string(hint[0]) + " < k");
+        if (!(*hqual <= 1e-6))
+          fail(BMG_ERR_NONFINITE, "enriched eigensolve refinement failed (error estimate " + std::to_string(*hqual) + ")");
+        max_dense_err = std::max(max_dense_err, *hqual);
         bool conv = true, finite = true;
         for (int i = 0; i < k; ++i) {
           lamv[i] = hlam[i];
@@ -668,6 +673,7 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
       double mx = 0.0;
       for (int i = 0; i < n_wanted; ++i) mx = std::max(mx, rho[i]);
       info->max_resid = mx;
+      info->max_dense_err = max_dense_err;
     }
     if (!converged) {
       final_status = BMG_ERR_NOT_CONVERGED;

@@ -117,10 +117,11 @@ struct SolveWork {
   DBuf<double> X, AX, MX, U, AU, MU, B, W, Zf;
   std::vector<DBuf<double>> cA, cB, cC, cD;  // per coarse level j < L: [N_j][ld]
   DBuf<double> Ahat, Mhat, Y, theta, lam, shift, GA, GM, dense, partial, res;
-  DBuf<int> rank, dstats;
+  DBuf<int> rank;
+  DBuf<double> dquality;                    // error estimate of the last enriched eigensolve
   std::vector<DBuf<double>> AQ, MQ;         // per f: dense n1 x n1 coarse blocks
   std::vector<std::vector<double>> ratio;   // [f][j] max_i dM_i / dA_i
-  double* hbuf = nullptr;                   // pinned host staging (res, lam, rank, stats)
+  double* hbuf = nullptr;                   // pinned host staging (res, lam, quality, rank)
   ~SolveWork() { if (hbuf) cudaFreeHost(hbuf); }
 };
 }  // namespace bmg
@@ -193,6 +194,6 @@ void axpy_block(double* Y, const double* X, int n, int ld, cudaStream_t s);
 
 // dense (dense.cu)
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k,
-               double* theta, double* Y, int* rank, double* work, int* stats, cudaStream_t s);
+               double* theta, double* Y, int* rank, double* work, double* quality, cudaStream_t s);
 size_t dense_work_doubles(int n);
 }  // namespace bmg
