@@ -206,6 +206,20 @@ bmg_status bmg_gram(const double* X, const double* Y, int n, int k, int ld, doub
 bmg_status bmg_dense_eig(const double* Ahat, const double* Mhat, int n, double sigma,
                          int k, double* theta, double* Y, int* rank_out, void* stream);
 
+/* The same product as bmg_gram for callers that must not allocate device memory:
+ * a framework that has already reserved all device memory for its own pool, a
+ * service held to a fixed device-memory budget, or a caller that cannot accept the
+ * device-wide wait that freeing memory implies.  The paper has no counterpart; it
+ * is a deployment variant.  The block partial sums live in one fixed array inside
+ * the library (4 MiB, held by every GPU that loads it until the process exits).
+ * The first call on each device looks up that array's device address; make that
+ * first call before any stream capture.  Asynchronous on `stream`; no device
+ * memory is allocated or freed.  k <= 160 (larger k: BMG_ERR_INVALID_ARG).  All
+ * calls share the array: calls whose work overlaps on the GPU (e.g. on two
+ * streams) race and give wrong results; order them on one stream.               */
+bmg_status bmg_gram_noalloc(const double* X, const double* Y, int n, int k, int ld, double* G,
+                            void* stream);
+
 /* ------------------------------------------------------------ measurement --- */
 /* Kernel-class timing for benchmarks (no counterpart in the paper).  When enabled,
  * the launches of each class made by any call are bracketed by CUDA events on the

@@ -65,6 +65,7 @@ def _load():
         "bmg_prolong": (i, [vp, i, vp, vp, i, i, i, vp]),
         "bmg_restrict": (i, [vp, i, vp, vp, i, i, vp]),
         "bmg_gram": (i, [vp, vp, i, i, i, vp, vp]),
+        "bmg_gram_noalloc": (i, [vp, vp, i, i, i, vp, vp]),
         "bmg_dense_eig": (i, [vp, vp, i, d, i, vp, vp, vp, vp]),
         "bmg_profile_enable": (i, [i]),
         "bmg_profile_reset": (i, []),
@@ -276,6 +277,11 @@ def _solve_raw(h, X0_ptr, x0_dev, U_ptr, u_dev, k, n_wanted, sigma, tol, opt):
 
 def gram(X, Y, k, G):
     _check(LIB.bmg_gram(_ptr(X), _ptr(Y), X.shape[0], k, X.shape[1], _ptr(G), _stream()))
+
+
+def gram_noalloc(X, Y, k, G):
+    """G = X^T Y through bmg_gram_noalloc (no device allocation; see include/bmg.h)."""
+    _check(LIB.bmg_gram_noalloc(_ptr(X), _ptr(Y), X.shape[0], k, X.shape[1], _ptr(G), _stream()))
 
 
 def dense_eig(Ahat, Mhat, sigma, k, theta, Y, rank=None):

@@ -26,11 +26,6 @@ static thread_local std::string g_last_error = "no error";
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
-struct BmgException {
-  bmg_status code;
-  std::string msg;
-};
-
 [[noreturn]] void fail(bmg_status code, const std::string& msg) { throw BmgException{code, msg}; }
 
 void check_cuda(cudaError_t e, const char* what) {

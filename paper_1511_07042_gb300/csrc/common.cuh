@@ -13,7 +13,8 @@ namespace bmg {
 
 // ---------------------------------------------------------------- errors ----
 void set_error(const std::string& msg);
-struct Error {
+// Thrown by fail(); every extern "C" entry catches it and returns its code.
+struct BmgException {
   bmg_status code;
   std::string msg;
 };
