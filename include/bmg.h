@@ -124,7 +124,7 @@ const char* bmg_last_error(void);
  * in V_{h_1} + span(X) (Sec. 4.1 block matrices), source-problem smoothing from
  * the finest level down (Alg. 3 step 3), prolongation of the Ritz vectors to the
  * next level.  Returns the n_wanted Ritz pairs nearest sigma on level L.
- *   k: block size (n_wanted <= k <= N_2, k <= 160, N_1 + k <= 320); sigma: shift; tol: the
+ *   k: block size (n_wanted <= k <= N_2, k <= 160, N_1 + k <= 224); sigma: shift; tol: the
  *      finest level stops when every wanted pair has
  *      ||A u - lambda M u||_2 / (||A||_1 ||u||_2) <= tol.
  *   opt: options (NULL = defaults).
@@ -196,7 +196,7 @@ bmg_status bmg_gram(const double* X, const double* Y, int n, int k, int ld, doub
                     void* stream);
 
 /* Smallest-|theta| k eigenpairs of the symmetric-semidefinite pencil
- * (Ahat - sigma Mhat) y = theta Mhat y, n x n row-major device matrices (n <= 320):
+ * (Ahat - sigma Mhat) y = theta Mhat y, n x n row-major device matrices (n <= 224):
  * Mhat is scaled to unit diagonal, reduced by a Cholesky factorisation with
  * diagonal pivoting that drops pivots below 1e-12 (rank-deficient enriched
  * spaces), and the reduced standard problem is solved (Alg. 2 step 4).

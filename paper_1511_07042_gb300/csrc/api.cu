@@ -388,7 +388,7 @@ extern "C" bmg_status bmg_dense_eig(const double* Ahat, const double* Mhat, int 
                                     double* theta, double* Y, int* rank_out, void* stream) {
   return guarded([&] {
     if (!Ahat || !Mhat || !theta || !Y) fail(BMG_ERR_INVALID_ARG, "null pointer");
-    if (n < 1 || n > 320 || k < 1 || k > n) fail(BMG_ERR_INVALID_ARG, "need 1 <= k <= n <= 320");
+    if (n < 1 || n > 224 || k < 1 || k > n) fail(BMG_ERR_INVALID_ARG, "need 1 <= k <= n <= 224");
     DBuf<double> work(dense_work_doubles(n));
     DBuf<int> rk(1);
     dense_eig(Ahat, Mhat, n, sigma, k, theta, Y, rank_out ? rank_out : rk.get(), work.get(), nullptr,
@@ -522,8 +522,8 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
     if (opt_in) o = *opt_in;
     const int L = p->L;
     const int n1 = p->meshOf(1).n, n2 = p->meshOf(2).n, nL = p->meshOf(L).n;
-    if (k < 1 || k > 160 || n_wanted < 1 || n_wanted > k || k > n2 || n1 + k > 320)
-      fail(BMG_ERR_INVALID_ARG, "need 1 <= n_wanted <= k <= min(N_2, 160) and N_1 + k <= 320");
+    if (k < 1 || k > 160 || n_wanted < 1 || n_wanted > k || k > n2 || n1 + k > 224)
+      fail(BMG_ERR_INVALID_ARG, "need 1 <= n_wanted <= k <= min(N_2, 160) and N_1 + k <= 224");
     if (!X0 || !evals) fail(BMG_ERR_INVALID_ARG, "X0 and evals are required");
     if (!(tol > 0.0) || !std::isfinite(sigma)) fail(BMG_ERR_INVALID_ARG, "bad tol or sigma");
     if (o.nu < 1 || o.nu > 64 || o.smoother < 0 || o.smoother > 2 || o.form < 0 || o.form > 1 ||

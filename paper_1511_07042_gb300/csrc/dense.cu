@@ -1,27 +1,28 @@
 // Eigensolve in the enriched coarse space (Alg. 2 step 4; Alg. 3 steps 1 and 5):
 // the k pairs of (Ahat - sigma Mhat) y = theta Mhat y with smallest |theta|, for the
-// block matrices of Sec. 4.1 (size n = N_1 + k <= 320).
+// block matrices of Sec. 4.1 (size n = N_1 + k <= 224).
 //
-// GB300 executes FP64 at about 1/70 of its FP32 rate, so a single CTA cannot afford
-// the O(n^3) work of a dense eigensolver in FP64.  The solve is split:
-//   1. [1 CTA, FP64]  M-orthonormal basis of the enriched space (the b_h-
-//      orthogonalisation of Alg. 2 step 3): Mhat scaled to unit diagonal, Cholesky
-//      with diagonal pivoting; pivots below kDropTol mark basis vectors already in
-//      the span of the others, which are dropped (rank r).
-//   2. [multi-CTA, FP64]  reduced standard matrix T = L^{-1} D P^T (Ahat - sigma
-//      Mhat) P D L^{-T} by two forward substitutions (one warp per column).
-//   3. [1 CTA, FP32]  cyclic Jacobi (round-robin order) on T in shared memory:
-//      eigenvectors W accurate to FP32.
-//   4. [multi-CTA, FP64]  refinement of W to FP64 accuracy by the iterative scheme
-//      of Ogita & Aishima (2018) for symmetric eigendecompositions:
+// GB300 executes FP64 at about 1/70 of its FP32 rate and a single CTA is bound by the
+// latency of its dependent steps, so the solve is organised around few steps:
+//   1. basis_kernel    [1 CTA, FP64]  the b_h-orthogonalisation of Alg. 2 step 3: Mhat
+//      scaled to unit diagonal, Cholesky with diagonal pivoting in shared memory;
+//      pivots below kDropTol mark basis vectors already in the span of the others,
+//      which are dropped (rank r).
+//   2. trsm_kernel     [multi-CTA, FP64]  reduced standard matrix
+//      T = L^{-1} D P^T (Ahat - sigma Mhat) P D L^{-T}: two forward substitutions, one
+//      warp per column, the column kept in shared memory.
+//   3. eig32_kernel    [1 CTA, FP32]  Householder tridiagonalisation of T, bisection
+//      on Sturm counts for all eigenvalues, inverse iteration (with modified
+//      Gram-Schmidt inside clusters of close eigenvalues) for the eigenvectors, and
+//      the back-transformation, each column owned by one warp.
+//   4. refinement      [multi-CTA, FP64]  the eigenvectors W are refined to FP64
+//      accuracy by the iterative scheme of Ogita & Aishima (2018):
 //          G = W^T W, R = I - G, S = W^T T W, lt_i = s_ii / (1 - r_ii),
 //          E_ij = (s_ij + lt_j r_ij) / (lt_j - lt_i) for well separated pairs,
 //          r_ij / 2 otherwise,   W <- W (I + E);
-//      pairs closer than the FP32 resolution form clusters whose m x m block is
-//      diagonalised exactly (FP64 Jacobi) once the separated pairs have converged,
-//      then one more step polishes the couplings.
-//   5. [multi-CTA, FP64]  selection of the k smallest |theta| and back-transform
-//      Y = D P L^{-T} W_sel (back substitution, one warp per column).
+//      clusters of nearly equal values are diagonalised exactly (FP64 Jacobi on the
+//      cluster block, one CTA per cluster) once the separated pairs converged.
+//   5. select / backsub  the k smallest |theta|; Y = D P L^{-T} W_sel.
 #include <algorithm>
 #include <cmath>
 
@@ -33,105 +34,171 @@ namespace {
 constexpr double kDropTol = 1e-12;
 constexpr double kClusterFloor = 1e-3;   // relative gap below which the FP32 start cannot separate pairs
 constexpr double kGuard = 0.05;          // largest first-order correction accepted by a step
-constexpr int kCholThreads = 512;
-constexpr int kJacThreads = 1024;
 constexpr int kMaxN = 320;
-constexpr int kMaxCluster = 40;   // larger clusters keep the orthonormalising step only
+constexpr int kMaxDense = 224;           // the FP32 stage keeps T (n^2 floats) in shared memory
+constexpr int kBig = 1024;               // threads of the single-CTA kernels
+constexpr int kMaxCluster = 40;          // larger clusters keep the orthonormalising step only
+constexpr int kTile = 8;                 // output tile of the refinement products
 
-// Scratch carved from one device allocation; n x n blocks row-major, stride n.
+// Scratch carved from one device allocation; n x n blocks row-major with stride n.
 struct DW {
-  double *S, *L, *T, *Z, *W, *W2, *G, *SS, *E, *P, *d, *lam, *misc;
-  int* perm;
-  int* order;
-  int* rank;
+  double *S, *L, *T, *Z, *W, *W2, *G, *SS, *P, *E, *d, *lam, *misc;
+  float *A32, *Z32;
+  int *perm, *order, *rank, *srt, *cl;
 };
 
-// ------------------------------------------------- 1. pivoted Cholesky (FP64) --
-__global__ void __launch_bounds__(kCholThreads)
-chol_kernel(const double* __restrict__ Mhat, int n, DW w) {
-  __shared__ double red_v[kCholThreads];
-  __shared__ int red_i[kCholThreads];
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block (every thread gets the result); red has 32 slots.  Two barriers.
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  T s = 0;
+  const int nw = blockDim.x >> 5;
+  for (int q = 0; q < nw; ++q) s += red[q];
+  __syncthreads();
+  return s;
+}
+
+// ------------------------------------------------ 1. basis (pivoted Cholesky) --
+// Symmetric pivoting is done physically on the upper triangle of S (row j holds
+// S[j][j..n)), so every step reads and writes contiguous rows.  L is written in pivot
+// order: L[i][q] for pivot position i and step q <= i (rows swapped with the pivots).
+__global__ void __launch_bounds__(kBig)
+basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS) {
+  extern __shared__ double dsm[];
+  double* S = smemS ? dsm : w.S;
+  __shared__ double wv[32];
+  __shared__ int wi[32];
   __shared__ int perm[kMaxN];
-  __shared__ int s_rank;
-  const int tid = threadIdx.x;
-  for (int i = tid; i < n; i += kCholThreads) {
+  __shared__ double d[kMaxN], lcol[kMaxN];
+  __shared__ int s_rank, s_p;
+  __shared__ double s_piv;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nwarps = kBig / 32;
+  for (int i = tid; i < n; i += kBig) {
     const double mii = Mhat[i * n + i];
-    w.d[i] = (mii > 0.0) ? 1.0 / sqrt(mii) : 0.0;
+    d[i] = (mii > 0.0) ? 1.0 / sqrt(mii) : 0.0;
     perm[i] = i;
   }
   __syncthreads();
-  for (int q = tid; q < n * n; q += kCholThreads) {
-    const int i = q / n, j = q % n;
-    w.S[q] = 0.5 * (Mhat[i * n + j] + Mhat[j * n + i]) * w.d[i] * w.d[j];
-    w.L[q] = 0.0;
-  }
+  for (int i = wid; i < n; i += nwarps)
+    for (int j = lane; j < n; j += 32) {
+      S[i * n + j] = 0.5 * (Mhat[i * n + j] + Mhat[j * n + i]) * d[i] * d[j];
+      w.L[i * n + j] = 0.0;
+    }
   if (tid == 0) s_rank = n;
   __syncthreads();
   for (int j = 0; j < n; ++j) {
     double best = -1.0;
     int bi = j;
-    for (int i = j + tid; i < n; i += kCholThreads) {
-      const double v = w.S[perm[i] * n + perm[i]];
+    for (int i = j + tid; i < n; i += kBig) {
+      const double v = S[i * n + i];
       if (v > best || (v == best && i < bi)) { best = v; bi = i; }
     }
-    red_v[tid] = best;
-    red_i[tid] = bi;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+    }
+    if (lane == 0) { wv[wid] = best; wi[wid] = bi; }
     __syncthreads();
-    for (int off = kCholThreads / 2; off > 0; off >>= 1) {
-      if (tid < off) {
-        const double v2 = red_v[tid + off];
-        const int i2 = red_i[tid + off];
-        if (v2 > red_v[tid] || (v2 == red_v[tid] && i2 < red_i[tid])) { red_v[tid] = v2; red_i[tid] = i2; }
+    if (wid == 0) {
+      best = wv[lane];
+      bi = wi[lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
       }
-      __syncthreads();
+      if (lane == 0) {
+        s_piv = best;
+        s_p = bi;
+        if (!(best > kDropTol)) s_rank = j;   // NaN fails the test too
+      }
     }
-    const double piv = red_v[0];
-    const int pi = red_i[0];
     __syncthreads();
-    if (!(piv > kDropTol)) {  // also catches NaN
-      if (tid == 0) s_rank = j;
-      __syncthreads();
-      break;
+    if (!(s_piv > kDropTol)) break;
+    const int p = s_p;
+    if (p != j) {
+      // symmetric swap of indices j < p in upper-triangle storage
+      for (int x = tid; x < n; x += kBig) {
+        if (x < j) {
+          const double t = S[x * n + j]; S[x * n + j] = S[x * n + p]; S[x * n + p] = t;
+        } else if (x > j && x < p) {
+          const double t = S[j * n + x]; S[j * n + x] = S[x * n + p]; S[x * n + p] = t;
+        } else if (x > p) {
+          const double t = S[j * n + x]; S[j * n + x] = S[p * n + x]; S[p * n + x] = t;
+        } else if (x == j) {
+          const double t = S[j * n + j]; S[j * n + j] = S[p * n + p]; S[p * n + p] = t;
+        }
+        if (x < j) {   // rows j and p of the factor computed so far
+          const double t = w.L[j * n + x]; w.L[j * n + x] = w.L[p * n + x]; w.L[p * n + x] = t;
+        }
+      }
+      if (tid == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
     }
-    if (tid == 0) { const int t = perm[j]; perm[j] = perm[pi]; perm[pi] = t; }
     __syncthreads();
-    const double ljj = sqrt(piv);
-    const int pj = perm[j];
-    for (int i = j + tid; i < n; i += kCholThreads)
-      w.L[perm[i] * n + j] = (i == j) ? ljj : w.S[perm[i] * n + pj] / ljj;
+    const double ljj = sqrt(s_piv), rl = 1.0 / ljj;
+    for (int i = j + tid; i < n; i += kBig) {
+      const double v = (i == j) ? ljj : S[j * n + i] * rl;
+      lcol[i] = v;
+      w.L[i * n + j] = v;
+    }
     __syncthreads();
-    const int m = n - j - 1;
-    for (int q = tid; q < m * m; q += kCholThreads) {
-      const int a = j + 1 + q / m, b = j + 1 + q % m;
-      if (b < a) continue;  // update the upper triangle and mirror it
-      const double v = w.S[perm[a] * n + perm[b]] - w.L[perm[a] * n + j] * w.L[perm[b] * n + j];
-      w.S[perm[a] * n + perm[b]] = v;
-      w.S[perm[b] * n + perm[a]] = v;
+    for (int a = j + 1 + wid; a < n; a += nwarps) {   // upper triangle of the trailing block
+      const double la = lcol[a];
+      double* Sa = S + a * n;
+      for (int b = a + lane; b < n; b += 32) Sa[b] -= la * lcol[b];
     }
     __syncthreads();
   }
-  for (int i = tid; i < n; i += kCholThreads) w.perm[i] = perm[i];
+  for (int i = tid; i < n; i += kBig) { w.perm[i] = perm[i]; w.d[i] = d[i]; }
   if (tid == 0) *w.rank = s_rank;
 }
 
-// --------------------------------------- 2. T = L^{-1} C L^{-T} (FP64, warps) --
-// pass 0: Z = L^{-1} C with C[i][c] = d_a (Ahat - sigma Mhat)_ab d_b, a = perm[i],
-//         b = perm[c] (symmetrised);  pass 1: T = L^{-1} Z^T.
-// One warp per column c; the rows run in order, lanes share each dot product.
-__global__ void trsm_fwd_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mhat,
-                                int n, double sigma, int pass, DW w) {
+// ---------------------------------------- 2. T = L^{-1} C L^{-T} (FP64, warps) --
+// pass 0: Z = L^{-1} C, C[i][c] = d_a sym(Ahat - sigma Mhat)_ab d_b with a = perm[i],
+// b = perm[c];  pass 1: T = L^{-1} Z^T.  One warp per column c.
+constexpr int kTrsmWarps = 8;
+__global__ void __launch_bounds__(kTrsmWarps * 32)
+trsm_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mhat, int n, double sigma,
+            int pass, DW w, int lsmem) {
+  extern __shared__ double lsm[];
+  __shared__ double zc[kTrsmWarps][kMaxN];
   const int r = *w.rank;
-  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double* L = w.L;
+  if (lsmem) {   // the leading r x r block of L, rows in pivot order
+    for (int q = threadIdx.x; q < r * r; q += kTrsmWarps * 32) lsm[q] = w.L[(q / r) * n + (q % r)];
+    __syncthreads();
+    L = lsm;
+  }
+  const int ldl = lsmem ? r : n;
+  const int c = blockIdx.x * kTrsmWarps + wid;
   if (c >= r) return;
-  double* out = pass == 0 ? w.Z : w.T;
+  double* z = zc[wid];
   const int* perm = w.perm;
   for (int i = 0; i < r; ++i) {
-    const double* Li = w.L + perm[i] * n;
+    const double* Li = L + i * ldl;
     double s = 0.0;
-    for (int q = lane; q < i; q += 32) s += Li[q] * out[q * n + c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    for (int q = lane; q < i; q += 32) s += Li[q] * z[q];
+    s = warp_sum(s);
     if (lane == 0) {
       double rhs;
       if (pass == 0) {
@@ -142,357 +209,497 @@ __global__ void trsm_fwd_kernel(const double* __restrict__ Ahat, const double* _
       } else {
         rhs = w.Z[c * n + i];
       }
-      out[i * n + c] = (rhs - s) / Li[i];
+      z[i] = (rhs - s) / Li[i];
     }
     __syncwarp();
   }
+  double* out = pass == 0 ? w.Z : w.T;
+  for (int i = lane; i < r; i += 32) out[i * n + c] = z[i];
 }
 
-// ------------------------------------------------ 3. FP32 Jacobi (1 CTA) ------
-// Round-robin parallel cyclic Jacobi on a float copy of T held in shared memory
-// (2 r^2 floats) or in global scratch when it does not fit.
-__global__ void __launch_bounds__(kJacThreads)
-jacobi32_kernel(int n, int use_smem, float* __restrict__ gscratch, DW w, int max_sweeps, float tol) {
-  extern __shared__ float sm[];
-  __shared__ float cs_c[kMaxN / 2], cs_s[kMaxN / 2];
-  __shared__ int pr_p[kMaxN / 2], pr_q[kMaxN / 2];
-  __shared__ float red[kJacThreads / 32][2];
-  __shared__ float s_off, s_fro;
+// ---------------------------------------------- 3. FP32 eigensolve (1 CTA) -----
+__global__ void __launch_bounds__(kBig)
+eig32_kernel(int n, int zsmem, int slots, DW w) {
+  extern __shared__ float fsm[];
+  __shared__ float d[kMaxN], e[kMaxN], e2[kMaxN], tau[kMaxN], vb[kMaxN], pv[kMaxN], lam[kMaxN];
+  __shared__ float redf[32], slo[32], shi[32];
   const int r = *w.rank;
-  const int tid = threadIdx.x;
-  float* A = use_smem ? sm : gscratch;
-  float* V = A + r * r;
-  for (int q = tid; q < r * r; q += kJacThreads) {
-    const int i = q / r, j = q % r;
-    A[q] = (float)(0.5 * (w.T[i * n + j] + w.T[j * n + i]));
-    V[q] = (i == j) ? 1.f : 0.f;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nwarps = kBig / 32;
+  float* A = fsm;                                   // r x r
+  float* Z = zsmem ? fsm + r * r : w.Z32;           // r x r eigenvectors (columns)
+  for (int i = wid; i < r; i += nwarps)
+    for (int j = lane; j < r; j += 32) A[i * r + j] = (float)(0.5 * (w.T[i * n + j] + w.T[j * n + i]));
+  __syncthreads();
+  // --- Householder tridiagonalisation, v_j stored in column j below the subdiagonal
+  for (int j = 0; j + 2 < r; ++j) {
+    const float a0 = A[(j + 1) * r + j];
+    float part = 0.f;
+    for (int i = j + 2 + tid; i < r; i += kBig) part += A[i * r + j] * A[i * r + j];
+    const float xn2 = block_sum<float>(part, redf);
+    float beta = a0, t = 0.f, scale = 0.f;
+    if (xn2 > 0.f) {
+      beta = -copysignf(sqrtf(a0 * a0 + xn2), a0);
+      t = (beta - a0) / beta;
+      scale = 1.f / (a0 - beta);
+    }
+    const int m = r - j - 1;
+    for (int q = tid; q < m; q += kBig) {
+      const float v = (q == 0) ? 1.f : A[(j + 1 + q) * r + j] * scale;
+      vb[q] = v;
+      if (q > 0) A[(j + 1 + q) * r + j] = v;
+    }
+    if (tid == 0) { d[j] = A[j * r + j]; e[j] = beta; tau[j] = t; }
+    __syncthreads();
+    if (t != 0.f) {
+      for (int a = wid; a < m; a += nwarps) {        // p = t A22 v
+        const float* Ar = A + (j + 1 + a) * r + (j + 1);
+        float s = 0.f;
+        for (int b = lane; b < m; b += 32) s += Ar[b] * vb[b];
+        s = warp_sumf(s);
+        if (lane == 0) pv[a] = t * s;
+      }
+      __syncthreads();
+      float kk = 0.f;                                 // K = (t/2) p.v, per warp
+      for (int a = lane; a < m; a += 32) kk += pv[a] * vb[a];
+      kk = 0.5f * t * warp_sumf(kk);
+      for (int a = wid; a < m; a += nwarps) {        // A22 -= v w^T + w v^T, w = p - K v
+        float* Ar = A + (j + 1 + a) * r + (j + 1);
+        const float va = vb[a], wa = pv[a] - kk * va;
+        for (int b = lane; b < m; b += 32) Ar[b] -= va * (pv[b] - kk * vb[b]) + wa * vb[b];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    if (r >= 2) {
+      d[r - 2] = A[(r - 2) * r + (r - 2)];
+      e[r - 2] = A[(r - 1) * r + (r - 2)];
+      tau[r - 2] = 0.f;
+    }
+    if (r >= 1) { d[r - 1] = A[(r - 1) * r + (r - 1)]; e[r - 1] = 0.f; tau[r - 1] = 0.f; }
   }
   __syncthreads();
-  const int m = (r % 2 == 0) ? r : r + 1;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    float off = 0.f, fro = 0.f;
-    for (int q = tid; q < r * r; q += kJacThreads) {
-      const float v = A[q];
-      fro += v * v;
-      if (q / r != q % r) off += v * v;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      fro += __shfl_xor_sync(0xffffffffu, fro, o);
-    }
-    if ((tid & 31) == 0) { red[tid >> 5][0] = off; red[tid >> 5][1] = fro; }
-    __syncthreads();
-    if (tid == 0) {
-      float a = 0.f, b = 0.f;
-      for (int q = 0; q < kJacThreads / 32; ++q) { a += red[q][0]; b += red[q][1]; }
-      s_off = a;
-      s_fro = b;
-    }
-    __syncthreads();
-    if (s_off <= tol * tol * s_fro || s_fro == 0.f) break;
-    for (int step = 0; step < m - 1; ++step) {
-      for (int i = tid; i < m / 2; i += kJacThreads) {
-        auto player = [&](int t) { return t == 0 ? 0 : ((t - 1 + step) % (m - 1)) + 1; };
-        int p = player(i), q = player(m - 1 - i);
-        if (p > q) { const int t = p; p = q; q = t; }
-        float c = 1.f, s = 0.f;
-        if (q < r) {
-          const float apq = A[p * r + q];
-          const float app = A[p * r + p], aqq = A[q * r + q];
-          if (apq != 0.f && fabsf(apq) > 1e-12f * sqrtf(fabsf(app * aqq))) {
-            const float tau = (aqq - app) / (2.f * apq);
-            const float t = (fabsf(tau) > 1e18f) ? 0.5f / tau
-                                                  : copysignf(1.f, tau) / (fabsf(tau) + sqrtf(1.f + tau * tau));
-            c = 1.f / sqrtf(1.f + t * t);
-            s = t * c;
-          }
-        }
-        cs_c[i] = c; cs_s[i] = s; pr_p[i] = p; pr_q[i] = (q < r && s != 0.f) ? q : -1;
-      }
-      __syncthreads();
-      const int half = m / 2;
-      for (int it = tid; it < half * r; it += kJacThreads) {   // rows p, q  <- J^T A
-        const int i = it / r, col = it % r;
-        const int q = pr_q[i];
-        if (q < 0) continue;
-        const int p = pr_p[i];
-        const float c = cs_c[i], s = cs_s[i];
-        const float ap = A[p * r + col], aq = A[q * r + col];
-        A[p * r + col] = c * ap - s * aq;
-        A[q * r + col] = s * ap + c * aq;
-      }
-      __syncthreads();
-      for (int it = tid; it < half * r; it += kJacThreads) {   // columns p, q <- A J ; V <- V J
-        const int i = it / r, row = it % r;
-        const int q = pr_q[i];
-        if (q < 0) continue;
-        const int p = pr_p[i];
-        const float c = cs_c[i], s = cs_s[i];
-        const float ap = A[row * r + p], aq = A[row * r + q];
-        A[row * r + p] = c * ap - s * aq;
-        A[row * r + q] = s * ap + c * aq;
-        const float vp = V[row * r + p], vq = V[row * r + q];
-        V[row * r + p] = c * vp - s * vq;
-        V[row * r + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-    }
-  }
-  for (int q = tid; q < r * r; q += kJacThreads) {
-    const int i = q / r, j = q % r;
-    w.W[i * n + j] = (double)V[q];
-  }
-}
-
-// ------------------------------------------------ small FP64 GEMM (tiles) -----
-// C = alpha * op(A) * B + beta * D  (m x p; inner q).  op(A) = A (m x q) or A^T
-// (A stored q x m).  A negative size means the rank r.
-constexpr int kT = 16;
-template <bool TA>
-__global__ void __launch_bounds__(kT * kT)
-gemm64_kernel(int m, int p, int q, const double* __restrict__ A, int lda,
-              const double* __restrict__ B, int ldb, double* C, int ldc, double alpha, double beta,
-              const double* D, int ldd, const int* __restrict__ rank) {
-  __shared__ double As[kT][kT + 1], Bs[kT][kT + 1];
-  const int r = *rank;
-  if (m < 0) m = r;
-  if (p < 0) p = r;
-  if (q < 0) q = r;
-  if (blockIdx.y * kT >= m || blockIdx.x * kT >= p) return;   // whole block
-  const int ty = threadIdx.x / kT, tx = threadIdx.x % kT;
-  const int row = blockIdx.y * kT + ty, col = blockIdx.x * kT + tx;
-  double acc = 0.0;
-  for (int k0 = 0; k0 < q; k0 += kT) {
-    const int ka = k0 + tx, kb = k0 + ty;
-    if (TA) As[ty][tx] = (row < m && ka < q) ? A[ka * lda + row] : 0.0;
-    else    As[ty][tx] = (row < m && ka < q) ? A[row * lda + ka] : 0.0;
-    Bs[ty][tx] = (kb < q && col < p) ? B[kb * ldb + col] : 0.0;
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < kT; ++t) acc = fma(As[ty][t], Bs[t][tx], acc);
-    __syncthreads();
-  }
-  if (row < m && col < p) {
-    double v = alpha * acc;
-    if (beta != 0.0) v += beta * D[row * ldd + col];
-    C[row * ldc + col] = v;
-  }
-}
-
-// ------------------------------------------------- 4. refinement step (1 CTA) --
-// From G = W^T W and SS = W^T T W: lam (Rayleigh quotients) and the update E
-// (W <- W + W E).
-//   mode 0: Ogita-Aishima step; pairs with gap <= max(delta, floor * max|lam|)
-//           only get the orthonormalising term.
-//   mode 1: clusters (chains of sorted lam with gaps <= the same threshold) are
-//           orthonormalised to first order and their blocks diagonalised exactly
-//           by FP64 Jacobi; E = blockdiag(F_c) - I.
-//   mode 2: lam and the error estimate only.
-constexpr int kOAThreads = 1024;
-__global__ void __launch_bounds__(kOAThreads)
-oa_kernel(int n, int mode, double floor_rel, DW w) {
-  __shared__ double red[kOAThreads / 32][3];
-  __shared__ double s_delta, s_amax;
-  __shared__ int srt[kMaxN];
-  __shared__ int cl_start[kMaxN + 1];
-  __shared__ int s_ncl;
-  __shared__ double cA[kMaxCluster * kMaxCluster], cV[kMaxCluster * kMaxCluster];
-  __shared__ double cK[kMaxCluster * kMaxCluster];
-  __shared__ double ccs_c[kMaxCluster / 2], ccs_s[kMaxCluster / 2];
-  __shared__ int cpr_p[kMaxCluster / 2], cpr_q[kMaxCluster / 2];
-  __shared__ double s_toff, s_tfro;
-  const int r = *w.rank;
-  const int tid = threadIdx.x;
-  // G and SS come from separate products and are symmetric only to rounding; the
-  // update needs E + E^T = R exactly for pairs with tiny gaps, so use their
-  // symmetric parts.
-  auto Gs = [&](int i, int j) { return 0.5 * (w.G[i * n + j] + w.G[j * n + i]); };
-  auto Ss = [&](int i, int j) { return 0.5 * (w.SS[i * n + j] + w.SS[j * n + i]); };
-  for (int i = tid; i < r; i += kOAThreads) {
-    const double gii = w.G[i * n + i];
-    w.lam[i] = w.SS[i * n + i] / (2.0 - gii);   // s_ii / (1 - r_ii) with r = I - G
-  }
-  __syncthreads();
-  double nS = 0.0, nR = 0.0, amax = 0.0;
-  for (int q = tid; q < r * r; q += kOAThreads) {
-    const int i = q / r, j = q % r;
-    const double rij = (i == j ? 1.0 : 0.0) - Gs(i, j);
-    const double sij = Ss(i, j) - (i == j ? w.lam[i] : 0.0);
-    nS += sij * sij;
-    nR += rij * rij;
-    if (i == j) amax = fmax(amax, fabs(w.lam[i]));
+  // --- Gershgorin interval
+  float lo = 3.4e38f, hi = -3.4e38f;
+  for (int i = tid; i < r; i += kBig) {
+    const float rad = fabsf(e[i]) + (i > 0 ? fabsf(e[i - 1]) : 0.f);
+    lo = fminf(lo, d[i] - rad);
+    hi = fmaxf(hi, d[i] + rad);
+    e2[i] = e[i] * e[i];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    nS += __shfl_xor_sync(0xffffffffu, nS, o);
-    nR += __shfl_xor_sync(0xffffffffu, nR, o);
-    amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
   }
-  if ((tid & 31) == 0) { red[tid >> 5][0] = nS; red[tid >> 5][1] = nR; red[tid >> 5][2] = amax; }
+  if (lane == 0) { slo[wid] = lo; shi[wid] = hi; }
   __syncthreads();
+  lo = slo[0]; hi = shi[0];
+  for (int q = 1; q < nwarps; ++q) { lo = fminf(lo, slo[q]); hi = fmaxf(hi, shi[q]); }
+  const float span = fmaxf(fmaxf(fabsf(lo), fabsf(hi)), 1e-30f);
+  const float pivmin = 1e-30f * fmaxf(span * span, 1.f);
+  // --- bisection: thread i finds the i-th smallest eigenvalue
+  for (int i = tid; i < r; i += kBig) {
+    float a = lo - 1e-6f * span, b = hi + 1e-6f * span;
+    for (int it = 0; it < 64; ++it) {
+      const float x = 0.5f * (a + b);
+      if (!(b - a > 2.4e-7f * fmaxf(fabsf(a), fabsf(b)) + 1e-30f) || x == a || x == b) break;
+      int cnt = 0;
+      float q = d[0] - x;
+      if (fabsf(q) < pivmin) q = -pivmin;
+      cnt += q < 0.f;
+      for (int jj = 1; jj < r; ++jj) {
+        q = (d[jj] - x) - __fdividef(e2[jj - 1], q);
+        if (fabsf(q) < pivmin) q = -pivmin;
+        cnt += q < 0.f;
+      }
+      if (cnt > i) b = x; else a = x;
+    }
+    lam[i] = 0.5f * (a + b);
+  }
+  __syncthreads();
+  // --- inverse iteration (the scheme of LAPACK's stein): clusters are chains of
+  // eigenvalues closer than 1e-4 span.  Each warp takes clusters w, w + nwarps, ...;
+  // inside a cluster the members run in order, each with its own shift (kept at
+  // least eps_sep above the previous one), two solves of (T3 - x I) z = z, and
+  // after every solve modified Gram-Schmidt against the earlier members (all lanes).
+  // Lane 0 does the tridiagonal factorisation and the solves; the factors live in a
+  // per-warp slot of shared memory.
+  __shared__ int cst[kMaxN + 1];
+  __shared__ int s_ncl;
+  const float ortol = 1e-4f * span;
+  const float eps_sep = 10.f * 1.2e-7f * span;
+  const float tiny = fmaxf(eps_sep * 1e-3f, pivmin);
   if (tid == 0) {
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int q = 0; q < kOAThreads / 32; ++q) { a += red[q][0]; b += red[q][1]; c = fmax(c, red[q][2]); }
-    s_delta = 2.0 * (sqrt(a) + c * sqrt(b));
-    s_amax = c;
-    w.misc[0] = s_delta;
-    w.misc[1] = (c > 0.0) ? (sqrt(a) / c + sqrt(b)) : sqrt(b);   // relative error estimate
+    int nc = 0;
+    cst[0] = 0;
+    for (int i = 1; i < r; ++i)
+      if (!(lam[i] - lam[i - 1] <= ortol)) cst[++nc] = i;
+    cst[++nc] = r;
+    s_ncl = nc;
   }
   __syncthreads();
-  if (mode == 2) return;
-  const double thr = fmax(s_delta, floor_rel * s_amax);
-  if (mode == 0) {
-    for (int q = tid; q < r * r; q += kOAThreads) {
-      const int i = q / r, j = q % r;
-      const double rij = (i == j ? 1.0 : 0.0) - Gs(i, j);
-      double e = 0.5 * rij;
-      if (i != j) {
-        const double li = w.lam[i], lj = w.lam[j];
-        if (fabs(li - lj) > thr) {
-          const double t = (Ss(i, j) + lj * rij) / (lj - li);
-          if (fabs(t) < kGuard) e = t;   // outside the convergence region: leave to clusters
+  float* pool = fsm + (zsmem ? 2 * r * r : r * r);
+  if (wid < slots) {
+    float* u0 = pool + wid * 4 * r;
+    float* u1 = u0 + r;
+    float* u2 = u1 + r;
+    float* ml = u2 + r;             // multiplier; its sign bit is not used, swaps are
+    unsigned* swp = reinterpret_cast<unsigned*>(pool + slots * 4 * r) + wid * ((r + 31) / 32);
+    for (int c = wid; c < s_ncl; c += slots) {
+      float xprev = -3.4e38f;
+      for (int jv = cst[c]; jv < cst[c + 1]; ++jv) {
+        float x = lam[jv];
+        if (jv > cst[c] && x - xprev < eps_sep) x = xprev + eps_sep;
+        xprev = x;
+        if (lane == 0) {            // LU with partial pivoting of T3 - x I
+          for (int q = 0; q < (r + 31) / 32; ++q) swp[q] = 0u;
+          float p0 = d[0] - x, p1 = (r > 1) ? e[0] : 0.f;
+          for (int jj = 0; jj + 1 < r; ++jj) {
+            const float bsub = e[jj], anext = d[jj + 1] - x, cnext = (jj + 2 < r) ? e[jj + 1] : 0.f;
+            float a0, a1, a2, m;
+            if (fabsf(bsub) > fabsf(p0)) {
+              a0 = bsub; a1 = anext; a2 = cnext;
+              swp[jj >> 5] |= 1u << (jj & 31);
+              m = p0 / bsub;
+              p0 = p1 - m * anext;
+              p1 = -m * cnext;
+            } else {
+              a0 = p0; a1 = p1; a2 = 0.f;
+              m = (p0 != 0.f) ? bsub / p0 : 0.f;
+              p0 = anext - m * p1;
+              p1 = cnext;
+            }
+            if (fabsf(a0) < tiny) a0 = (a0 < 0.f) ? -tiny : tiny;
+            u0[jj] = 1.f / a0; u1[jj] = a1; u2[jj] = a2; ml[jj] = m;   // reciprocal pivot
+          }
+          u0[r - 1] = 1.f / ((fabsf(p0) < tiny) ? ((p0 < 0.f) ? -tiny : tiny) : p0);
+          u1[r - 1] = 0.f; u2[r - 1] = 0.f;
+        }
+        for (int a = lane; a < r; a += 32) Z[a * r + jv] = 1.f / (1.f + (float)((a * 7 + jv * 13) % 17));
+        __syncwarp();
+        for (int itr = 0; itr < 2; ++itr) {
+          if (lane == 0) {
+            float* zc = Z + jv;
+            for (int jj = 0; jj + 1 < r; ++jj) {
+              if ((swp[jj >> 5] >> (jj & 31)) & 1u) {
+                const float t0 = zc[jj * r];
+                zc[jj * r] = zc[(jj + 1) * r];
+                zc[(jj + 1) * r] = t0 - ml[jj] * zc[jj * r];
+              } else {
+                zc[(jj + 1) * r] -= ml[jj] * zc[jj * r];
+              }
+            }
+            for (int a = r - 1; a >= 0; --a) {
+              float t = zc[a * r];
+              if (a + 1 < r) t -= u1[a] * zc[(a + 1) * r];
+              if (a + 2 < r) t -= u2[a] * zc[(a + 2) * r];
+              zc[a * r] = t * u0[a];
+            }
+          }
+          __syncwarp();
+          // scale first (the solve can grow the vector by 1/tiny), then orthogonalise
+          float mx = 0.f;
+          for (int a = lane; a < r; a += 32) mx = fmaxf(mx, fabsf(Z[a * r + jv]));
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          const float inv = (mx > 0.f) ? 1.f / mx : 0.f;
+          for (int a = lane; a < r; a += 32) Z[a * r + jv] *= inv;
+          __syncwarp();
+          for (int q = cst[c]; q < jv; ++q) {
+            float dot = 0.f;
+            for (int a = lane; a < r; a += 32) dot += Z[a * r + q] * Z[a * r + jv];
+            dot = warp_sumf(dot);
+            for (int a = lane; a < r; a += 32) Z[a * r + jv] -= dot * Z[a * r + q];
+            __syncwarp();
+          }
+          float nrm = 0.f;
+          for (int a = lane; a < r; a += 32) nrm += Z[a * r + jv] * Z[a * r + jv];
+          nrm = warp_sumf(nrm);
+          nrm = (nrm > 0.f) ? rsqrtf(nrm) : 0.f;
+          for (int a = lane; a < r; a += 32) Z[a * r + jv] *= nrm;
+          __syncwarp();
         }
       }
-      w.E[i * n + j] = e;
     }
-    return;
   }
-  // mode 1
-  for (int i = tid; i < r; i += kOAThreads) {
-    const double li = w.lam[i];
+  __syncthreads();
+  // --- back-transformation Z <- H_0 ... H_{r-3} Z; warp wid owns columns wid + 32 t
+  for (int c = wid; c < r; c += nwarps) {
+    for (int j = r - 3; j >= 0; --j) {
+      const float t = tau[j];
+      if (t == 0.f) continue;
+      float s = 0.f;
+      for (int a = j + 1 + lane; a < r; a += 32) s += ((a == j + 1) ? 1.f : A[a * r + j]) * Z[a * r + c];
+      s = t * warp_sumf(s);
+      for (int a = j + 1 + lane; a < r; a += 32) Z[a * r + c] -= s * ((a == j + 1) ? 1.f : A[a * r + j]);
+      __syncwarp();
+    }
+    for (int a = lane; a < r; a += 32) w.W[a * n + c] = (double)Z[a * r + c];
+  }
+}
+
+// ------------------------------------------------ 4. refinement (FP64) ---------
+// Products of r x r matrices (stride n) with kTile x kTile output tiles; the A row
+// panel and the B column panel are staged whole in shared memory.
+//   bmode 0: B read from memory;  1: B = E computed on the fly (Ogita-Aishima step;
+//   lam_i = s_ii / (2 - g_ii) and the threshold from the accumulated norms);
+//   2: B = E read from memory (cluster step).  With addD: C = D + op(A) B.
+//   acc_mode 1 (the G product): accumulate ||I - G||_F^2 into acc[1];
+//   acc_mode 2 (the S product): accumulate ||S - diag(lam)||_F^2 into acc[0] and
+//   max |lam| into acc[2] (as the bits of a non-negative double).
+struct GemmJob {
+  const double* A; const double* B; double* C; const double* D;
+  int ta, bmode, addD, acc_mode;
+};
+__device__ __forceinline__ double thr_from(const double* acc, double floor_rel) {
+  const double amax = __longlong_as_double((long long)((const unsigned long long*)acc)[2]);
+  return fmax(2.0 * (sqrt(acc[0]) + amax * sqrt(acc[1])), floor_rel * amax);
+}
+__global__ void __launch_bounds__(kTile * kTile)
+gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) {
+  extern __shared__ double gsm[];
+  __shared__ double red[2][2];
+  const GemmJob jb = blockIdx.z == 0 ? j0 : j1;
+  const int r = *w.rank;
+  const int row0 = blockIdx.y * kTile, col0 = blockIdx.x * kTile;
+  if (row0 >= r || col0 >= r) return;
+  double* As = gsm;                 // kTile x r
+  double* Bs = gsm + kTile * r;     // r x kTile
+  const int tid = threadIdx.x;
+  for (int q = tid; q < kTile * r; q += kTile * kTile) {
+    const int a = q / r, kq = q % r;
+    const int row = row0 + a;
+    As[q] = (row < r) ? (jb.ta ? jb.A[kq * n + row] : jb.A[row * n + kq]) : 0.0;
+  }
+  const double thr = (jb.bmode == 1) ? thr_from(acc, floor_rel) : 0.0;
+  for (int q = tid; q < r * kTile; q += kTile * kTile) {
+    const int kq = q / kTile, b = q % kTile;
+    const int col = col0 + b;
+    double v = 0.0;
+    if (col < r) {
+      if (jb.bmode == 0) {
+        v = jb.B[kq * n + col];
+      } else if (jb.bmode == 2) {
+        v = w.E[kq * n + col];
+      } else {
+        const double gs = 0.5 * (w.G[kq * n + col] + w.G[col * n + kq]);
+        const double rij = (kq == col ? 1.0 : 0.0) - gs;
+        v = 0.5 * rij;
+        if (kq != col) {
+          const double li = w.SS[kq * n + kq] / (2.0 - w.G[kq * n + kq]);
+          const double lj = w.SS[col * n + col] / (2.0 - w.G[col * n + col]);
+          if (fabs(li - lj) > thr) {
+            const double ss = 0.5 * (w.SS[kq * n + col] + w.SS[col * n + kq]);
+            const double t = (ss + lj * rij) / (lj - li);
+            if (fabs(t) < kGuard) v = t;
+          }
+        }
+      }
+    }
+    Bs[q] = v;
+  }
+  __syncthreads();
+  const int ty = tid / kTile, tx = tid % kTile;
+  const int row = row0 + ty, col = col0 + tx;
+  double a_acc = 0.0;
+  for (int kq = 0; kq < r; ++kq) a_acc = fma(As[ty * r + kq], Bs[kq * kTile + tx], a_acc);
+  const bool in = row < r && col < r;
+  if (in) jb.C[row * n + col] = jb.addD ? jb.D[row * n + col] + a_acc : a_acc;
+  if (jb.acc_mode) {
+    double c0 = 0.0, c1 = 0.0;
+    if (in) {
+      if (jb.acc_mode == 1) {
+        const double rij = (row == col ? 1.0 : 0.0) - a_acc;
+        c0 = rij * rij;
+      } else if (row == col) {
+        const double lam = a_acc / (2.0 - w.G[row * n + row]);
+        c0 = (a_acc - lam) * (a_acc - lam);
+        c1 = fabs(lam);
+      } else {
+        c0 = a_acc * a_acc;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      c0 += __shfl_xor_sync(0xffffffffu, c0, o);
+      c1 = fmax(c1, __shfl_xor_sync(0xffffffffu, c1, o));
+    }
+    if ((tid & 31) == 0) { red[tid >> 5][0] = c0; red[tid >> 5][1] = c1; }
+    __syncthreads();
+    if (tid == 0) {
+      const double s0 = red[0][0] + red[1][0], s1 = fmax(red[0][1], red[1][1]);
+      if (jb.acc_mode == 1) {
+        atomicAdd(acc + 1, s0);
+      } else {
+        atomicAdd(acc + 0, s0);
+        atomicMax((unsigned long long*)(acc + 2), (unsigned long long)__double_as_longlong(s1));
+      }
+    }
+  }
+}
+
+// Cluster formation for a cluster step: lam (Rayleigh quotients) sorted, chains of
+// gaps <= the threshold, E initialised to diag(r_ii / 2).
+__global__ void __launch_bounds__(kBig)
+coeff_kernel(int n, const double* acc, double floor_rel, DW w) {
+  __shared__ double sl[kMaxN];
+  const int r = *w.rank;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nwarps = kBig / 32;
+  const double thr = thr_from(acc, floor_rel);
+  for (int i = tid; i < r; i += kBig) sl[i] = w.SS[i * n + i] / (2.0 - w.G[i * n + i]);
+  for (int i = wid; i < r; i += nwarps)
+    for (int j = lane; j < r; j += 32) w.E[i * n + j] = (i == j) ? 0.5 * (1.0 - w.G[i * n + i]) : 0.0;
+  __syncthreads();
+  for (int i = tid; i < r; i += kBig) {
+    const double li = sl[i];
     int rk = 0;
     for (int j = 0; j < r; ++j) {
-      const double lj = w.lam[j];
+      const double lj = sl[j];
       rk += (lj < li || (lj == li && j < i)) ? 1 : 0;
     }
-    srt[rk] = i;
-  }
-  for (int q = tid; q < r * r; q += kOAThreads) {
-    const int i = q / r, j = q % r;
-    w.E[i * n + j] = (i == j) ? 0.5 * (1.0 - w.G[i * n + i]) : 0.0;
+    w.srt[rk] = i;
   }
   __syncthreads();
   if (tid == 0) {
     int nc = 0;
-    cl_start[nc++] = 0;
+    w.cl[1] = 0;
     for (int t = 1; t < r; ++t)
-      if (!(w.lam[srt[t]] - w.lam[srt[t - 1]] <= thr)) cl_start[nc++] = t;
-    cl_start[nc] = r;
-    s_ncl = nc;
+      if (!(sl[w.srt[t]] - sl[w.srt[t - 1]] <= thr)) w.cl[1 + (++nc)] = t;
+    ++nc;
+    w.cl[1 + nc] = r;
+    w.cl[0] = nc;
+  }
+}
+
+// One CTA per cluster: first-order orthonormalisation K = I + R_c / 2, exact FP64
+// Jacobi diagonalisation of K S_c K, E block = K V - I.
+constexpr int kClThreads = 256;
+__global__ void __launch_bounds__(kClThreads)
+cluster_kernel(int n, DW w) {
+  __shared__ double cK[kMaxCluster * kMaxCluster], cA[kMaxCluster * kMaxCluster],
+      cV[kMaxCluster * kMaxCluster];
+  __shared__ double ccs_c[kMaxCluster / 2], ccs_s[kMaxCluster / 2];
+  __shared__ int cpr_p[kMaxCluster / 2], cpr_q[kMaxCluster / 2];
+  __shared__ int idx[kMaxCluster];
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  if (c >= w.cl[0]) return;
+  const int b = w.cl[1 + c], mm = w.cl[2 + c] - b;
+  if (mm < 2 || mm > kMaxCluster) return;
+  const int tid = threadIdx.x;
+  for (int a = tid; a < mm; a += kClThreads) idx[a] = w.srt[b + a];
+  __syncthreads();
+  for (int q = tid; q < mm * mm; q += kClThreads) {
+    const int a = q / mm, e = q % mm;
+    const double gs = 0.5 * (w.G[idx[a] * n + idx[e]] + w.G[idx[e] * n + idx[a]]);
+    cK[q] = (a == e ? 1.5 : 0.0) - 0.5 * gs;
   }
   __syncthreads();
-  for (int c = 0; c < s_ncl; ++c) {
-    const int b = cl_start[c], mm = cl_start[c + 1] - b;
-    if (mm < 2 || mm > kMaxCluster) continue;   // singletons keep the normalisation
-    // K = I + R_c / 2 (first-order G_c^{-1/2});  cA = K S_c K
-    for (int q = tid; q < mm * mm; q += kOAThreads) {
-      const int a = q / mm, e = q % mm;
-      cK[q] = (a == e ? 1.5 : 0.0) - 0.5 * Gs(srt[b + a], srt[b + e]);
+  for (int q = tid; q < mm * mm; q += kClThreads) {    // cV = K S_c
+    const int a = q / mm, e = q % mm;
+    double s = 0.0;
+    for (int u = 0; u < mm; ++u)
+      s += cK[a * mm + u] * 0.5 * (w.SS[idx[u] * n + idx[e]] + w.SS[idx[e] * n + idx[u]]);
+    cV[q] = s;
+  }
+  __syncthreads();
+  for (int q = tid; q < mm * mm; q += kClThreads) {    // cA = (K S_c) K
+    const int a = q / mm, e = q % mm;
+    double s = 0.0;
+    for (int u = 0; u < mm; ++u) s += cV[a * mm + u] * cK[u * mm + e];
+    cA[q] = s;
+  }
+  __syncthreads();
+  for (int q = tid; q < mm * mm; q += kClThreads) {
+    const int a = q / mm, e = q % mm;
+    if (a < e) {
+      const double v = 0.5 * (cA[a * mm + e] + cA[e * mm + a]);
+      cA[a * mm + e] = v;
+      cA[e * mm + a] = v;
     }
-    __syncthreads();
-    for (int q = tid; q < mm * mm; q += kOAThreads) {   // cV = K S_c (temporary)
-      const int a = q / mm, e = q % mm;
-      double s = 0.0;
-      for (int u = 0; u < mm; ++u) s += cK[a * mm + u] * Ss(srt[b + u], srt[b + e]);
-      cV[q] = s;
+  }
+  __syncthreads();
+  for (int q = tid; q < mm * mm; q += kClThreads) cV[q] = (q / mm == q % mm) ? 1.0 : 0.0;
+  __syncthreads();
+  const int m2 = (mm % 2 == 0) ? mm : mm + 1;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    double off = 0.0, fro = 0.0;
+    for (int q = tid; q < mm * mm; q += kClThreads) {
+      const double v = cA[q];
+      fro += v * v;
+      if (q / mm != q % mm) off += v * v;
     }
-    __syncthreads();
-    for (int q = tid; q < mm * mm; q += kOAThreads) {
-      const int a = q / mm, e = q % mm;
-      double s = 0.0;
-      for (int u = 0; u < mm; ++u) s += cV[a * mm + u] * cK[u * mm + e];
-      cA[q] = s;
-    }
-    __syncthreads();
-    for (int q = tid; q < mm * mm; q += kOAThreads) {
-      const int a = q / mm, e = q % mm;
-      if (a < e) {
-        const double v = 0.5 * (cA[a * mm + e] + cA[e * mm + a]);
-        cA[a * mm + e] = v;
-        cA[e * mm + a] = v;
-      }
-    }
-    __syncthreads();
-    for (int q = tid; q < mm * mm; q += kOAThreads) cV[q] = (q / mm == q % mm) ? 1.0 : 0.0;
-    __syncthreads();
-    const int m2 = (mm % 2 == 0) ? mm : mm + 1;
-    for (int sweep = 0; sweep < 30; ++sweep) {
-      if (tid == 0) {
-        double off = 0.0, fro = 0.0;
-        for (int q = 0; q < mm * mm; ++q) {
-          fro += cA[q] * cA[q];
-          if (q / mm != q % mm) off += cA[q] * cA[q];
+    off = block_sum<double>(off, red);
+    fro = block_sum<double>(fro, red);
+    if (off <= 1e-32 * fro || fro == 0.0) break;
+    for (int step = 0; step < m2 - 1; ++step) {
+      if (tid < m2 / 2) {
+        const int i = tid;
+        auto player = [&](int t) { return t == 0 ? 0 : ((t - 1 + step) % (m2 - 1)) + 1; };
+        int p = player(i), q = player(m2 - 1 - i);
+        if (p > q) { const int t = p; p = q; q = t; }
+        double cc = 1.0, ss = 0.0;
+        if (q < mm) {
+          const double apq = cA[p * mm + q], app = cA[p * mm + p], aqq = cA[q * mm + q];
+          if (apq != 0.0) {
+            const double tau = (aqq - app) / (2.0 * apq);
+            const double t = (fabs(tau) > 1e150) ? 0.5 / tau
+                                                  : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            cc = 1.0 / sqrt(1.0 + t * t);
+            ss = t * cc;
+          }
         }
-        s_toff = off;
-        s_tfro = fro;
+        ccs_c[i] = cc; ccs_s[i] = ss; cpr_p[i] = p; cpr_q[i] = (q < mm && ss != 0.0) ? q : -1;
       }
       __syncthreads();
-      if (s_toff <= 1e-32 * s_tfro || s_tfro == 0.0) break;
-      for (int step = 0; step < m2 - 1; ++step) {
-        if (tid < m2 / 2) {
-          const int i = tid;
-          auto player = [&](int t) { return t == 0 ? 0 : ((t - 1 + step) % (m2 - 1)) + 1; };
-          int p = player(i), q = player(m2 - 1 - i);
-          if (p > q) { const int t = p; p = q; q = t; }
-          double cc = 1.0, ss = 0.0;
-          if (q < mm) {
-            const double apq = cA[p * mm + q], app = cA[p * mm + p], aqq = cA[q * mm + q];
-            if (apq != 0.0) {
-              const double tau = (aqq - app) / (2.0 * apq);
-              const double t = (fabs(tau) > 1e150) ? 0.5 / tau
-                                                    : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
-              cc = 1.0 / sqrt(1.0 + t * t);
-              ss = t * cc;
-            }
-          }
-          ccs_c[i] = cc; ccs_s[i] = ss; cpr_p[i] = p; cpr_q[i] = (q < mm && ss != 0.0) ? q : -1;
-        }
-        __syncthreads();
-        const int half = m2 / 2;
-        for (int it = tid; it < half * mm; it += kOAThreads) {
-          const int i = it / mm, col = it % mm;
-          const int q = cpr_q[i];
-          if (q < 0) continue;
-          const int p = cpr_p[i];
-          const double cc = ccs_c[i], ss = ccs_s[i];
-          const double ap = cA[p * mm + col], aq = cA[q * mm + col];
-          cA[p * mm + col] = cc * ap - ss * aq;
-          cA[q * mm + col] = ss * ap + cc * aq;
-        }
-        __syncthreads();
-        for (int it = tid; it < half * mm; it += kOAThreads) {
-          const int i = it / mm, row = it % mm;
-          const int q = cpr_q[i];
-          if (q < 0) continue;
-          const int p = cpr_p[i];
-          const double cc = ccs_c[i], ss = ccs_s[i];
-          const double ap = cA[row * mm + p], aq = cA[row * mm + q];
-          cA[row * mm + p] = cc * ap - ss * aq;
-          cA[row * mm + q] = ss * ap + cc * aq;
-          const double vp = cV[row * mm + p], vq = cV[row * mm + q];
-          cV[row * mm + p] = cc * vp - ss * vq;
-          cV[row * mm + q] = ss * vp + cc * vq;
-        }
-        __syncthreads();
+      const int half = m2 / 2;
+      for (int it = tid; it < half * mm; it += kClThreads) {
+        const int i = it / mm, col = it % mm;
+        const int q = cpr_q[i];
+        if (q < 0) continue;
+        const int p = cpr_p[i];
+        const double cc = ccs_c[i], ss = ccs_s[i];
+        const double ap = cA[p * mm + col], aq = cA[q * mm + col];
+        cA[p * mm + col] = cc * ap - ss * aq;
+        cA[q * mm + col] = ss * ap + cc * aq;
       }
+      __syncthreads();
+      for (int it = tid; it < half * mm; it += kClThreads) {
+        const int i = it / mm, row = it % mm;
+        const int q = cpr_q[i];
+        if (q < 0) continue;
+        const int p = cpr_p[i];
+        const double cc = ccs_c[i], ss = ccs_s[i];
+        const double ap = cA[row * mm + p], aq = cA[row * mm + q];
+        cA[row * mm + p] = cc * ap - ss * aq;
+        cA[row * mm + q] = ss * ap + cc * aq;
+        const double vp = cV[row * mm + p], vq = cV[row * mm + q];
+        cV[row * mm + p] = cc * vp - ss * vq;
+        cV[row * mm + q] = ss * vp + cc * vq;
+      }
+      __syncthreads();
     }
-    // F_c = K V ; E block = F_c - I (indices through srt)
-    for (int q = tid; q < mm * mm; q += kOAThreads) {
-      const int a = q / mm, e = q % mm;
-      double s = 0.0;
-      for (int u = 0; u < mm; ++u) s += cK[a * mm + u] * cV[u * mm + e];
-      w.E[srt[b + a] * n + srt[b + e]] = s - (a == e ? 1.0 : 0.0);
-    }
-    __syncthreads();
+  }
+  for (int q = tid; q < mm * mm; q += kClThreads) {
+    const int a = q / mm, e = q % mm;
+    double s = 0.0;
+    for (int u = 0; u < mm; ++u) s += cK[a * mm + u] * cV[u * mm + e];
+    w.E[idx[a] * n + idx[e]] = s - (a == e ? 1.0 : 0.0);
   }
 }
 
 // ------------------------------------------- 5. selection and back-transform --
-// order[0..k) = indices of the k smallest |lam| (ties: value, then index).
-__global__ void select_kernel(int k, DW w, double* __restrict__ theta) {
+__global__ void select_kernel(int k, int n, const double* acc, DW w, double* __restrict__ theta) {
   const int r = *w.rank;
   for (int c = threadIdx.x; c < k; c += blockDim.x) w.order[c] = 0;   // rank < k: stays in bounds
+  for (int i = threadIdx.x; i < r; i += blockDim.x) w.lam[i] = w.SS[i * n + i] / (2.0 - w.G[i * n + i]);
+  if (threadIdx.x == 0) {
+    const double amax = __longlong_as_double((long long)((const unsigned long long*)acc)[2]);
+    w.misc[1] = (amax > 0.0) ? sqrt(acc[0]) / amax + sqrt(acc[1]) : sqrt(acc[1]);
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     const double li = w.lam[i];
@@ -507,26 +714,43 @@ __global__ void select_kernel(int k, DW w, double* __restrict__ theta) {
   for (int c = threadIdx.x; c < k; c += blockDim.x) theta[c] = w.lam[w.order[c]];
 }
 
-// Z = L^{-T} W_sel (back substitution, one warp per selected column), then
-// Y[perm[i]][c] = d[perm[i]] Z[i][c] for i < r and 0 for the dropped rows.
-__global__ void backsub_kernel(int n, int k, DW w, double* __restrict__ Y) {
+// z = L^{-T} w_sel (one warp per selected column, z in shared memory), then
+// Y[perm[i]][c] = d[perm[i]] z[i] for i < r and 0 for the dropped rows.
+__global__ void __launch_bounds__(kTrsmWarps * 32)
+backsub_kernel(int n, int k, DW w, double* __restrict__ Y, int lsmem) {
+  extern __shared__ double lsm[];
+  __shared__ double zc[kTrsmWarps][kMaxN];
   const int r = *w.rank;
-  const int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double* L = w.L;
+  if (lsmem) {   // transposed: row i holds column i of L
+    for (int q = threadIdx.x; q < r * r; q += kTrsmWarps * 32) {
+      const int i = q / r, qq = q % r;
+      lsm[qq * r + i] = w.L[i * n + qq];
+    }
+    __syncthreads();
+    L = lsm;
+  }
+  const int c = blockIdx.x * kTrsmWarps + wid;
   if (c >= k) return;
+  double* z = zc[wid];
   const int* perm = w.perm;
   const int oc = w.order[c];
   for (int i = r - 1; i >= 0; --i) {
     double s = 0.0;
-    for (int q = i + 1 + lane; q < r; q += 32) s += w.L[perm[q] * n + i] * w.Z[q * n + c];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) w.Z[i * n + c] = (w.W[i * n + oc] - s) / w.L[perm[i] * n + i];
+    if (lsmem) {
+      const double* Lt = L + i * r;   // column i of L
+      for (int q = i + 1 + lane; q < r; q += 32) s += Lt[q] * z[q];
+    } else {
+      for (int q = i + 1 + lane; q < r; q += 32) s += L[q * n + i] * z[q];
+    }
+    s = warp_sum(s);
+    if (lane == 0) z[i] = (w.W[i * n + oc] - s) / (lsmem ? L[i * r + i] : L[i * n + i]);
     __syncwarp();
   }
   for (int i = lane; i < n; i += 32) {
     const int row = perm[i];
-    Y[row * k + c] = (i < r) ? w.d[row] * w.Z[i * n + c] : 0.0;
+    Y[row * k + c] = (i < r) ? w.d[row] * z[i] : 0.0;
   }
 }
 
@@ -547,84 +771,106 @@ DW carve(double* work, int n) {
   w.W2 = p; p += nn;
   w.G = p; p += nn;
   w.SS = p; p += nn;
-  w.E = p; p += nn;
   w.P = p; p += nn;
+  w.E = p; p += nn;
   w.d = p; p += n;
   w.lam = p; p += n;
-  w.misc = p; p += 8;
+  w.misc = p; p += 48;   // [0..8) scalars, [8..48) per-step norm accumulators
+  w.A32 = reinterpret_cast<float*>(p); p += nn / 2 + 1;
+  w.Z32 = reinterpret_cast<float*>(p); p += nn / 2 + 1;
   w.perm = reinterpret_cast<int*>(p); p += n / 2 + 1;
   w.order = reinterpret_cast<int*>(p); p += n / 2 + 1;
+  w.srt = reinterpret_cast<int*>(p); p += n / 2 + 1;
+  w.cl = reinterpret_cast<int*>(p); p += n / 2 + 2;
   w.rank = reinterpret_cast<int*>(p); p += 1;
   return w;
 }
 
-float* float_scratch(const DW& w) { return reinterpret_cast<float*>(w.rank + 2); }
-
-void gemm64(bool ta, const double* A, const double* B, double* C, double beta, const double* D,
-            const DW& w, int n, cudaStream_t s) {
-  dim3 grid((n + kT - 1) / kT, (n + kT - 1) / kT);
-  if (ta) gemm64_kernel<true><<<grid, kT * kT, 0, s>>>(-1, -1, -1, A, n, B, n, C, n, 1.0, beta, D, n, w.rank);
-  else    gemm64_kernel<false><<<grid, kT * kT, 0, s>>>(-1, -1, -1, A, n, B, n, C, n, 1.0, beta, D, n, w.rank);
-  check_launch("gemm64_kernel");
+void gemm(const GemmJob& j0, const GemmJob& j1, int nz, const DW& w, int n, double* acc, double floor_rel,
+          cudaStream_t s) {
+  dim3 grid((n + kTile - 1) / kTile, (n + kTile - 1) / kTile, nz);
+  const size_t smem = 2 * (size_t)kTile * n * sizeof(double);
+  gemm_kernel<<<grid, kTile * kTile, smem, s>>>(j0, j1, n, w, acc, floor_rel);
+  check_launch("gemm_kernel");
 }
 
 }  // namespace
 
 size_t dense_work_doubles(int n) {
-  // 10 n^2 blocks, d, lam, misc, perm, order, rank, then 2 n^2 floats for the Jacobi
-  return 10 * (size_t)n * n + 2 * (size_t)n + 8 + 2 * (size_t)(n / 2 + 1) + 1 + (size_t)n * n + 16;
+  const size_t nn = (size_t)n * n;
+  return 10 * nn + 2 * (size_t)n + 48 + 2 * (nn / 2 + 1) + 4 * ((size_t)n / 2 + 2) + 1 + 16;
 }
 
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k, double* theta,
                double* Y, int* rank, double* work, double* quality, cudaStream_t s) {
-  if (n < 1 || n > kMaxN || k < 1 || k > n) fail(BMG_ERR_INVALID_ARG, "dense_eig: need 1 <= k <= n <= 320");
+  if (n < 1 || n > kMaxDense || k < 1 || k > n) fail(BMG_ERR_INVALID_ARG, "dense_eig: need 1 <= k <= n <= 224");
   prof_begin(KC_DENSE, s);
   DW w = carve(work, n);
   // 1. basis
-  chol_kernel<<<1, kCholThreads, 0, s>>>(Mhat, n, w);
-  check_launch("chol_kernel");
+  const size_t smemS = (size_t)n * n * sizeof(double);
+  const bool useS = smemS <= 200 * 1024;
+  if (useS) BMG_CUDA(cudaFuncSetAttribute(basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemS));
+  basis_kernel<<<1, kBig, useS ? smemS : 0, s>>>(Mhat, n, w, useS ? 1 : 0);
+  check_launch("basis_kernel");
   // 2. reduced standard matrix
-  const int wpb = 8;
-  trsm_fwd_kernel<<<(n + wpb - 1) / wpb, 32 * wpb, 0, s>>>(Ahat, Mhat, n, sigma, 0, w);
-  check_launch("trsm_fwd_kernel");
-  trsm_fwd_kernel<<<(n + wpb - 1) / wpb, 32 * wpb, 0, s>>>(Ahat, Mhat, n, sigma, 1, w);
-  check_launch("trsm_fwd_kernel");
-  // 3. FP32 Jacobi
-  const size_t smem = 2 * (size_t)n * n * sizeof(float);
-  const bool use_smem = smem <= 200 * 1024;
-  if (use_smem)
-    BMG_CUDA(cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  // run to the FP32 resolution: the refinement needs eigenvectors good to ~1e-6 of
-  // the gaps it separates
-  jacobi32_kernel<<<1, kJacThreads, use_smem ? smem : 0, s>>>(n, use_smem ? 1 : 0, float_scratch(w), w, 10,
-                                                              2e-7f);
-  check_launch("jacobi32_kernel");
-  // 4. refinement schedule: steps separate pairs farther apart than a floor (relative
-  //    to max|lam|); cluster steps diagonalise the groups below it exactly.  The
-  //    floor starts at the FP32 resolution of W and is lowered once the separated
+  const int tb = (n + kTrsmWarps - 1) / kTrsmWarps;
+  const size_t lsm = (size_t)n * n * sizeof(double);
+  const bool lsmem = lsm <= 180 * 1024;
+  if (lsmem) {
+    BMG_CUDA(cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+    BMG_CUDA(cudaFuncSetAttribute(backsub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
+  }
+  trsm_kernel<<<tb, kTrsmWarps * 32, lsmem ? lsm : 0, s>>>(Ahat, Mhat, n, sigma, 0, w, lsmem ? 1 : 0);
+  check_launch("trsm_kernel");
+  trsm_kernel<<<tb, kTrsmWarps * 32, lsmem ? lsm : 0, s>>>(Ahat, Mhat, n, sigma, 1, w, lsmem ? 1 : 0);
+  check_launch("trsm_kernel");
+  // 3. FP32 eigensolve (A in shared memory; Z too when both fit)
+  //    (T in shared memory; the eigenvector block too when it fits; the rest of the
+  //    shared memory holds the LU factorisations of the inverse iteration)
+  const size_t a32 = (size_t)n * n * sizeof(float);
+  const size_t smax = 210 * 1024;
+  const size_t slot_bytes = 16 * (size_t)n + 4 * (((size_t)n + 31) / 32);   // 4 float rows + swap bits
+  const bool zs = 2 * a32 + 16 * slot_bytes <= smax;
+  const size_t base = zs ? 2 * a32 : a32;
+  const int slots = (int)std::max<size_t>(1, std::min<size_t>(kBig / 32, (smax - base) / slot_bytes));
+  const size_t esm = base + slot_bytes * slots;
+  BMG_CUDA(cudaFuncSetAttribute(eig32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+  eig32_kernel<<<1, kBig, esm, s>>>(n, zs ? 1 : 0, slots, w);
+  check_launch("eig32_kernel");
+  // 4. refinement: steps separate pairs farther apart than a floor (relative to
+  //    max|lam|); cluster steps diagonalise the groups below it exactly.  The floor
+  //    starts at the resolution of the FP32 start and is lowered once the separated
   //    pairs converged; pairs closer than 1e-10 max|lam| are left to the cluster
   //    steps (their computed couplings are rounding noise).
+  const size_t gsm = 2 * (size_t)kTile * n * sizeof(double);
+  if (gsm > 48 * 1024)
+    BMG_CUDA(cudaFuncSetAttribute(gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm));
   const int nsteps = 7;
   const int modes[nsteps] = {0, 0, 1, 0, 0, 1, 0};
   const double floors[nsteps] = {kClusterFloor, kClusterFloor, kClusterFloor, 1e-7, 1e-7, 1e-7, 1e-10};
-  for (int it = 0; it < nsteps; ++it) {
-    gemm64(false, w.T, w.W, w.P, 0.0, nullptr, w, n, s);    // P = T W
-    gemm64(true, w.W, w.P, w.SS, 0.0, nullptr, w, n, s);    // SS = W^T P
-    gemm64(true, w.W, w.W, w.G, 0.0, nullptr, w, n, s);     // G = W^T W
-    oa_kernel<<<1, kOAThreads, 0, s>>>(n, modes[it], floors[it], w);
-    check_launch("oa_kernel");
-    gemm64(false, w.W, w.E, w.W2, 1.0, w.W, w, n, s);       // W2 = W + W E
+  double* accs = w.misc + 8;   // 3 doubles per step
+  BMG_CUDA(cudaMemsetAsync(accs, 0, sizeof(double) * 3 * (nsteps + 1), s));
+  for (int it = 0; it <= nsteps; ++it) {
+    double* acc = accs + 3 * it;
+    // P = T W and G = W^T W in one launch (G accumulates ||I - G||), then SS = W^T P
+    gemm({w.T, w.W, w.P, nullptr, 0, 0, 0, 0}, {w.W, w.W, w.G, nullptr, 1, 0, 0, 1}, 2, w, n, acc, 0.0, s);
+    gemm({w.W, w.P, w.SS, nullptr, 1, 0, 0, 2}, {}, 1, w, n, acc, 0.0, s);
+    if (it == nsteps) break;
+    if (modes[it] == 1) {
+      coeff_kernel<<<1, kBig, 0, s>>>(n, acc, floors[it], w);
+      check_launch("coeff_kernel");
+      cluster_kernel<<<n, kClThreads, 0, s>>>(n, w);
+      check_launch("cluster_kernel");
+    }
+    // W2 = W + W E  (E on the fly, or from the cluster step)
+    gemm({w.W, nullptr, w.W2, w.W, 0, modes[it] == 1 ? 2 : 1, 1, 0}, {}, 1, w, n, acc, floors[it], s);
     std::swap(w.W, w.W2);
   }
-  gemm64(false, w.T, w.W, w.P, 0.0, nullptr, w, n, s);
-  gemm64(true, w.W, w.P, w.SS, 0.0, nullptr, w, n, s);
-  gemm64(true, w.W, w.W, w.G, 0.0, nullptr, w, n, s);
-  oa_kernel<<<1, kOAThreads, 0, s>>>(n, 2, 0.0, w);
-  check_launch("oa_kernel");
   // 5. selection and back-transform
-  select_kernel<<<1, 512, 0, s>>>(k, w, theta);
+  select_kernel<<<1, 512, 0, s>>>(k, n, accs + 3 * nsteps, w, theta);
   check_launch("select_kernel");
-  backsub_kernel<<<(k + wpb - 1) / wpb, 32 * wpb, 0, s>>>(n, k, w, Y);
+  backsub_kernel<<<(k + kTrsmWarps - 1) / kTrsmWarps, kTrsmWarps * 32, lsmem ? lsm : 0, s>>>(n, k, w, Y,
+                                                                                         lsmem ? 1 : 0);
   check_launch("backsub_kernel");
   copy_out_kernel<<<1, 1, 0, s>>>(w, rank, quality);
   check_launch("copy_out_kernel");
