@@ -42,15 +42,25 @@ constexpr int kTile = 8;                 // output tile of the refinement produc
 
 // Scratch carved from one device allocation; n x n blocks row-major with stride n.
 struct DW {
-  double *S, *L, *T, *Z, *W, *W2, *G, *SS, *P, *E, *d, *lam, *misc;
-  float *A32, *Z32;
+  double *S, *L, *Lt, *T, *Z, *W, *W2, *G, *SS, *P, *E, *d, *rl, *lam, *misc;
+  float *A32, *Z32, *LU32;
   int *perm, *order, *rank, *srt, *cl;
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+// 1/x to about 1e-14 relative: an FP32 seed refined by one Newton-Raphson step
+// y <- y (2 - x y) in FP64 (the relative error squares).  For |x| within the FP32
+// range; the callers pass differences of Rayleigh quotients that are well inside it.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const double y = (double)(1.0f / (float)x);
+  return y * fma(-x, y, 2.0);
+}
+// 1/sqrt(x) for x in [1, 2]: FP32 seed and two Newton-Raphson steps
+// y <- y (3 - x y^2) / 2 in FP64.
+__device__ __forceinline__ double rsqrt_nr12(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  return y;
 }
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
@@ -75,18 +85,28 @@ __device__ T block_sum(T v, T* red) {
 
 // ------------------------------------------------ 1. basis (pivoted Cholesky) --
 // Symmetric pivoting is done physically on the upper triangle of S (row j holds
-// S[j][j..n)), so every step reads and writes contiguous rows.  L is written in pivot
-// order: L[i][q] for pivot position i and step q <= i (rows swapped with the pivots).
+// S[j][j..n)), so every step reads and writes contiguous rows.  The factor is written
+// in pivot order twice, as L (row i holds L[i][0..i]) and as Lt (row q holds column q
+// of L), with the reciprocal pivots 1 / L[q][q] in rl; rows of the part computed so
+// far are swapped with the pivots.  FP64 arithmetic is scarce on this GPU, so the
+// pivot search compares the bit patterns of the (non-negative) diagonal as integers
+// and one thread computes the square root and the reciprocal of each pivot.
+__device__ __forceinline__ unsigned long long pivot_key(double v) {
+  const long long b = __double_as_longlong(v);
+  // positive finite values and +inf order like their bit patterns; 0, negatives and
+  // NaN get key 0 and are never chosen above a positive value
+  return (b > 0 && b <= 0x7FF0000000000000LL) ? (unsigned long long)b : 0ull;
+}
 __global__ void __launch_bounds__(kBig)
 basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS) {
   extern __shared__ double dsm[];
   double* S = smemS ? dsm : w.S;
-  __shared__ double wv[32];
+  __shared__ unsigned long long wk[32];
   __shared__ int wi[32];
   __shared__ int perm[kMaxN];
   __shared__ double d[kMaxN], lcol[kMaxN];
-  __shared__ int s_rank, s_p;
-  __shared__ double s_piv;
+  __shared__ int s_rank, s_p, s_go;
+  __shared__ double s_l, s_rl;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = kBig / 32;
   for (int i = tid; i < n; i += kBig) {
@@ -97,43 +117,52 @@ basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS) {
   __syncthreads();
   for (int i = wid; i < n; i += nwarps)
     for (int j = lane; j < n; j += 32) {
-      S[i * n + j] = 0.5 * (Mhat[i * n + j] + Mhat[j * n + i]) * d[i] * d[j];
+      S[i * n + j] = 0.5 * (Mhat[i * n + j] + Mhat[j * n + i]) * (d[i] * d[j]);
       w.L[i * n + j] = 0.0;
+      w.Lt[i * n + j] = 0.0;
     }
   if (tid == 0) s_rank = n;
   __syncthreads();
   for (int j = 0; j < n; ++j) {
-    double best = -1.0;
+    unsigned long long best = 0ull;
     int bi = j;
     for (int i = j + tid; i < n; i += kBig) {
-      const double v = S[i * n + i];
-      if (v > best || (v == best && i < bi)) { best = v; bi = i; }
+      const unsigned long long key = pivot_key(S[i * n + i]);
+      if (key > best) { best = key; bi = i; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, best, o);
       const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+      if (k2 > best || (k2 == best && i2 < bi)) { best = k2; bi = i2; }
     }
-    if (lane == 0) { wv[wid] = best; wi[wid] = bi; }
+    if (lane == 0) { wk[wid] = best; wi[wid] = bi; }
     __syncthreads();
     if (wid == 0) {
-      best = wv[lane];
+      best = wk[lane];
       bi = wi[lane];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
-        const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, best, o);
         const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (v2 > best || (v2 == best && i2 < bi)) { best = v2; bi = i2; }
+        if (k2 > best || (k2 == best && i2 < bi)) { best = k2; bi = i2; }
       }
       if (lane == 0) {
-        s_piv = best;
+        const double piv = __longlong_as_double((long long)best);
+        const int go = piv > kDropTol;
+        s_go = go;
         s_p = bi;
-        if (!(best > kDropTol)) s_rank = j;   // NaN fails the test too
+        if (go) {
+          s_l = sqrt(piv);
+          s_rl = 1.0 / s_l;
+          w.rl[j] = s_rl;
+        } else {
+          s_rank = j;
+        }
       }
     }
     __syncthreads();
-    if (!(s_piv > kDropTol)) break;
+    if (!s_go) break;
     const int p = s_p;
     if (p != j) {
       // symmetric swap of indices j < p in upper-triangle storage
@@ -149,16 +178,18 @@ basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS) {
         }
         if (x < j) {   // rows j and p of the factor computed so far
           const double t = w.L[j * n + x]; w.L[j * n + x] = w.L[p * n + x]; w.L[p * n + x] = t;
+          const double u = w.Lt[x * n + j]; w.Lt[x * n + j] = w.Lt[x * n + p]; w.Lt[x * n + p] = u;
         }
       }
       if (tid == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
     }
     __syncthreads();
-    const double ljj = sqrt(s_piv), rl = 1.0 / ljj;
+    const double ljj = s_l, rl = s_rl;
     for (int i = j + tid; i < n; i += kBig) {
       const double v = (i == j) ? ljj : S[j * n + i] * rl;
       lcol[i] = v;
       w.L[i * n + j] = v;
+      w.Lt[j * n + i] = v;
     }
     __syncthreads();
     for (int a = j + 1 + wid; a < n; a += nwarps) {   // upper triangle of the trailing block
@@ -173,53 +204,65 @@ basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS) {
 }
 
 // ---------------------------------------- 2. T = L^{-1} C L^{-T} (FP64, warps) --
+// Forward substitution, one warp (and one CTA, to spread the FP64 work over the SMs)
+// per right-hand side c; lane l keeps the running values of rows l, l + 32, ... in
+// registers and, once z_i is known, subtracts column i of L (a contiguous row of Lt)
+// times z_i from them.
 // pass 0: Z = L^{-1} C, C[i][c] = d_a sym(Ahat - sigma Mhat)_ab d_b with a = perm[i],
-// b = perm[c];  pass 1: T = L^{-1} Z^T.  One warp per column c.
-constexpr int kTrsmWarps = 8;
-__global__ void __launch_bounds__(kTrsmWarps * 32)
+// b = perm[c];  pass 1: T = L^{-1} Z^T.
+constexpr int kRowsPerLane = kMaxDense / 32;   // rows per lane for rank <= 224
+__global__ void __launch_bounds__(32)
 trsm_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mhat, int n, double sigma,
-            int pass, DW w, int lsmem) {
-  extern __shared__ double lsm[];
-  __shared__ double zc[kTrsmWarps][kMaxN];
+            int pass, DW w) {
   const int r = *w.rank;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const double* L = w.L;
-  if (lsmem) {   // the leading r x r block of L, rows in pivot order
-    for (int q = threadIdx.x; q < r * r; q += kTrsmWarps * 32) lsm[q] = w.L[(q / r) * n + (q % r)];
-    __syncthreads();
-    L = lsm;
-  }
-  const int ldl = lsmem ? r : n;
-  const int c = blockIdx.x * kTrsmWarps + wid;
+  const int lane = threadIdx.x;
+  const int c = blockIdx.x;
   if (c >= r) return;
-  double* z = zc[wid];
+  double acc[kRowsPerLane];
   const int* perm = w.perm;
-  for (int i = 0; i < r; ++i) {
-    const double* Li = L + i * ldl;
-    double s = 0.0;
-    for (int q = lane; q < i; q += 32) s += Li[q] * z[q];
-    s = warp_sum(s);
-    if (lane == 0) {
-      double rhs;
+#pragma unroll
+  for (int t = 0; t < kRowsPerLane; ++t) {
+    const int q = lane + 32 * t;
+    double v = 0.0;
+    if (q < r) {
       if (pass == 0) {
-        const int a = perm[i], b = perm[c];
+        const int a = perm[q], b = perm[c];
         const double aij = 0.5 * (Ahat[a * n + b] + Ahat[b * n + a]);
         const double mij = 0.5 * (Mhat[a * n + b] + Mhat[b * n + a]);
-        rhs = (aij - sigma * mij) * w.d[a] * w.d[b];
+        v = (aij - sigma * mij) * (w.d[a] * w.d[b]);
       } else {
-        rhs = w.Z[c * n + i];
+        v = w.Z[c * n + q];
       }
-      z[i] = (rhs - s) / Li[i];
     }
-    __syncwarp();
+    acc[t] = v;
+  }
+  for (int i = 0; i < r; ++i) {
+    const int ti = i >> 5, own = i & 31;
+    double zi = 0.0;
+#pragma unroll
+    for (int t = 0; t < kRowsPerLane; ++t)
+      if (t == ti && lane == own) { acc[t] *= w.rl[i]; zi = acc[t]; }
+    zi = __shfl_sync(0xffffffffu, zi, own);
+    const double* Lc = w.Lt + i * n;   // column i of L
+#pragma unroll
+    for (int t = 0; t < kRowsPerLane; ++t) {
+      if (32 * t + 31 > i && 32 * t < r) {   // warp-uniform
+        const int q = lane + 32 * t;
+        if (q > i && q < r) acc[t] = fma(-Lc[q], zi, acc[t]);
+      }
+    }
   }
   double* out = pass == 0 ? w.Z : w.T;
-  for (int i = lane; i < r; i += 32) out[i * n + c] = z[i];
+#pragma unroll
+  for (int t = 0; t < kRowsPerLane; ++t) {
+    const int q = lane + 32 * t;
+    if (q < r) out[q * n + c] = acc[t];
+  }
 }
 
 // ---------------------------------------------- 3. FP32 eigensolve (1 CTA) -----
 __global__ void __launch_bounds__(kBig)
-eig32_kernel(int n, int zsmem, int slots, DW w) {
+eig32_kernel(int n, int zsmem, DW w) {
   extern __shared__ float fsm[];
   __shared__ float d[kMaxN], e[kMaxN], e2[kMaxN], tau[kMaxN], vb[kMaxN], pv[kMaxN], lam[kMaxN];
   __shared__ float redf[32], slo[32], shi[32];
@@ -299,114 +342,173 @@ eig32_kernel(int n, int zsmem, int slots, DW w) {
   for (int q = 1; q < nwarps; ++q) { lo = fminf(lo, slo[q]); hi = fmaxf(hi, shi[q]); }
   const float span = fmaxf(fmaxf(fabsf(lo), fabsf(hi)), 1e-30f);
   const float pivmin = 1e-30f * fmaxf(span * span, 1.f);
-  // --- bisection: thread i finds the i-th smallest eigenvalue
-  for (int i = tid; i < r; i += kBig) {
-    float a = lo - 1e-6f * span, b = hi + 1e-6f * span;
-    for (int it = 0; it < 64; ++it) {
-      const float x = 0.5f * (a + b);
-      if (!(b - a > 2.4e-7f * fmaxf(fabsf(a), fabsf(b)) + 1e-30f) || x == a || x == b) break;
-      int cnt = 0;
-      float q = d[0] - x;
-      if (fabsf(q) < pivmin) q = -pivmin;
-      cnt += q < 0.f;
-      for (int jj = 1; jj < r; ++jj) {
-        q = (d[jj] - x) - __fdividef(e2[jj - 1], q);
+  // --- eigenvalues by multisection of the Sturm count: a group of 8 lanes brackets
+  // one eigenvalue; each lane counts the eigenvalues below one of 8 interior points
+  // of the group's interval, which splits it into 9 parts.  8 rounds shrink the
+  // Gershgorin interval by 9^8 = 4.3e7, to the FP32 resolution of the spectrum
+  // (eigenvalues near 0 need no more: the refinement takes them to FP64).
+  {
+    const int grp = tid >> 3, sl = tid & 7;
+    const int gsh = lane & 24;
+    const float frac = (float)(sl + 1) * (1.0f / 9.0f);
+    for (int i0 = 0; i0 < r; i0 += kBig / 8) {
+      const int i = i0 + grp;
+      float a = lo - 1e-6f * span, b = hi + 1e-6f * span;
+      for (int round = 0; round < 8; ++round) {
+        const float wd = b - a;
+        const float x = fmaf(wd, frac, a);
+        int cnt = 0;
+        float q = d[0] - x;
         if (fabsf(q) < pivmin) q = -pivmin;
         cnt += q < 0.f;
+        for (int jj = 1; jj < r; ++jj) {
+          q = (d[jj] - x) - __fdividef(e2[jj - 1], q);
+          if (fabsf(q) < pivmin) q = -pivmin;
+          cnt += q < 0.f;
+        }
+        // counts grow with x: the first point with more than i eigenvalues below it
+        const unsigned m = (__ballot_sync(0xffffffffu, cnt > i) >> gsh) & 0xffu;
+        const int first = m ? __ffs(m) - 1 : 8;
+        const float na = (first == 0) ? a : fmaf(wd, (float)first * (1.0f / 9.0f), a);
+        const float nb = (first == 8) ? b : fmaf(wd, (float)(first + 1) * (1.0f / 9.0f), a);
+        a = na;
+        b = nb;
       }
-      if (cnt > i) b = x; else a = x;
+      if (sl == 0 && i < r) lam[i] = 0.5f * (a + b);
     }
-    lam[i] = 0.5f * (a + b);
   }
   __syncthreads();
-  // --- inverse iteration (the scheme of LAPACK's stein): clusters are chains of
-  // eigenvalues closer than 1e-4 span.  Each warp takes clusters w, w + nwarps, ...;
-  // inside a cluster the members run in order, each with its own shift (kept at
-  // least eps_sep above the previous one), two solves of (T3 - x I) z = z, and
-  // after every solve modified Gram-Schmidt against the earlier members (all lanes).
-  // Lane 0 does the tridiagonal factorisation and the solves; the factors live in a
-  // per-warp slot of shared memory.
+  // --- inverse iteration, block form of the scheme of LAPACK's stein.  Clusters are
+  // chains of eigenvalues closer than 1e-4 span; members of a cluster get shifts at
+  // least eps_sep apart.  Thread j factors T3 - x_j I (LU with partial pivoting, the
+  // factors in global scratch, planes [5][row][j]) and solves for column j of Z; after
+  // each of the two solves the columns are scaled by their largest entry, and one
+  // warp per cluster orthonormalises the members in order (modified Gram-Schmidt).
+  // All eigenvectors advance together, so the sequential work is one factorisation
+  // and two solves of length r, not one per member of the largest cluster.
   __shared__ int cst[kMaxN + 1];
   __shared__ int s_ncl;
   const float ortol = 1e-4f * span;
   const float eps_sep = 10.f * 1.2e-7f * span;
   const float tiny = fmaxf(eps_sep * 1e-3f, pivmin);
+  float* shift = vb;   // the tridiagonalisation is done with vb
   if (tid == 0) {
     int nc = 0;
     cst[0] = 0;
-    for (int i = 1; i < r; ++i)
-      if (!(lam[i] - lam[i - 1] <= ortol)) cst[++nc] = i;
+    float xprev = -3.4e38f;
+    for (int i = 0; i < r; ++i) {
+      float x = lam[i];
+      if (i > 0 && !(lam[i] - lam[i - 1] <= ortol)) cst[++nc] = i;
+      else if (i > 0 && x - xprev < eps_sep) x = xprev + eps_sep;
+      shift[i] = x;
+      xprev = x;
+    }
     cst[++nc] = r;
     s_ncl = nc;
   }
   __syncthreads();
-  float* pool = fsm + (zsmem ? 2 * r * r : r * r);
-  if (wid < slots) {
-    float* u0 = pool + wid * 4 * r;
-    float* u1 = u0 + r;
-    float* u2 = u1 + r;
-    float* ml = u2 + r;             // multiplier; its sign bit is not used, swaps are
-    unsigned* swp = reinterpret_cast<unsigned*>(pool + slots * 4 * r) + wid * ((r + 31) / 32);
-    for (int c = wid; c < s_ncl; c += slots) {
-      float xprev = -3.4e38f;
-      for (int jv = cst[c]; jv < cst[c + 1]; ++jv) {
-        float x = lam[jv];
-        if (jv > cst[c] && x - xprev < eps_sep) x = xprev + eps_sep;
-        xprev = x;
-        if (lane == 0) {            // LU with partial pivoting of T3 - x I
-          for (int q = 0; q < (r + 31) / 32; ++q) swp[q] = 0u;
-          float p0 = d[0] - x, p1 = (r > 1) ? e[0] : 0.f;
-          for (int jj = 0; jj + 1 < r; ++jj) {
-            const float bsub = e[jj], anext = d[jj + 1] - x, cnext = (jj + 2 < r) ? e[jj + 1] : 0.f;
-            float a0, a1, a2, m;
-            if (fabsf(bsub) > fabsf(p0)) {
-              a0 = bsub; a1 = anext; a2 = cnext;
-              swp[jj >> 5] |= 1u << (jj & 31);
-              m = p0 / bsub;
-              p0 = p1 - m * anext;
-              p1 = -m * cnext;
-            } else {
-              a0 = p0; a1 = p1; a2 = 0.f;
-              m = (p0 != 0.f) ? bsub / p0 : 0.f;
-              p0 = anext - m * p1;
-              p1 = cnext;
-            }
-            if (fabsf(a0) < tiny) a0 = (a0 < 0.f) ? -tiny : tiny;
-            u0[jj] = 1.f / a0; u1[jj] = a1; u2[jj] = a2; ml[jj] = m;   // reciprocal pivot
-          }
-          u0[r - 1] = 1.f / ((fabsf(p0) < tiny) ? ((p0 < 0.f) ? -tiny : tiny) : p0);
-          u1[r - 1] = 0.f; u2[r - 1] = 0.f;
+  {
+    const size_t pl = (size_t)r * r;
+    float* __restrict__ LU = w.LU32;
+    if (tid < r) {
+      const int jv = tid;
+      const float x = shift[jv];
+      float p0 = d[0] - x, p1 = (r > 1) ? e[0] : 0.f;
+      for (int jj = 0; jj + 1 < r; ++jj) {
+        const float bsub = e[jj], anext = d[jj + 1] - x, cnext = (jj + 2 < r) ? e[jj + 1] : 0.f;
+        float a0, a1, a2, m, sw;
+        if (fabsf(bsub) > fabsf(p0)) {
+          a0 = bsub; a1 = anext; a2 = cnext; sw = 1.f;
+          m = __fdividef(p0, bsub);
+          p0 = p1 - m * anext;
+          p1 = -m * cnext;
+        } else {
+          a0 = p0; a1 = p1; a2 = 0.f; sw = 0.f;
+          m = (p0 != 0.f) ? __fdividef(bsub, p0) : 0.f;
+          p0 = anext - m * p1;
+          p1 = cnext;
         }
-        for (int a = lane; a < r; a += 32) Z[a * r + jv] = 1.f / (1.f + (float)((a * 7 + jv * 13) % 17));
-        __syncwarp();
-        for (int itr = 0; itr < 2; ++itr) {
-          if (lane == 0) {
-            float* zc = Z + jv;
-            for (int jj = 0; jj + 1 < r; ++jj) {
-              if ((swp[jj >> 5] >> (jj & 31)) & 1u) {
-                const float t0 = zc[jj * r];
-                zc[jj * r] = zc[(jj + 1) * r];
-                zc[(jj + 1) * r] = t0 - ml[jj] * zc[jj * r];
+        if (fabsf(a0) < tiny) a0 = (a0 < 0.f) ? -tiny : tiny;
+        const size_t o = (size_t)jj * r + jv;
+        LU[o] = __frcp_rn(a0);
+        LU[pl + o] = a1;
+        LU[2 * pl + o] = a2;
+        LU[3 * pl + o] = m;
+        LU[4 * pl + o] = sw;
+      }
+      const size_t o = (size_t)(r - 1) * r + jv;
+      LU[o] = __frcp_rn((fabsf(p0) < tiny) ? ((p0 < 0.f) ? -tiny : tiny) : p0);
+      LU[pl + o] = 0.f;
+      LU[2 * pl + o] = 0.f;
+      for (int a = 0; a < r; ++a) Z[a * r + jv] = 1.f / (1.f + (float)((a * 7 + jv * 13) % 17));
+    }
+    for (int itr = 0; itr < 2; ++itr) {
+      if (tid < r) {
+        const int jv = tid;
+        float* Zc = Z + jv;
+        // forward elimination with the row swaps; cur carries the updated z[jj]
+        float cur = Zc[0];
+        for (int j0 = 0; j0 + 1 < r; j0 += 8) {
+          float mv[8], sv[8], nx[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int jj = j0 + u;
+            if (jj + 1 < r) {
+              const size_t o = (size_t)jj * r + jv;
+              mv[u] = LU[3 * pl + o];
+              sv[u] = LU[4 * pl + o];
+              nx[u] = Zc[(jj + 1) * r];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int jj = j0 + u;
+            if (jj + 1 < r) {
+              if (sv[u] != 0.f) {
+                Zc[jj * r] = nx[u];
+                cur = cur - mv[u] * nx[u];
               } else {
-                zc[(jj + 1) * r] -= ml[jj] * zc[jj * r];
+                Zc[jj * r] = cur;
+                cur = nx[u] - mv[u] * cur;
               }
             }
-            for (int a = r - 1; a >= 0; --a) {
-              float t = zc[a * r];
-              if (a + 1 < r) t -= u1[a] * zc[(a + 1) * r];
-              if (a + 2 < r) t -= u2[a] * zc[(a + 2) * r];
-              zc[a * r] = t * u0[a];
+          }
+        }
+        Zc[(r - 1) * r] = cur;
+        // back substitution with the upper factor (three diagonals)
+        float z1 = 0.f, z2 = 0.f, mx = 0.f;
+        for (int a1 = r - 1; a1 >= 0; a1 -= 4) {
+          float u0v[4], u1v[4], u2v[4], zv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int a = a1 - u;
+            if (a >= 0) {
+              const size_t o = (size_t)a * r + jv;
+              u0v[u] = LU[o];
+              u1v[u] = LU[pl + o];
+              u2v[u] = LU[2 * pl + o];
+              zv[u] = Zc[a * r];
             }
           }
-          __syncwarp();
-          // scale first (the solve can grow the vector by 1/tiny), then orthogonalise
-          float mx = 0.f;
-          for (int a = lane; a < r; a += 32) mx = fmaxf(mx, fabsf(Z[a * r + jv]));
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-          const float inv = (mx > 0.f) ? 1.f / mx : 0.f;
-          for (int a = lane; a < r; a += 32) Z[a * r + jv] *= inv;
-          __syncwarp();
+          for (int u = 0; u < 4; ++u) {
+            const int a = a1 - u;
+            if (a >= 0) {
+              const float t = (zv[u] - u1v[u] * z1 - u2v[u] * z2) * u0v[u];
+              Zc[a * r] = t;
+              z2 = z1;
+              z1 = t;
+              mx = fmaxf(mx, fabsf(t));
+            }
+          }
+        }
+        // scale first (the solve can grow the vector by 1/tiny)
+        const float inv = (mx > 0.f) ? 1.f / mx : 0.f;
+        for (int a = 0; a < r; ++a) Zc[a * r] *= inv;
+      }
+      __syncthreads();
+      for (int c = wid; c < s_ncl; c += nwarps) {
+        for (int jv = cst[c]; jv < cst[c + 1]; ++jv) {
           for (int q = cst[c]; q < jv; ++q) {
             float dot = 0.f;
             for (int a = lane; a < r; a += 32) dot += Z[a * r + q] * Z[a * r + jv];
@@ -422,21 +524,56 @@ eig32_kernel(int n, int zsmem, int slots, DW w) {
           __syncwarp();
         }
       }
+      __syncthreads();
     }
   }
-  __syncthreads();
-  // --- back-transformation Z <- H_0 ... H_{r-3} Z; warp wid owns columns wid + 32 t
-  for (int c = wid; c < r; c += nwarps) {
-    for (int j = r - 3; j >= 0; --j) {
-      const float t = tau[j];
-      if (t == 0.f) continue;
-      float s = 0.f;
-      for (int a = j + 1 + lane; a < r; a += 32) s += ((a == j + 1) ? 1.f : A[a * r + j]) * Z[a * r + c];
-      s = t * warp_sumf(s);
-      for (int a = j + 1 + lane; a < r; a += 32) Z[a * r + c] -= s * ((a == j + 1) ? 1.f : A[a * r + j]);
-      __syncwarp();
+  // --- back-transformation W = H_0 ... H_{r-3} Z.  A half-warp owns one column (two
+  // columns per warp); lane g of the half keeps rows g, g + 16, ... of it in
+  // registers, so applying a reflector takes one pass over the stored vector (kept
+  // in registers too) and a 4-step shuffle sum.  The result goes to W in FP64.
+  {
+    constexpr int RQ = kMaxDense / 16;
+    const int g = lane & 15, sub = lane >> 4;
+    for (int c0 = 2 * wid; c0 < r; c0 += 2 * nwarps) {
+      const int c = c0 + sub;
+      const bool cv = c < r;
+      float z[RQ];
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) {
+        const int a = g + 16 * q;
+        z[q] = (cv && a < r) ? Z[a * r + c] : 0.f;
+      }
+      for (int j = r - 3; j >= 0; --j) {
+        const float t = tau[j];
+        if (t == 0.f) continue;
+        float s0 = 0.f, s1 = 0.f, v[RQ];
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+          v[q] = 0.f;
+          if (16 * q + 15 > j && 16 * q < r) {   // warp-uniform
+            const int a = g + 16 * q;
+            v[q] = (a == j + 1) ? 1.f : ((a > j + 1 && a < r) ? A[a * r + j] : 0.f);
+            if (q & 1) s1 = fmaf(v[q], z[q], s1); else s0 = fmaf(v[q], z[q], s0);
+          }
+        }
+        float s = s0 + s1;
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        s += __shfl_xor_sync(0xffffffffu, s, 8);
+        s *= t;
+#pragma unroll
+        for (int q = 0; q < RQ; ++q)
+          if (16 * q + 15 > j && 16 * q < r) z[q] = fmaf(-s, v[q], z[q]);
+      }
+      if (cv) {
+#pragma unroll
+        for (int q = 0; q < RQ; ++q) {
+          const int a = g + 16 * q;
+          if (a < r) w.W[a * n + c] = (double)z[q];
+        }
+      }
     }
-    for (int a = lane; a < r; a += 32) w.W[a * n + c] = (double)Z[a * r + c];
   }
 }
 
@@ -447,8 +584,9 @@ eig32_kernel(int n, int zsmem, int slots, DW w) {
 //   lam_i = s_ii / (2 - g_ii) and the threshold from the accumulated norms);
 //   2: B = E read from memory (cluster step).  With addD: C = D + op(A) B.
 //   acc_mode 1 (the G product): accumulate ||I - G||_F^2 into acc[1];
-//   acc_mode 2 (the S product): accumulate ||S - diag(lam)||_F^2 into acc[0] and
-//   max |lam| into acc[2] (as the bits of a non-negative double).
+//   acc_mode 2 (the S product): store lam_i = s_ii / (2 - g_ii), accumulate
+//   ||S - diag(lam)||_F^2 into acc[0] and max |lam| into acc[2] (as the bits of a
+//   non-negative double).
 struct GemmJob {
   const double* A; const double* B; double* C; const double* D;
   int ta, bmode, addD, acc_mode;
@@ -473,7 +611,12 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
     const int row = row0 + a;
     As[q] = (row < r) ? (jb.ta ? jb.A[kq * n + row] : jb.A[row * n + kq]) : 0.0;
   }
-  const double thr = (jb.bmode == 1) ? thr_from(acc, floor_rel) : 0.0;
+  __shared__ double s_thr;
+  if (jb.bmode == 1) {
+    if (tid == 0) s_thr = thr_from(acc, floor_rel);
+    __syncthreads();
+  }
+  const double thr = (jb.bmode == 1) ? s_thr : 0.0;
   for (int q = tid; q < r * kTile; q += kTile * kTile) {
     const int kq = q / kTile, b = q % kTile;
     const int col = col0 + b;
@@ -488,11 +631,10 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
         const double rij = (kq == col ? 1.0 : 0.0) - gs;
         v = 0.5 * rij;
         if (kq != col) {
-          const double li = w.SS[kq * n + kq] / (2.0 - w.G[kq * n + kq]);
-          const double lj = w.SS[col * n + col] / (2.0 - w.G[col * n + col]);
+          const double li = w.lam[kq], lj = w.lam[col];
           if (fabs(li - lj) > thr) {
             const double ss = 0.5 * (w.SS[kq * n + col] + w.SS[col * n + kq]);
-            const double t = (ss + lj * rij) / (lj - li);
+            const double t = fma(lj, rij, ss) * rcp_nr(lj - li);
             if (fabs(t) < kGuard) v = t;
           }
         }
@@ -515,6 +657,7 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
         c0 = rij * rij;
       } else if (row == col) {
         const double lam = a_acc / (2.0 - w.G[row * n + row]);
+        w.lam[row] = lam;
         c0 = (a_acc - lam) * (a_acc - lam);
         c1 = fabs(lam);
       } else {
@@ -549,7 +692,7 @@ coeff_kernel(int n, const double* acc, double floor_rel, DW w) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = kBig / 32;
   const double thr = thr_from(acc, floor_rel);
-  for (int i = tid; i < r; i += kBig) sl[i] = w.SS[i * n + i] / (2.0 - w.G[i * n + i]);
+  for (int i = tid; i < r; i += kBig) sl[i] = w.lam[i];
   for (int i = wid; i < r; i += nwarps)
     for (int j = lane; j < r; j += 32) w.E[i * n + j] = (i == j) ? 0.5 * (1.0 - w.G[i * n + i]) : 0.0;
   __syncthreads();
@@ -643,12 +786,19 @@ cluster_kernel(int n, DW w) {
         if (p > q) { const int t = p; p = q; q = t; }
         double cc = 1.0, ss = 0.0;
         if (q < mm) {
-          const double apq = cA[p * mm + q], app = cA[p * mm + p], aqq = cA[q * mm + q];
+          const double apq = cA[p * mm + q], dd = cA[q * mm + q] - cA[p * mm + p];
           if (apq != 0.0) {
-            const double tau = (aqq - app) / (2.0 * apq);
-            const double t = (fabs(tau) > 1e150) ? 0.5 / tau
-                                                  : copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            cc = 1.0 / sqrt(1.0 + t * t);
+            // t = tan of the rotation angle, 2 apq sgn(d) / (|d| + sqrt(d^2 + 4 apq^2)),
+            // in FP32 on values scaled to about 1 by a power of two; an inexact angle
+            // only slows the last sweep down, while c and s below are consistent to
+            // FP64 accuracy, so the rotation stays orthogonal.
+            const double m = fmax(fabs(dd), 2.0 * fabs(apq));
+            const int ex = (int)((__double_as_longlong(m) >> 52) & 0x7FF) - 1023;
+            const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
+            const float df = (float)(dd * sc), pf = (float)(2.0 * apq * sc);
+            const float tf = ((df < 0.f) ? -pf : pf) / (fabsf(df) + sqrtf(df * df + pf * pf));
+            const double t = (df == 0.f) ? ((apq > 0.0) ? 1.0 : -1.0) : (double)tf;
+            cc = rsqrt_nr12(fma(t, t, 1.0));
             ss = t * cc;
           }
         }
@@ -695,7 +845,6 @@ cluster_kernel(int n, DW w) {
 __global__ void select_kernel(int k, int n, const double* acc, DW w, double* __restrict__ theta) {
   const int r = *w.rank;
   for (int c = threadIdx.x; c < k; c += blockDim.x) w.order[c] = 0;   // rank < k: stays in bounds
-  for (int i = threadIdx.x; i < r; i += blockDim.x) w.lam[i] = w.SS[i * n + i] / (2.0 - w.G[i * n + i]);
   if (threadIdx.x == 0) {
     const double amax = __longlong_as_double((long long)((const unsigned long long*)acc)[2]);
     w.misc[1] = (amax > 0.0) ? sqrt(acc[0]) / amax + sqrt(acc[1]) : sqrt(acc[1]);
@@ -714,43 +863,47 @@ __global__ void select_kernel(int k, int n, const double* acc, DW w, double* __r
   for (int c = threadIdx.x; c < k; c += blockDim.x) theta[c] = w.lam[w.order[c]];
 }
 
-// z = L^{-T} w_sel (one warp per selected column, z in shared memory), then
-// Y[perm[i]][c] = d[perm[i]] z[i] for i < r and 0 for the dropped rows.
-__global__ void __launch_bounds__(kTrsmWarps * 32)
-backsub_kernel(int n, int k, DW w, double* __restrict__ Y, int lsmem) {
-  extern __shared__ double lsm[];
-  __shared__ double zc[kTrsmWarps][kMaxN];
+// z = L^{-T} w_sel by back substitution (one warp and one CTA per selected column;
+// lane l keeps rows l, l + 32, ...; once z_i is known, row i of L times z_i is
+// subtracted from the rows above), then Y[perm[i]][c] = d[perm[i]] z[i] for i < r and
+// 0 for the dropped rows.
+__global__ void __launch_bounds__(32)
+backsub_kernel(int n, int k, DW w, double* __restrict__ Y) {
   const int r = *w.rank;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const double* L = w.L;
-  if (lsmem) {   // transposed: row i holds column i of L
-    for (int q = threadIdx.x; q < r * r; q += kTrsmWarps * 32) {
-      const int i = q / r, qq = q % r;
-      lsm[qq * r + i] = w.L[i * n + qq];
-    }
-    __syncthreads();
-    L = lsm;
-  }
-  const int c = blockIdx.x * kTrsmWarps + wid;
+  const int lane = threadIdx.x;
+  const int c = blockIdx.x;
   if (c >= k) return;
-  double* z = zc[wid];
-  const int* perm = w.perm;
   const int oc = w.order[c];
-  for (int i = r - 1; i >= 0; --i) {
-    double s = 0.0;
-    if (lsmem) {
-      const double* Lt = L + i * r;   // column i of L
-      for (int q = i + 1 + lane; q < r; q += 32) s += Lt[q] * z[q];
-    } else {
-      for (int q = i + 1 + lane; q < r; q += 32) s += L[q * n + i] * z[q];
-    }
-    s = warp_sum(s);
-    if (lane == 0) z[i] = (w.W[i * n + oc] - s) / (lsmem ? L[i * r + i] : L[i * n + i]);
-    __syncwarp();
+  double acc[kRowsPerLane];
+#pragma unroll
+  for (int t = 0; t < kRowsPerLane; ++t) {
+    const int q = lane + 32 * t;
+    acc[t] = (q < r) ? w.W[q * n + oc] : 0.0;
   }
-  for (int i = lane; i < n; i += 32) {
-    const int row = perm[i];
-    Y[row * k + c] = (i < r) ? w.d[row] * z[i] : 0.0;
+  for (int i = r - 1; i >= 0; --i) {
+    const int ti = i >> 5, own = i & 31;
+    double zi = 0.0;
+#pragma unroll
+    for (int t = 0; t < kRowsPerLane; ++t)
+      if (t == ti && lane == own) { acc[t] *= w.rl[i]; zi = acc[t]; }
+    zi = __shfl_sync(0xffffffffu, zi, own);
+    const double* Li = w.L + i * n;   // row i of L
+#pragma unroll
+    for (int t = 0; t < kRowsPerLane; ++t) {
+      if (32 * t < i) {   // warp-uniform
+        const int q = lane + 32 * t;
+        if (q < i) acc[t] = fma(-Li[q], zi, acc[t]);
+      }
+    }
+  }
+  const int* perm = w.perm;
+#pragma unroll
+  for (int t = 0; t < kRowsPerLane; ++t) {
+    const int i = lane + 32 * t;
+    if (i < n) {
+      const int row = perm[i];
+      Y[row * k + c] = (i < r) ? w.d[row] * acc[t] : 0.0;
+    }
   }
 }
 
@@ -765,6 +918,7 @@ DW carve(double* work, int n) {
   double* p = work;
   w.S = p; p += nn;
   w.L = p; p += nn;
+  w.Lt = p; p += nn;
   w.T = p; p += nn;
   w.Z = p; p += nn;
   w.W = p; p += nn;
@@ -774,10 +928,12 @@ DW carve(double* work, int n) {
   w.P = p; p += nn;
   w.E = p; p += nn;
   w.d = p; p += n;
+  w.rl = p; p += n;
   w.lam = p; p += n;
   w.misc = p; p += 48;   // [0..8) scalars, [8..48) per-step norm accumulators
   w.A32 = reinterpret_cast<float*>(p); p += nn / 2 + 1;
   w.Z32 = reinterpret_cast<float*>(p); p += nn / 2 + 1;
+  w.LU32 = reinterpret_cast<float*>(p); p += (5 * nn + 1) / 2 + 1;
   w.perm = reinterpret_cast<int*>(p); p += n / 2 + 1;
   w.order = reinterpret_cast<int*>(p); p += n / 2 + 1;
   w.srt = reinterpret_cast<int*>(p); p += n / 2 + 1;
@@ -798,7 +954,7 @@ void gemm(const GemmJob& j0, const GemmJob& j1, int nz, const DW& w, int n, doub
 
 size_t dense_work_doubles(int n) {
   const size_t nn = (size_t)n * n;
-  return 10 * nn + 2 * (size_t)n + 48 + 2 * (nn / 2 + 1) + 4 * ((size_t)n / 2 + 2) + 1 + 16;
+  return 11 * nn + 3 * (size_t)n + 48 + 2 * (nn / 2 + 1) + (5 * nn + 1) / 2 + 1 + 4 * ((size_t)n / 2 + 2) + 1 + 16;
 }
 
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k, double* theta,
@@ -813,29 +969,18 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
   basis_kernel<<<1, kBig, useS ? smemS : 0, s>>>(Mhat, n, w, useS ? 1 : 0);
   check_launch("basis_kernel");
   // 2. reduced standard matrix
-  const int tb = (n + kTrsmWarps - 1) / kTrsmWarps;
-  const size_t lsm = (size_t)n * n * sizeof(double);
-  const bool lsmem = lsm <= 180 * 1024;
-  if (lsmem) {
-    BMG_CUDA(cudaFuncSetAttribute(trsm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
-    BMG_CUDA(cudaFuncSetAttribute(backsub_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm));
-  }
-  trsm_kernel<<<tb, kTrsmWarps * 32, lsmem ? lsm : 0, s>>>(Ahat, Mhat, n, sigma, 0, w, lsmem ? 1 : 0);
+  trsm_kernel<<<n, 32, 0, s>>>(Ahat, Mhat, n, sigma, 0, w);
   check_launch("trsm_kernel");
-  trsm_kernel<<<tb, kTrsmWarps * 32, lsmem ? lsm : 0, s>>>(Ahat, Mhat, n, sigma, 1, w, lsmem ? 1 : 0);
+  trsm_kernel<<<n, 32, 0, s>>>(Ahat, Mhat, n, sigma, 1, w);
   check_launch("trsm_kernel");
   // 3. FP32 eigensolve (A in shared memory; Z too when both fit)
   //    (T in shared memory; the eigenvector block too when it fits; the rest of the
   //    shared memory holds the LU factorisations of the inverse iteration)
   const size_t a32 = (size_t)n * n * sizeof(float);
-  const size_t smax = 210 * 1024;
-  const size_t slot_bytes = 16 * (size_t)n + 4 * (((size_t)n + 31) / 32);   // 4 float rows + swap bits
-  const bool zs = 2 * a32 + 16 * slot_bytes <= smax;
-  const size_t base = zs ? 2 * a32 : a32;
-  const int slots = (int)std::max<size_t>(1, std::min<size_t>(kBig / 32, (smax - base) / slot_bytes));
-  const size_t esm = base + slot_bytes * slots;
+  const bool zs = 2 * a32 <= 210 * 1024;
+  const size_t esm = zs ? 2 * a32 : a32;
   BMG_CUDA(cudaFuncSetAttribute(eig32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
-  eig32_kernel<<<1, kBig, esm, s>>>(n, zs ? 1 : 0, slots, w);
+  eig32_kernel<<<1, kBig, esm, s>>>(n, zs ? 1 : 0, w);
   check_launch("eig32_kernel");
   // 4. refinement: steps separate pairs farther apart than a floor (relative to
   //    max|lam|); cluster steps diagonalise the groups below it exactly.  The floor
@@ -869,8 +1014,7 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
   // 5. selection and back-transform
   select_kernel<<<1, 512, 0, s>>>(k, n, accs + 3 * nsteps, w, theta);
   check_launch("select_kernel");
-  backsub_kernel<<<(k + kTrsmWarps - 1) / kTrsmWarps, kTrsmWarps * 32, lsmem ? lsm : 0, s>>>(n, k, w, Y,
-                                                                                         lsmem ? 1 : 0);
+  backsub_kernel<<<k, 32, 0, s>>>(n, k, w, Y);
   check_launch("backsub_kernel");
   copy_out_kernel<<<1, 1, 0, s>>>(w, rank, quality);
   check_launch("copy_out_kernel");
