@@ -56,6 +56,19 @@ typedef enum { BMG_SMOOTH_JACOBI = 0, BMG_SMOOTH_MCGS = 1, BMG_SMOOTH_MCSGS = 2 
  * Both start from x_i = u_i and have the same residual there.                       */
 typedef enum { BMG_FORM_SHIFTED = 0, BMG_FORM_HOMOGENEOUS = 1 } bmg_form;
 
+/* Arithmetic of the k-blocks during the cycles:
+ *   BMG_PREC_FP64: every block, matrix value and product in float64 (the plain method).
+ *   BMG_PREC_FP32: the precision form.  Blocks X, AX, MX, U, ... are stored in float32;
+ *      SpMM, smoothing, transfers and the Ritz-vector expansion run in float32 with
+ *      float32 copies of A, M and the Galerkin operators.  The Gram matrices are
+ *      formed from the float32 blocks with error-free products and compensated sums
+ *      (float64-class results), and the enriched eigensolve stays float64.  On the
+ *      finest level the solve hands over to float64 cycles once every wanted pair
+ *      has residual <= switch_tol or the float32 residual stops falling (3 cycles
+ *      without halving), and finishes there to tol.  A tol >= switch_tol can be met
+ *      in float32 alone.                                                           */
+typedef enum { BMG_PREC_FP64 = 0, BMG_PREC_FP32 = 1 } bmg_precision;
+
 typedef struct {
   int smoother;              /* bmg_smoother                                      */
   int nu;                    /* sweeps per level (SGS: forward+backward = 1)       */
@@ -65,10 +78,13 @@ typedef struct {
   int cycles_intermediate;   /* cycle cap on levels 2..L-1                         */
   double tol_intermediate;   /* early stop on levels 2..L-1 (<0: none)             */
   int max_cycles;            /* cycle cap on the finest level                      */
+  int precision;             /* bmg_precision                                     */
+  double switch_tol;         /* FP32 -> FP64 hand-over residual (BMG_PREC_FP32)    */
 } bmg_options;
 
 /* Fills the defaults: Jacobi, nu=2, omega=2/3, shifted form, full depth,
- * 6 intermediate cycles, no intermediate tolerance, 200 finest cycles.            */
+ * 6 intermediate cycles, no intermediate tolerance, 200 finest cycles, float64,
+ * switch_tol 1e-6.                                                              */
 void bmg_default_options(bmg_options* opt);
 
 typedef struct bmg_problem bmg_problem;
@@ -80,6 +96,7 @@ typedef struct {
   int converged;             /* 1 if every wanted pair met tol                    */
   double max_resid;          /* largest wanted relative residual at exit          */
   double max_dense_err;      /* largest error estimate of the enriched eigensolve */
+  int fp32_cycles;           /* cycles run with float32 blocks (all levels)       */
 } bmg_solve_info;
 
 /* ---------------------------------------------------------------- set-up ----- */
@@ -183,6 +200,15 @@ bmg_status bmg_smooth(const bmg_problem* p, int f, int level, double* X, const d
                       const double* s, int k, int ld, int smoother, int nu, double omega,
                       double* work, void* stream);
 
+/* float32 forms of the two calls above (the precision form, BMG_PREC_FP32): float32
+ * blocks with ld a multiple of 4, float32 copies of the operators and float32
+ * arithmetic.  s [ld] device float32 shifts (zero in the padding).               */
+bmg_status bmg_spmm_f32(bmg_problem* p, int f, int level, const float* X, int k, int ld,
+                        float* AX, float* MX, void* stream);
+bmg_status bmg_smooth_f32(bmg_problem* p, int f, int level, float* X, const float* B,
+                          const float* s, int k, int ld, int smoother, int nu, double omega,
+                          float* work, void* stream);
+
 /* Y = P_l Xc (level l-1 -> l, Eq. proj-1); with add != 0: Y += P_l Xc.          */
 bmg_status bmg_prolong(const bmg_problem* p, int level, const double* Xc, double* Y,
                        int k, int ld, int add, void* stream);
@@ -194,6 +220,13 @@ bmg_status bmg_restrict(const bmg_problem* p, int level, const double* R, double
  * 1 <= k <= 160.  Synchronous.                                                   */
 bmg_status bmg_gram(const double* X, const double* Y, int n, int k, int ld, double* G,
                     void* stream);
+
+/* G = X^T Y for float32 blocks X, Y [n][ld] (ld a multiple of 4), float64 result:
+ * each product is split exactly into two float32 parts and the sums are
+ * compensated (TwoSum), so G is accurate to about 2^-46 sum_r |X[r][i] Y[r][j]|
+ * before the float64 summation of the block partials.  1 <= k <= 160. Synchronous.*/
+bmg_status bmg_gram_f32(const float* X, const float* Y, int n, int k, int ld, double* G,
+                        void* stream);
 
 /* Smallest-|theta| k eigenpairs of the symmetric-semidefinite pencil
  * (Ahat - sigma Mhat) y = theta Mhat y, n x n row-major device matrices (n <= 224):

@@ -19,6 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "bmg.h")
 
 SMOOTHERS = {"jacobi": 0, "mcgs": 1, "mcsgs": 2}
 FORMS = {"shifted": 0, "homogeneous": 1}
+PRECISIONS = {"fp64": 0, "fp32": 1}
 STATUS = {0: "BMG_OK", 1: "BMG_ERR_INVALID_ARG", 2: "BMG_ERR_CUDA", 3: "BMG_ERR_OOM",
           4: "BMG_ERR_SINGULAR", 5: "BMG_ERR_NOT_CONVERGED", 6: "BMG_ERR_NONFINITE",
           7: "BMG_ERR_MESH", 8: "BMG_ERR_STATE"}
@@ -33,12 +34,14 @@ class BmgError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("smoother", C.c_int), ("nu", C.c_int), ("omega", C.c_double), ("form", C.c_int),
                 ("vcycle_depth", C.c_int), ("cycles_intermediate", C.c_int),
-                ("tol_intermediate", C.c_double), ("max_cycles", C.c_int)]
+                ("tol_intermediate", C.c_double), ("max_cycles", C.c_int), ("precision", C.c_int),
+                ("switch_tol", C.c_double)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("levels", C.c_int), ("cycles", C.c_int * 32), ("total_cycles", C.c_int),
-                ("converged", C.c_int), ("max_resid", C.c_double), ("max_dense_err", C.c_double)]
+                ("converged", C.c_int), ("max_resid", C.c_double), ("max_dense_err", C.c_double),
+                ("fp32_cycles", C.c_int)]
 
 
 def _load():
@@ -62,6 +65,9 @@ def _load():
         "bmg_get_colouring": (i, [vp, i, vp, P(C.c_int)]),
         "bmg_spmm": (i, [vp, i, i, vp, i, i, vp, vp, vp]),
         "bmg_smooth": (i, [vp, i, i, vp, vp, vp, i, i, i, i, d, vp, vp]),
+        "bmg_spmm_f32": (i, [vp, i, i, vp, i, i, vp, vp, vp]),
+        "bmg_smooth_f32": (i, [vp, i, i, vp, vp, vp, i, i, i, i, d, vp, vp]),
+        "bmg_gram_f32": (i, [vp, vp, i, i, i, vp, vp]),
         "bmg_prolong": (i, [vp, i, vp, vp, i, i, i, vp]),
         "bmg_restrict": (i, [vp, i, vp, vp, i, i, vp]),
         "bmg_gram": (i, [vp, vp, i, i, i, vp, vp]),
@@ -112,7 +118,8 @@ def _stream():
 
 
 def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_depth=99,
-            cycles_intermediate=6, tol_intermediate=-1.0, max_cycles=200) -> Options:
+            cycles_intermediate=6, tol_intermediate=-1.0, max_cycles=200, precision="fp64",
+            switch_tol=1e-6) -> Options:
     o = Options()
     LIB.bmg_default_options(C.byref(o))
     o.smoother = SMOOTHERS[smoother]
@@ -123,6 +130,8 @@ def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_dep
     o.cycles_intermediate = cycles_intermediate
     o.tol_intermediate = tol_intermediate
     o.max_cycles = max_cycles
+    o.precision = PRECISIONS[precision]
+    o.switch_tol = switch_tol
     return o
 
 
@@ -198,6 +207,14 @@ class Problem:
     def smooth(self, f, level, X, B, shift, k, smoother, nu, omega, work):
         _check(LIB.bmg_smooth(self.h, f, level, _ptr(X), _ptr(B), _ptr(shift), k, X.shape[1],
                               SMOOTHERS[smoother], nu, omega, _ptr(work), _stream()))
+
+    def spmm_f32(self, f, level, X, k, AX, MX):
+        """float32 blocks ([N][ld] with ld % 4 == 0), float32 operators."""
+        _check(LIB.bmg_spmm_f32(self.h, f, level, _ptr(X), k, X.shape[1], _ptr(AX), _ptr(MX), _stream()))
+
+    def smooth_f32(self, f, level, X, B, shift, k, smoother, nu, omega, work):
+        _check(LIB.bmg_smooth_f32(self.h, f, level, _ptr(X), _ptr(B), _ptr(shift), k, X.shape[1],
+                                  SMOOTHERS[smoother], nu, omega, _ptr(work), _stream()))
 
     def prolong(self, level, Xc, Y, k, add=False):
         _check(LIB.bmg_prolong(self.h, level, _ptr(Xc), _ptr(Y), k, Y.shape[1], int(add), _stream()))
@@ -277,6 +294,11 @@ def _solve_raw(h, X0_ptr, x0_dev, U_ptr, u_dev, k, n_wanted, sigma, tol, opt):
 
 def gram(X, Y, k, G):
     _check(LIB.bmg_gram(_ptr(X), _ptr(Y), X.shape[0], k, X.shape[1], _ptr(G), _stream()))
+
+
+def gram_f32(X, Y, k, G):
+    """G (float64) = X^T Y for float32 blocks, compensated accumulation."""
+    _check(LIB.bmg_gram_f32(_ptr(X), _ptr(Y), X.shape[0], k, X.shape[1], _ptr(G), _stream()))
 
 
 def gram_noalloc(X, Y, k, G):

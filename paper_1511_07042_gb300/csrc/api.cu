@@ -86,42 +86,8 @@ __global__ void ratio_max_kernel(const double* da, const double* dm, int n, unsi
   atomicMax(out, (unsigned long long)__double_as_longlong(r));
 }
 
-// Ahat = [[AQ, CA], [CA^T, GA]] (n = n1 + k), CA read from a [n1][ld] block.
-__global__ void assemble_hat_kernel(const double* AQ, const double* CA, const double* GA, int n1,
-                                    int k, int ld, double* H) {
-  const int n = n1 + k;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n * n) return;
-  const int i = q / n, j = q % n;
-  double v;
-  if (i < n1 && j < n1) v = AQ[i * n1 + j];
-  else if (i < n1) v = CA[(size_t)i * ld + (j - n1)];
-  else if (j < n1) v = CA[(size_t)j * ld + (i - n1)];
-  else v = GA[(i - n1) * k + (j - n1)];
-  H[q] = v;
-}
 
-// Coarse coefficients Y[0:n1][0:k] into a [n1][ld] block (zero padding).
-__global__ void pack_coarse_kernel(const double* Y, int n1, int k, int ld, double* Z) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n1 * ld) return;
-  const int i = q / ld, c = q % ld;
-  Z[q] = (c < k) ? Y[i * k + c] : 0.0;
-}
 
-// lam = theta + sigma; shift per column (form), zero in the padding.
-__global__ void shifts_kernel(const double* theta, int k, int ld, double sigma, int form,
-                              double* lam, double* shift) {
-  const int c = threadIdx.x + blockIdx.x * blockDim.x;
-  if (c >= ld) return;
-  if (c < k) {
-    lam[c] = theta[c] + sigma;
-    shift[c] = (form == BMG_FORM_SHIFTED) ? sigma : theta[c] + sigma;
-  } else {
-    lam[c] = 0.0;
-    shift[c] = 0.0;
-  }
-}
 
 int grid_of(size_t n, int b) { return (int)std::max<size_t>(1, (n + b - 1) / b); }
 
@@ -141,6 +107,8 @@ extern "C" void bmg_default_options(bmg_options* o) {
   o->cycles_intermediate = 6;
   o->tol_intermediate = -1.0;
   o->max_cycles = 200;
+  o->precision = BMG_PREC_FP64;
+  o->switch_tol = 1e-6;
 }
 
 extern "C" const char* bmg_last_error(void) { return g_last_error.c_str(); }
@@ -392,38 +360,193 @@ extern "C" bmg_status bmg_dense_eig(const double* Ahat, const double* Mhat, int 
     DBuf<double> work(dense_work_doubles(n));
     DBuf<int> rk(1);
     dense_eig(Ahat, Mhat, n, sigma, k, theta, Y, rank_out ? rank_out : rk.get(), work.get(), nullptr,
-              (cudaStream_t)stream);
+              kDropFP64, (cudaStream_t)stream);
     BMG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   });
 }
 
 // ------------------------------------------------------------------- solve ----
+namespace bmg {
 namespace {
+
+// Operators of finest level f on level j in the block arithmetic T.
+template <typename T> struct Ops;
+template <> struct Ops<double> {
+  static const double* A(const bmg_problem* p, int f, int j) { return p->opA(f, j); }
+  static const double* M(const bmg_problem* p, int f, int j) { return p->opM(f, j); }
+  static const double* DA(const bmg_problem* p, int f, int j) { return p->opDA(f, j); }
+  static const double* DM(const bmg_problem* p, int f, int j) { return p->opDM(f, j); }
+};
+template <> struct Ops<float> {
+  static const float* A(const bmg_problem* p, int f, int j) { return p->ops32[f][j].a.get(); }
+  static const float* M(const bmg_problem* p, int f, int j) { return p->ops32[f][j].m.get(); }
+  static const float* DA(const bmg_problem* p, int f, int j) { return p->ops32[f][j].da.get(); }
+  static const float* DM(const bmg_problem* p, int f, int j) { return p->ops32[f][j].dm.get(); }
+};
+
+__global__ void to_float_kernel(const double* __restrict__ in, size_t n, float* __restrict__ out) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = (float)in[t];
+}
+
+// Block copy between leading dimensions and arithmetic types (columns [0, cols)).
+template <typename S, typename D>
+__global__ void convert_block_kernel(const S* __restrict__ in, int ldi, D* __restrict__ out, int ldo,
+                                     int rows, int cols) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)rows * cols) return;
+  const size_t r = t / cols, c = t % cols;
+  out[r * ldo + c] = (D)in[r * ldi + c];
+}
+
+// float32 copies of every operator set (precision form), built once per problem.
+void ensure_ops32(bmg_problem* p) {
+  if (!p->ops32.empty()) return;
+  cudaStream_t s = p->stream;
+  const int L = p->L;
+  std::vector<std::vector<OpSet32>> ops(L + 1);
+  auto conv = [&](const double* src, size_t n, DBuf<float>& dst) {
+    dst.alloc(n);
+    to_float_kernel<<<grid_of(n, 256), 256, 0, s>>>(src, n, dst.get());
+    check_launch("to_float_kernel");
+  };
+  for (int f = 2; f <= L; ++f) {
+    ops[f].resize(f + 1);
+    for (int j = 1; j <= f; ++j) {
+      const Mesh& mj = p->meshOf(j);
+      conv(p->opA(f, j), mj.nnz, ops[f][j].a);
+      conv(p->opM(f, j), mj.nnz, ops[f][j].m);
+      conv(p->opDA(f, j), mj.n, ops[f][j].da);
+      conv(p->opDM(f, j), mj.n, ops[f][j].dm);
+    }
+  }
+  BMG_CUDA(cudaStreamSynchronize(s));
+  p->ops32 = std::move(ops);
+}
+
+// Device views of the blocks of one arithmetic.
+template <typename T>
+struct Blocks {
+  int ld = 0;
+  T *X = nullptr, *AX = nullptr, *MX = nullptr, *U = nullptr, *AU = nullptr, *MU = nullptr;
+  T *B = nullptr, *W = nullptr, *Zf = nullptr, *shift = nullptr;
+  std::vector<T*> cA, cB, cC, cD;
+};
+
+Blocks<double> blocks64(SolveWork& w) {
+  Blocks<double> b;
+  b.ld = w.ld;
+  b.X = w.X.get(); b.AX = w.AX.get(); b.MX = w.MX.get(); b.U = w.U.get(); b.AU = w.AU.get();
+  b.MU = w.MU.get(); b.B = w.B.get(); b.W = w.W.get(); b.Zf = w.Zf.get(); b.shift = w.shift.get();
+  for (auto* v : {&w.cA, &w.cB, &w.cC, &w.cD}) {
+    std::vector<double*>& dst = (v == &w.cA) ? b.cA : (v == &w.cB) ? b.cB : (v == &w.cC) ? b.cC : b.cD;
+    for (auto& d : *v) dst.push_back(d.get());
+  }
+  return b;
+}
+
+Blocks<float> blocks32(bmg_problem* p, SolveWork& w) {
+  cudaStream_t s = p->stream;
+  if (!w.ld32) {
+    w.ld32 = (w.k + 3) & ~3;
+    const size_t big = (size_t)p->meshOf(w.L).n * w.ld32;
+    for (DBuf<float>* b : {&w.X32, &w.AX32, &w.MX32, &w.U32, &w.AU32, &w.MU32, &w.B32, &w.W32, &w.Zf32}) {
+      b->alloc(big);
+      BMG_CUDA(cudaMemsetAsync(b->get(), 0, sizeof(float) * big, s));
+    }
+    w.shift32.alloc(w.ld32);
+    BMG_CUDA(cudaMemsetAsync(w.shift32.get(), 0, sizeof(float) * w.ld32, s));
+    w.cA32.resize(w.L); w.cB32.resize(w.L); w.cC32.resize(w.L); w.cD32.resize(w.L);
+    for (int j = 1; j < w.L; ++j) {
+      const size_t sz = (size_t)p->meshOf(j).n * w.ld32;
+      for (auto* v : {&w.cA32, &w.cB32, &w.cC32, &w.cD32}) {
+        (*v)[j].alloc(sz);
+        BMG_CUDA(cudaMemsetAsync((*v)[j].get(), 0, sizeof(float) * sz, s));
+      }
+    }
+  }
+  Blocks<float> b;
+  b.ld = w.ld32;
+  b.X = w.X32.get(); b.AX = w.AX32.get(); b.MX = w.MX32.get(); b.U = w.U32.get(); b.AU = w.AU32.get();
+  b.MU = w.MU32.get(); b.B = w.B32.get(); b.W = w.W32.get(); b.Zf = w.Zf32.get(); b.shift = w.shift32.get();
+  for (auto* v : {&w.cA32, &w.cB32, &w.cC32, &w.cD32}) {
+    std::vector<float*>& dst = (v == &w.cA32) ? b.cA : (v == &w.cB32) ? b.cB : (v == &w.cC32) ? b.cC : b.cD;
+    for (auto& d : *v) dst.push_back(d.get());
+  }
+  return b;
+}
+
+template <typename S, typename D>
+void convert_block(const S* in, int ldi, D* out, int ldo, int rows, int cols, cudaStream_t s) {
+  const size_t total = (size_t)rows * cols;
+  convert_block_kernel<S, D><<<grid_of(total, 256), 256, 0, s>>>(in, ldi, out, ldo, rows, cols);
+  check_launch("convert_block_kernel");
+}
+
+// Ahat = [[AQ, CA], [CA^T, GA]] (n = n1 + k), CA read from a [n1][ld] block.
+template <typename T>
+__global__ void assemble_hat_kernel(const double* AQ, const T* CA, const double* GA, int n1, int k,
+                                    int ld, double* H) {
+  const int n = n1 + k;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * n) return;
+  const int i = q / n, j = q % n;
+  double v;
+  if (i < n1 && j < n1) v = AQ[i * n1 + j];
+  else if (i < n1) v = (double)CA[(size_t)i * ld + (j - n1)];
+  else if (j < n1) v = (double)CA[(size_t)j * ld + (i - n1)];
+  else v = GA[(i - n1) * k + (j - n1)];
+  H[q] = v;
+}
+
+// Coarse coefficients Y[0:n1][0:k] into a [n1][ld] block (zero padding).
+template <typename T>
+__global__ void pack_coarse_kernel(const double* Y, int n1, int k, int ld, T* Z) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n1 * ld) return;
+  const int i = q / ld, c = q % ld;
+  Z[q] = (c < k) ? (T)Y[i * k + c] : T(0);
+}
+
+// lam = theta + sigma (k values); the per-column smoothing shift in the block
+// arithmetic (form), zero in the padding.
+template <typename T>
+__global__ void shifts_kernel(const double* theta, int k, int ld, double sigma, int form, double* lam,
+                              T* shift) {
+  const int c = threadIdx.x + blockIdx.x * blockDim.x;
+  if (c >= ld) return;
+  if (c < k) {
+    lam[c] = theta[c] + sigma;
+    shift[c] = (T)((form == BMG_FORM_SHIFTED) ? sigma : theta[c] + sigma);
+  } else {
+    shift[c] = T(0);
+  }
+}
 
 // nu sweeps of the configured smoother on level j (operators of finest level f),
 // from Xin into Xout (Xin may equal Xout).  Jacobi alternates between Xout and work
 // so that the last sweep lands in Xout; Gauss-Seidel runs in place on Xout.
-void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, const double* Xin,
-                  double* Xout, const double* B, const double* shift, int ld, double* work,
-                  cudaStream_t s) {
+template <typename T>
+void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, const T* Xin, T* Xout,
+                  const T* B, const T* shift, int ld, T* work, cudaStream_t s) {
   const Mesh& m = p->meshOf(j);
-  const double *a = p->opA(f, j), *mm = p->opM(f, j), *da = p->opDA(f, j), *dm = p->opDM(f, j);
-  const size_t bytes = sizeof(double) * (size_t)m.n * ld;
+  const T *a = Ops<T>::A(p, f, j), *mm = Ops<T>::M(p, f, j), *da = Ops<T>::DA(p, f, j), *dm = Ops<T>::DM(p, f, j);
+  const size_t bytes = sizeof(T) * (size_t)m.n * ld;
   if (o.smoother == BMG_SMOOTH_JACOBI) {
-    const double* src = Xin;
+    const T* src = Xin;
     if (Xin == Xout && (o.nu % 2 == 1)) {
       BMG_CUDA(cudaMemcpyAsync(work, Xin, bytes, cudaMemcpyDeviceToDevice, s));
       src = work;
       for (int it = 0; it < o.nu; ++it) {
-        double* dst = (it % 2 == 0) ? Xout : work;
-        jacobi_sweep(m, a, mm, da, dm, src, dst, B, shift, ld, o.omega, s);
+        T* dst = (it % 2 == 0) ? Xout : work;
+        jacobi_sweep<T>(m, a, mm, da, dm, src, dst, B, shift, ld, o.omega, s);
         src = dst;
       }
       return;
     }
     for (int it = 0; it < o.nu; ++it) {
-      double* dst = ((o.nu - 1 - it) % 2 == 0) ? Xout : work;
-      jacobi_sweep(m, a, mm, da, dm, src, dst, B, shift, ld, o.omega, s);
+      T* dst = ((o.nu - 1 - it) % 2 == 0) ? Xout : work;
+      jacobi_sweep<T>(m, a, mm, da, dm, src, dst, B, shift, ld, o.omega, s);
       src = dst;
     }
     return;
@@ -431,9 +554,9 @@ void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, cons
   if (Xin != Xout) BMG_CUDA(cudaMemcpyAsync(Xout, Xin, bytes, cudaMemcpyDeviceToDevice, s));
   const Level& lv = p->lev[j];
   for (int it = 0; it < o.nu; ++it) {
-    for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s);
+    for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s);
     if (o.smoother == BMG_SMOOTH_MCSGS)
-      for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s);
+      for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s);
   }
 }
 
@@ -469,7 +592,7 @@ SolveWork& workspace(bmg_problem* p, int k) {
   w.Mhat.alloc((size_t)w.nh * w.nh);
   w.Y.alloc((size_t)w.nh * k);
   w.theta.alloc(k);
-  w.lam.alloc(ld);
+  w.lam.alloc((k + 3) & ~3);
   w.shift.alloc(ld);
   w.GA.alloc((size_t)k * k);
   w.GM.alloc((size_t)k * k);
@@ -507,7 +630,123 @@ SolveWork& workspace(bmg_problem* p, int k) {
   return *p->ws;
 }
 
+// Outcome of one cycle: Ritz values, residuals and convergence of the wanted pairs.
+struct CycleState {
+  std::vector<double> rho, lamv;
+  double max_dense_err = 0.0;
+};
+
+// One BMG cycle on level f with blocks of arithmetic T (steps 1-5 of the file
+// header).  Smoothing (step 5) runs unless the wanted pairs met ftol or `last` is
+// set.  Returns whether every wanted pair met ftol.
+template <typename T>
+bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_options& o, double sigma, int k,
+               int n_wanted, double ftol, bool last, CycleState& cs) {
+  cudaStream_t s = p->stream;
+  const int ld = b.ld, n1 = w.n1, nh = w.nh;
+  const Mesh& mf = p->meshOf(f);
+  const int nf = mf.n;
+  const T *Af = Ops<T>::A(p, f, f), *Mf = Ops<T>::M(p, f, f);
+  double* hres = w.hbuf;            // 2k residual sums
+  double* hlam = w.hbuf + 2 * k;    // k Ritz values
+  double* hqual = w.hbuf + 3 * k;   // error estimate of the enriched eigensolve
+  int* hint = reinterpret_cast<int*>(w.hbuf + 3 * k + 1);  // rank
+  // 1-2: products, Grams, couplings Q^T AX, Q^T MX by the restriction chain
+  spmm_am<T>(mf, Af, Mf, b.X, ld, b.AX, b.MX, s);
+  gram(b.X, b.AX, nf, k, ld, w.GA.get(), w.partial.get(), gram_parts(nf), s);
+  gram(b.X, b.MX, nf, k, ld, w.GM.get(), w.partial.get(), gram_parts(nf), s);
+  const T* ca = b.AX;
+  const T* cm = b.MX;
+  for (int j = f; j >= 2; --j) {
+    restrict_<T>(p->meshOf(j - 1), ca, b.cA[j - 1], ld, s);
+    restrict_<T>(p->meshOf(j - 1), cm, b.cB[j - 1], ld, s);
+    ca = b.cA[j - 1];
+    cm = b.cB[j - 1];
+  }
+  prof_begin(KC_SMALL, s);
+  assemble_hat_kernel<T><<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.AQ[f].get(), ca, w.GA.get(), n1, k, ld, w.Ahat.get());
+  check_launch("assemble_hat_kernel");
+  assemble_hat_kernel<T><<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.MQ[f].get(), cm, w.GM.get(), n1, k, ld, w.Mhat.get());
+  check_launch("assemble_hat_kernel");
+  prof_end(KC_SMALL, s, 32.0 * nh * nh, 0.0);
+  // 3: enriched eigensolve
+  dense_eig(w.Ahat.get(), w.Mhat.get(), nh, sigma, k, w.theta.get(), w.Y.get(), w.rank.get(), w.dense.get(),
+            w.dquality.get(), sizeof(T) == sizeof(float) ? kDropFP32 : kDropFP64, s);
+  prof_begin(KC_SMALL, s);
+  shifts_kernel<T><<<grid_of(ld, 128), 128, 0, s>>>(w.theta.get(), k, ld, sigma, o.form, w.lam.get(), b.shift);
+  check_launch("shifts_kernel");
+  // 4: Ritz vectors U = Q Y_c + X Y_x
+  pack_coarse_kernel<T><<<grid_of((size_t)n1 * ld, 256), 256, 0, s>>>(w.Y.get(), n1, k, ld, b.cC[1]);
+  check_launch("pack_coarse_kernel");
+  prof_end(KC_SMALL, s, 8.0 * n1 * ld, 0.0);
+  const T* z = b.cC[1];
+  for (int j = 2; j < f; ++j) {
+    prolong<T>(p->meshOf(j), z, b.cC[j], ld, false, s);
+    z = b.cC[j];
+  }
+  prolong<T>(mf, z, b.Zf, ld, false, s);
+  expand<T>(b.Zf, b.X, w.Y.get() + (size_t)n1 * k, nf, k, ld, k, b.U, s);
+  spmm_am<T>(mf, Af, Mf, b.U, ld, b.AU, b.MU, s);
+  eig_residuals<T>(b.AU, b.MU, b.U, w.lam.get(), nf, k, ld, w.partial.get(), gram_parts(nf), w.res.get(), s);
+  BMG_CUDA(cudaMemcpyAsync(hres, w.res.get(), sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaMemcpyAsync(hlam, w.lam.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaMemcpyAsync(hint, w.rank.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaMemcpyAsync(hqual, w.dquality.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaStreamSynchronize(s));
+  if (hint[0] < k) fail(BMG_ERR_SINGULAR, "enriched space rank " + std::to_string(hint[0]) + " < k");
+  if (!(*hqual <= 1e-6))
+    fail(BMG_ERR_NONFINITE, "enriched eigensolve refinement failed (error estimate " + std::to_string(*hqual) + ")");
+  cs.max_dense_err = std::max(cs.max_dense_err, *hqual);
+  bool conv = true, finite = true;
+  for (int i = 0; i < k; ++i) {
+    cs.lamv[i] = hlam[i];
+    cs.rho[i] = std::sqrt(hres[i]) / (p->norm1[f] * std::sqrt(hres[k + i]));
+    if (!std::isfinite(cs.rho[i]) || !std::isfinite(hlam[i])) finite = false;
+    if (i < n_wanted && !(cs.rho[i] <= ftol)) conv = false;
+  }
+  if (!finite) fail(BMG_ERR_NONFINITE, "non-finite Ritz pair on level " + std::to_string(f));
+  if (conv || last) return conv;
+  // 5: smoothing of the source problems from U, then the down-leg
+  const T* Bp = nullptr;
+  if (o.form == BMG_FORM_SHIFTED) {
+    prof_begin(KC_SMALL, s);
+    scale_rhs<T>(b.MU, w.theta.get(), nf, k, ld, b.B, s);
+    prof_end(KC_SMALL, s, 2.0 * sizeof(T) * nf * ld, 1.0 * nf * ld);
+    Bp = b.B;
+  }
+  smooth_level<T>(p, f, f, o, b.U, b.X, Bp, b.shift, ld, b.W, s);
+  double smax = (o.form == BMG_FORM_SHIFTED) ? sigma : -1e300;
+  if (o.form != BMG_FORM_SHIFTED) for (int i = 0; i < k; ++i) smax = std::max(smax, cs.lamv[i]);
+  std::vector<int> legs;
+  for (int j = f - 1; j >= 1 && (int)legs.size() < o.vcycle_depth; --j) {
+    if (!(smax * w.ratio[f][j] < 1.0 - 0.25)) break;
+    legs.push_back(j);
+  }
+  if (!legs.empty()) {
+    residual<T>(mf, Af, Mf, b.X, Bp, b.shift, ld, b.W, s);
+    const T* rprev = b.W;
+    for (size_t t = 0; t < legs.size(); ++t) {
+      const int j = legs[t];
+      const Mesh& mj = p->meshOf(j);
+      restrict_<T>(mj, rprev, b.cA[j], ld, s);
+      BMG_CUDA(cudaMemsetAsync(b.cB[j], 0, sizeof(T) * (size_t)mj.n * ld, s));
+      smooth_level<T>(p, f, j, o, b.cB[j], b.cB[j], b.cA[j], b.shift, ld, b.cD[j], s);
+      if (t + 1 < legs.size()) {
+        residual<T>(mj, Ops<T>::A(p, f, j), Ops<T>::M(p, f, j), b.cB[j], b.cA[j], b.shift, ld, b.cC[j], s);
+        rprev = b.cC[j];
+      }
+    }
+    for (size_t t = legs.size() - 1; t >= 1; --t) {
+      const int j = legs[t];  // coarser; add into level j+1
+      prolong<T>(p->meshOf(j + 1), b.cB[j], b.cB[j + 1], ld, true, s);
+    }
+    prolong<T>(mf, b.cB[f - 1], b.X, ld, true, s);
+  }
+  return false;
+}
+
 }  // namespace
+}  // namespace bmg
 
 extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigma, double tol,
                                 const bmg_options* opt_in, const double* X0, int x0_on_device,
@@ -521,138 +760,74 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
     bmg_default_options(&o);
     if (opt_in) o = *opt_in;
     const int L = p->L;
-    const int n1 = p->meshOf(1).n, n2 = p->meshOf(2).n, nL = p->meshOf(L).n;
+    const int n2 = p->meshOf(2).n, nL = p->meshOf(L).n;
+    const int n1 = p->meshOf(1).n;
     if (k < 1 || k > 160 || n_wanted < 1 || n_wanted > k || k > n2 || n1 + k > 224)
       fail(BMG_ERR_INVALID_ARG, "need 1 <= n_wanted <= k <= min(N_2, 160) and N_1 + k <= 224");
     if (!X0 || !evals) fail(BMG_ERR_INVALID_ARG, "X0 and evals are required");
     if (!(tol > 0.0) || !std::isfinite(sigma)) fail(BMG_ERR_INVALID_ARG, "bad tol or sigma");
     if (o.nu < 1 || o.nu > 64 || o.smoother < 0 || o.smoother > 2 || o.form < 0 || o.form > 1 ||
-        o.max_cycles < 1 || o.cycles_intermediate < 1 || !(o.omega > 0.0))
+        o.max_cycles < 1 || o.cycles_intermediate < 1 || !(o.omega > 0.0) || o.precision < 0 ||
+        o.precision > 1 || !(o.switch_tol > 0.0))
       fail(BMG_ERR_INVALID_ARG, "bad options");
     cudaStream_t s = p->stream;
     SolveWork& w = workspace(p, k);
     const int ld = w.ld;
-    double* hres = w.hbuf;            // 2k residual sums
-    double* hlam = w.hbuf + 2 * k;    // k Ritz values
-    double* hqual = w.hbuf + 3 * k;   // error estimate of the enriched eigensolve
-    int* hint = reinterpret_cast<int*>(w.hbuf + 3 * k + 1);  // rank
+    Blocks<double> b64 = blocks64(w);
+    Blocks<float> b32;
+    bool fp32 = o.precision == BMG_PREC_FP32;
+    if (fp32) {
+      ensure_ops32(p);
+      b32 = blocks32(p, w);
+    }
     // X0 -> X on level 2 (ld-strided; padding columns stay zero)
     BMG_CUDA(cudaMemsetAsync(w.X.get(), 0, sizeof(double) * (size_t)n2 * ld, s));
     BMG_CUDA(cudaMemcpy2DAsync(w.X.get(), sizeof(double) * ld, X0, sizeof(double) * k, sizeof(double) * k, n2,
                                x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (fp32) convert_block(w.X.get(), ld, b32.X, b32.ld, n2, k, s);
 
-    std::vector<double> rho(k, 0.0), lamv(k, 0.0);
-    int total_cycles = 0;
-    double max_dense_err = 0.0;
+    CycleState cs;
+    cs.rho.assign(k, 0.0);
+    cs.lamv.assign(k, 0.0);
+    int total_cycles = 0, fp32_cycles = 0;
     bool converged = false;
     std::vector<int> cyc(L + 1, 0);
+    std::vector<double> hist;   // finest-level FP32 max residuals
     for (int f = 2; f <= L; ++f) {
       const Mesh& mf = p->meshOf(f);
-      const int nf = mf.n;
-      if (f > 2) prolong(mf, w.U.get(), w.X.get(), ld, false, s);
+      if (f > 2) {
+        if (fp32) prolong<float>(mf, b32.U, b32.X, b32.ld, false, s);
+        else prolong<double>(mf, b64.U, b64.X, ld, false, s);
+      }
       const int budget = (f == L) ? o.max_cycles : o.cycles_intermediate;
       const double ftol = (f == L) ? tol : o.tol_intermediate;
       for (int c = 0; c < budget; ++c) {
-        // 1-2: products, Grams, couplings Q^T AX, Q^T MX by the restriction chain
-        spmm_am(mf, mf.valA.get(), mf.valM.get(), w.X.get(), ld, w.AX.get(), w.MX.get(), s);
-        gram(w.X.get(), w.AX.get(), nf, k, ld, w.GA.get(), w.partial.get(), gram_parts(nf), s);
-        gram(w.X.get(), w.MX.get(), nf, k, ld, w.GM.get(), w.partial.get(), gram_parts(nf), s);
-        const double* ca = w.AX.get();
-        const double* cm = w.MX.get();
-        for (int j = f; j >= 2; --j) {
-          restrict_(p->meshOf(j - 1), ca, w.cA[j - 1].get(), ld, s);
-          restrict_(p->meshOf(j - 1), cm, w.cB[j - 1].get(), ld, s);
-          ca = w.cA[j - 1].get();
-          cm = w.cB[j - 1].get();
-        }
-        const int nh = w.nh;
-        prof_begin(KC_SMALL, s);
-        assemble_hat_kernel<<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.AQ[f].get(), ca, w.GA.get(), n1, k, ld, w.Ahat.get());
-        check_launch("assemble_hat_kernel");
-        assemble_hat_kernel<<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.MQ[f].get(), cm, w.GM.get(), n1, k, ld, w.Mhat.get());
-        check_launch("assemble_hat_kernel");
-        prof_end(KC_SMALL, s, 32.0 * nh * nh, 0.0);
-        // 3: enriched eigensolve
-        dense_eig(w.Ahat.get(), w.Mhat.get(), nh, sigma, k, w.theta.get(), w.Y.get(), w.rank.get(), w.dense.get(),
-                  w.dquality.get(), s);
-        prof_begin(KC_SMALL, s);
-        shifts_kernel<<<grid_of(ld, 128), 128, 0, s>>>(w.theta.get(), k, ld, sigma, o.form, w.lam.get(), w.shift.get());
-        check_launch("shifts_kernel");
-        // 4: Ritz vectors U = Q Y_c + X Y_x
-        pack_coarse_kernel<<<grid_of((size_t)n1 * ld, 256), 256, 0, s>>>(w.Y.get(), n1, k, ld, w.cC[1].get());
-        check_launch("pack_coarse_kernel");
-        prof_end(KC_SMALL, s, 8.0 * n1 * ld, 0.0);
-        const double* z = w.cC[1].get();
-        for (int j = 2; j < f; ++j) {
-          prolong(p->meshOf(j), z, w.cC[j].get(), ld, false, s);
-          z = w.cC[j].get();
-        }
-        prolong(mf, z, w.Zf.get(), ld, false, s);
-        expand(w.Zf.get(), w.X.get(), w.Y.get() + (size_t)n1 * k, nf, k, ld, k, w.U.get(), s);
-        spmm_am(mf, mf.valA.get(), mf.valM.get(), w.U.get(), ld, w.AU.get(), w.MU.get(), s);
-        eig_residuals(w.AU.get(), w.MU.get(), w.U.get(), w.lam.get(), nf, k, ld, w.partial.get(), gram_parts(nf), w.res.get(), s);
-        BMG_CUDA(cudaMemcpyAsync(hres, w.res.get(), sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
-        BMG_CUDA(cudaMemcpyAsync(hlam, w.lam.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-        BMG_CUDA(cudaMemcpyAsync(hint, w.rank.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
-        BMG_CUDA(cudaMemcpyAsync(hqual, w.dquality.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
-        BMG_CUDA(cudaStreamSynchronize(s));
+        const bool last = c + 1 == budget;
+        const bool conv = fp32 ? run_cycle<float>(p, w, b32, f, o, sigma, k, n_wanted, ftol, last, cs)
+                               : run_cycle<double>(p, w, b64, f, o, sigma, k, n_wanted, ftol, last, cs);
         ++total_cycles;
+        if (fp32) ++fp32_cycles;
         cyc[f] = c + 1;
-        if (hint[0] < k) fail(BMG_ERR_SINGULAR, "enriched space rank " + std::to_string(hint[0]) + " < k");
-        if (!(*hqual <= 1e-6))
-          fail(BMG_ERR_NONFINITE, "enriched eigensolve refinement failed (error estimate " + std::to_string(*hqual) + ")");
-        max_dense_err = std::max(max_dense_err, *hqual);
-        bool conv = true, finite = true;
-        for (int i = 0; i < k; ++i) {
-          lamv[i] = hlam[i];
-          rho[i] = std::sqrt(hres[i]) / (p->norm1[f] * std::sqrt(hres[k + i]));
-          if (!std::isfinite(rho[i]) || !std::isfinite(hlam[i])) finite = false;
-          if (i < n_wanted && !(rho[i] <= ftol)) conv = false;
-        }
-        if (!finite) fail(BMG_ERR_NONFINITE, "non-finite Ritz pair on level " + std::to_string(f));
         if (f == L) converged = conv;
-        if (conv || c + 1 == budget) break;
-        // 5: smoothing of the source problems from U, then the down-leg
-        const double* Bp = nullptr;
-        if (o.form == BMG_FORM_SHIFTED) {
-          prof_begin(KC_SMALL, s);
-          scale_rhs(w.MU.get(), w.theta.get(), nf, k, ld, w.B.get(), s);
-          prof_end(KC_SMALL, s, 16.0 * nf * ld, 1.0 * nf * ld);
-          Bp = w.B.get();
-        }
-        smooth_level(p, f, f, o, w.U.get(), w.X.get(), Bp, w.shift.get(), ld, w.W.get(), s);
-        double smax = (o.form == BMG_FORM_SHIFTED) ? sigma : -1e300;
-        if (o.form != BMG_FORM_SHIFTED) for (int i = 0; i < k; ++i) smax = std::max(smax, lamv[i]);
-        std::vector<int> legs;
-        for (int j = f - 1; j >= 1 && (int)legs.size() < o.vcycle_depth; --j) {
-          if (!(smax * w.ratio[f][j] < 1.0 - 0.25)) break;
-          legs.push_back(j);
-        }
-        if (!legs.empty()) {
-          residual(mf, mf.valA.get(), mf.valM.get(), w.X.get(), Bp, w.shift.get(), ld, w.W.get(), s);
-          const double* rprev = w.W.get();
-          for (size_t t = 0; t < legs.size(); ++t) {
-            const int j = legs[t];
-            const Mesh& mj = p->meshOf(j);
-            restrict_(mj, rprev, w.cA[j].get(), ld, s);
-            BMG_CUDA(cudaMemsetAsync(w.cB[j].get(), 0, sizeof(double) * (size_t)mj.n * ld, s));
-            smooth_level(p, f, j, o, w.cB[j].get(), w.cB[j].get(), w.cA[j].get(), w.shift.get(), ld, w.cD[j].get(), s);
-            if (t + 1 < legs.size()) {
-              residual(mj, p->opA(f, j), p->opM(f, j), w.cB[j].get(), w.cA[j].get(), w.shift.get(), ld, w.cC[j].get(), s);
-              rprev = w.cC[j].get();
-            }
+        if (conv || last) break;
+        if (fp32 && f == L) {
+          // hand-over to FP64 cycles: the FP32 residual reached switch_tol, or it
+          // did not halve over the last three cycles
+          double mr = 0.0;
+          for (int i = 0; i < n_wanted; ++i) mr = std::max(mr, cs.rho[i]);
+          hist.push_back(mr);
+          const size_t h = hist.size();
+          if (mr <= o.switch_tol || (h >= 4 && mr > 0.5 * hist[h - 4])) {
+            convert_block(b32.X, b32.ld, w.X.get(), ld, nL, ld, s);
+            fp32 = false;
           }
-          for (size_t t = legs.size() - 1; t >= 1; --t) {
-            const int j = legs[t];  // coarser; add into level j+1
-            prolong(p->meshOf(j + 1), w.cB[j].get(), w.cB[j + 1].get(), ld, true, s);
-          }
-          prolong(mf, w.cB[f - 1].get(), w.X.get(), ld, true, s);
         }
       }
     }
     // outputs: the last Ritz pairs on level L
-    for (int i = 0; i < n_wanted; ++i) evals[i] = lamv[i];
-    if (resid) for (int i = 0; i < n_wanted; ++i) resid[i] = rho[i];
+    if (fp32) convert_block(b32.U, b32.ld, w.U.get(), ld, nL, ld, s);
+    for (int i = 0; i < n_wanted; ++i) evals[i] = cs.lamv[i];
+    if (resid) for (int i = 0; i < n_wanted; ++i) resid[i] = cs.rho[i];
     if (evecs) {
       BMG_CUDA(cudaMemcpy2DAsync(evecs, sizeof(double) * n_wanted, w.U.get(), sizeof(double) * ld,
                                  sizeof(double) * n_wanted, nL,
@@ -664,11 +839,12 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
       info->levels = L;
       for (int f = 2; f <= L && f - 2 < 32; ++f) info->cycles[f - 2] = cyc[f];
       info->total_cycles = total_cycles;
+      info->fp32_cycles = fp32_cycles;
       info->converged = converged ? 1 : 0;
       double mx = 0.0;
-      for (int i = 0; i < n_wanted; ++i) mx = std::max(mx, rho[i]);
+      for (int i = 0; i < n_wanted; ++i) mx = std::max(mx, cs.rho[i]);
       info->max_resid = mx;
-      info->max_dense_err = max_dense_err;
+      info->max_dense_err = cs.max_dense_err;
     }
     if (!converged) {
       final_status = BMG_ERR_NOT_CONVERGED;
@@ -676,4 +852,58 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
     }
   });
   return st != BMG_OK ? st : final_status;
+}
+
+// ---------------------------------------------- precision-form step entries ---
+extern "C" bmg_status bmg_spmm_f32(bmg_problem* p, int f, int level, const float* X, int k, int ld, float* AX,
+                                   float* MX, void* stream) {
+  return guarded([&] {
+    check_levels(p, f, level);
+    if (f < 2) fail(BMG_ERR_INVALID_ARG, "f must be >= 2");
+    if (!X || !AX || !MX || k < 1 || ld < k || (ld & 3)) fail(BMG_ERR_INVALID_ARG, "bad block arguments (ld % 4 == 0)");
+    ensure_ops32(p);
+    spmm_am<float>(p->meshOf(level), Ops<float>::A(p, f, level), Ops<float>::M(p, f, level), X, ld, AX, MX,
+                   (cudaStream_t)stream);
+  });
+}
+
+extern "C" bmg_status bmg_smooth_f32(bmg_problem* p, int f, int level, float* X, const float* B, const float* sft,
+                                     int k, int ld, int smoother, int nu, double omega, float* work, void* stream) {
+  return guarded([&] {
+    check_levels(p, f, level);
+    if (f < 2) fail(BMG_ERR_INVALID_ARG, "f must be >= 2");
+    if (!X || !sft || k < 1 || ld < k || (ld & 3) || nu < 0) fail(BMG_ERR_INVALID_ARG, "bad block arguments (ld % 4 == 0)");
+    ensure_ops32(p);
+    cudaStream_t s = (cudaStream_t)stream;
+    const Mesh& m = p->meshOf(level);
+    const float *a = Ops<float>::A(p, f, level), *mm = Ops<float>::M(p, f, level);
+    const float *da = Ops<float>::DA(p, f, level), *dm = Ops<float>::DM(p, f, level);
+    if (smoother == BMG_SMOOTH_JACOBI) {
+      if (!work) fail(BMG_ERR_INVALID_ARG, "Jacobi needs a work block");
+      for (int it = 0; it < nu; ++it) {
+        jacobi_sweep<float>(m, a, mm, da, dm, X, work, B, sft, ld, omega, s);
+        BMG_CUDA(cudaMemcpyAsync(X, work, sizeof(float) * (size_t)m.n * ld, cudaMemcpyDeviceToDevice, s));
+      }
+    } else if (smoother == BMG_SMOOTH_MCGS || smoother == BMG_SMOOTH_MCSGS) {
+      const Level& lv = p->lev[level];
+      for (int it = 0; it < nu; ++it) {
+        for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep<float>(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
+        if (smoother == BMG_SMOOTH_MCSGS)
+          for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep<float>(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
+      }
+    } else {
+      fail(BMG_ERR_INVALID_ARG, "unknown smoother");
+    }
+  });
+}
+
+extern "C" bmg_status bmg_gram_f32(const float* X, const float* Y, int n, int k, int ld, double* G, void* stream) {
+  return guarded([&] {
+    if (!X || !Y || !G || n < 1 || k < 1 || k > 160 || ld < k || (ld & 3))
+      fail(BMG_ERR_INVALID_ARG, "bad gram arguments (1 <= k <= 160, ld % 4 == 0)");
+    const int parts = gram_parts(n);
+    DBuf<double> partial((size_t)parts * k * k);
+    gram(X, Y, n, k, ld, G, partial.get(), parts, (cudaStream_t)stream);
+    BMG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  });
 }

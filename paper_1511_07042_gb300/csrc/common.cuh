@@ -86,6 +86,11 @@ struct OpSet {
   DBuf<double> da, dm;   // [n_l] diagonals
 };
 
+// float32 copies of one OpSet (precision form).
+struct OpSet32 {
+  DBuf<float> a, m, da, dm;
+};
+
 struct Level {
   int refinement = 0;
   int n_colours = 0;
@@ -120,6 +125,10 @@ struct SolveWork {
   DBuf<double> Ahat, Mhat, Y, theta, lam, shift, GA, GM, dense, partial, res;
   DBuf<int> rank;
   DBuf<double> dquality;                    // error estimate of the last enriched eigensolve
+  // float32 blocks of the precision form (allocated on first use), ld32 % 4 == 0
+  int ld32 = 0;
+  DBuf<float> X32, AX32, MX32, U32, AU32, MU32, B32, W32, Zf32, shift32;
+  std::vector<DBuf<float>> cA32, cB32, cC32, cD32;
   std::vector<DBuf<double>> AQ, MQ;         // per f: dense n1 x n1 coarse blocks
   std::vector<std::vector<double>> ratio;   // [f][j] max_i dM_i / dA_i
   double* hbuf = nullptr;                   // pinned host staging (res, lam, quality, rank)
@@ -140,6 +149,9 @@ struct bmg_problem {
   // the assembled matrices through pointers below.
   std::vector<std::vector<bmg::OpSet>> ops;
   std::vector<double> norm1;        // ||A_f||_1 per level (host)
+  // float32 copies of every operator set, ops32[f][j] for j <= f (j == f: the
+  // assembled matrices); built on the first precision-form call.
+  std::vector<std::vector<bmg::OpSet32>> ops32;
   std::unique_ptr<bmg::SolveWork> ws;  // cached solve workspace
   bmg::Mesh& meshOf(int level) { return mesh[r0 + level - 1]; }
   const bmg::Mesh& meshOf(int level) const { return mesh[r0 + level - 1]; }
@@ -169,32 +181,46 @@ void fill_sh_constants(double* c17);
 void project_input(Mesh& m, double amplitude, const double* sh_consts_dev,
                    const double* coefs_dev, cudaStream_t s);
 
-// cycle steps (ops.cu)
-void spmm_am(const Mesh& m, const double* a, const double* mm, const double* X, int ld,
-             double* AX, double* MX, cudaStream_t s);
-void jacobi_sweep(const Mesh& m, const double* a, const double* mm, const double* da,
-                  const double* dm, const double* X, double* Xout, const double* B,
-                  const double* shift, int ld, double omega, cudaStream_t s);
-void gs_colour_sweep(const Mesh& m, const Level& lv, int colour, const double* a,
-                     const double* mm, const double* da, const double* dm, double* X,
-                     const double* B, const double* shift, int ld, cudaStream_t s);
-void residual(const Mesh& m, const double* a, const double* mm, const double* X,
-              const double* B, const double* shift, int ld, double* R, cudaStream_t s);
-void prolong(const Mesh& fine, const double* Xc, double* Y, int ld, bool add, cudaStream_t s);
-void restrict_(const Mesh& coarse, const double* R, double* Zc, int ld, cudaStream_t s);
+// cycle steps (ops.cu), for FP64 blocks (T = double) and FP32 blocks (T = float);
+// an FP32 block has ld % 4 == 0, an FP64 block ld % 2 == 0.
+template <typename T>
+void spmm_am(const Mesh& m, const T* a, const T* mm, const T* X, int ld, T* AX, T* MX, cudaStream_t s);
+template <typename T>
+void jacobi_sweep(const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const T* X,
+                  T* Xout, const T* B, const T* shift, int ld, double omega, cudaStream_t s);
+template <typename T>
+void gs_colour_sweep(const Mesh& m, const Level& lv, int colour, const T* a, const T* mm,
+                     const T* da, const T* dm, T* X, const T* B, const T* shift, int ld,
+                     cudaStream_t s);
+template <typename T>
+void residual(const Mesh& m, const T* a, const T* mm, const T* X, const T* B, const T* shift,
+              int ld, T* R, cudaStream_t s);
+template <typename T>
+void prolong(const Mesh& fine, const T* Xc, T* Y, int ld, bool add, cudaStream_t s);
+template <typename T>
+void restrict_(const Mesh& coarse, const T* R, T* Zc, int ld, cudaStream_t s);
 void gram(const double* X, const double* Y, int n, int k, int ld, double* G, double* partial,
           int nparts, cudaStream_t s);
+void gram(const float* X, const float* Y, int n, int k, int ld, double* G, double* partial,
+          int nparts, cudaStream_t s);
 int gram_parts(int n);
-void eig_residuals(const double* AU, const double* MU, const double* U, const double* lam, int n,
-                   int k, int ld, double* partial, int nparts, double* out, cudaStream_t s);
-void expand(const double* Zf, const double* X, const double* Yx, int n, int k, int ld,
-            int ldy, double* U, cudaStream_t s);
-void scale_rhs(const double* MU, const double* theta, int n, int k, int ld, double* B,
-               cudaStream_t s);
-void axpy_block(double* Y, const double* X, int n, int ld, cudaStream_t s);
+template <typename T>
+void eig_residuals(const T* AU, const T* MU, const T* U, const double* lam, int n, int k, int ld,
+                   double* partial, int nparts, double* out, cudaStream_t s);
+template <typename T>
+void expand(const T* Zf, const T* X, const double* Yx, int n, int k, int ld, int ldy, T* U,
+            cudaStream_t s);
+template <typename T>
+void scale_rhs(const T* MU, const double* theta, int n, int k, int ld, T* B, cudaStream_t s);
 
 // dense (dense.cu)
+// drop_tol: pivots of the unit-diagonal M-hat below it are dropped (kDropFP64 for
+// float64 data; kDropFP32 when the enriched matrices come from float32 blocks, whose
+// entries carry relative errors near 1e-7 so that smaller pivots are noise).
+constexpr double kDropFP64 = 1e-12;
+constexpr double kDropFP32 = 1e-5;
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k,
-               double* theta, double* Y, int* rank, double* work, double* quality, cudaStream_t s);
+               double* theta, double* Y, int* rank, double* work, double* quality, double drop_tol,
+               cudaStream_t s);
 size_t dense_work_doubles(int n);
 }  // namespace bmg

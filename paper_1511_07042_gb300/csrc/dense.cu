@@ -31,7 +31,6 @@
 namespace bmg {
 namespace {
 
-constexpr double kDropTol = 1e-12;
 constexpr double kClusterFloor = 1e-3;   // relative gap below which the FP32 start cannot separate pairs
 constexpr double kGuard = 0.05;          // largest first-order correction accepted by a step
 constexpr int kMaxN = 320;
@@ -98,7 +97,7 @@ __device__ __forceinline__ unsigned long long pivot_key(double v) {
   return (b > 0 && b <= 0x7FF0000000000000LL) ? (unsigned long long)b : 0ull;
 }
 __global__ void __launch_bounds__(kBig)
-basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS) {
+basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS, double drop_tol) {
   extern __shared__ double dsm[];
   double* S = smemS ? dsm : w.S;
   __shared__ unsigned long long wk[32];
@@ -149,7 +148,7 @@ basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS) {
       }
       if (lane == 0) {
         const double piv = __longlong_as_double((long long)best);
-        const int go = piv > kDropTol;
+        const int go = piv > drop_tol;
         s_go = go;
         s_p = bi;
         if (go) {
@@ -261,6 +260,21 @@ trsm_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mhat, in
 }
 
 // ---------------------------------------------- 3. FP32 eigensolve (1 CTA) -----
+// Start vectors of the inverse iteration: zero-mean pseudo-random values in [-1, 1)
+// from an integer hash of (row, column).  Vectors with a common positive component
+// project almost parallel onto a near-degenerate group, and the last member of the
+// group then keeps almost nothing after orthogonalisation.
+__device__ __forceinline__ float start_value(int a, int j) {
+  unsigned x = ((unsigned)a * 0x9E3779B1u) ^ ((unsigned)(j + 1) * 0x85EBCA77u);
+  x ^= x >> 15;
+  x *= 0x2C1B3C6Du;
+  x ^= x >> 12;
+  x *= 0x297A2D39u;
+  x ^= x >> 15;
+  return (float)(x >> 8) * (1.0f / 8388608.0f) - 1.0f;
+}
+// Solves per eigenvector (each followed by orthonormalisation inside the clusters).
+constexpr int kInvIters = 3;
 __global__ void __launch_bounds__(kBig)
 eig32_kernel(int n, int zsmem, DW w) {
   extern __shared__ float fsm[];
@@ -380,17 +394,17 @@ eig32_kernel(int n, int zsmem, DW w) {
   __syncthreads();
   // --- inverse iteration, block form of the scheme of LAPACK's stein.  Clusters are
   // chains of eigenvalues closer than 1e-4 span; members of a cluster get shifts at
-  // least eps_sep apart.  Thread j factors T3 - x_j I (LU with partial pivoting, the
+  // least 10 ulps apart.  Thread j factors T3 - x_j I (LU with partial pivoting, the
   // factors in global scratch, planes [5][row][j]) and solves for column j of Z; after
-  // each of the two solves the columns are scaled by their largest entry, and one
-  // warp per cluster orthonormalises the members in order (modified Gram-Schmidt).
-  // All eigenvectors advance together, so the sequential work is one factorisation
-  // and two solves of length r, not one per member of the largest cluster.
+  // each of the kInvIters solves the columns are scaled by their largest entry, and
+  // one warp per cluster orthonormalises the members in order (modified
+  // Gram-Schmidt).  All eigenvectors advance together, so the sequential work is one
+  // factorisation and kInvIters solves of length r, not one per member of the
+  // largest cluster.
   __shared__ int cst[kMaxN + 1];
   __shared__ int s_ncl;
   const float ortol = 1e-4f * span;
-  const float eps_sep = 10.f * 1.2e-7f * span;
-  const float tiny = fmaxf(eps_sep * 1e-3f, pivmin);
+  const float tiny = fmaxf(1.2e-9f * span, pivmin);
   float* shift = vb;   // the tridiagonalisation is done with vb
   if (tid == 0) {
     int nc = 0;
@@ -398,8 +412,12 @@ eig32_kernel(int n, int zsmem, DW w) {
     float xprev = -3.4e38f;
     for (int i = 0; i < r; ++i) {
       float x = lam[i];
+      // shifts of one cluster at least 10 ulps (of x) apart, as LAPACK's stein does;
+      // a separation relative to the whole span would push the members of a tight
+      // subgroup towards the next subgroup of the same cluster
+      const float sep = 1.2e-6f * fmaxf(fabsf(x), 1e-6f * span);
       if (i > 0 && !(lam[i] - lam[i - 1] <= ortol)) cst[++nc] = i;
-      else if (i > 0 && x - xprev < eps_sep) x = xprev + eps_sep;
+      else if (i > 0 && x - xprev < sep) x = xprev + sep;
       shift[i] = x;
       xprev = x;
     }
@@ -440,9 +458,9 @@ eig32_kernel(int n, int zsmem, DW w) {
       LU[o] = __frcp_rn((fabsf(p0) < tiny) ? ((p0 < 0.f) ? -tiny : tiny) : p0);
       LU[pl + o] = 0.f;
       LU[2 * pl + o] = 0.f;
-      for (int a = 0; a < r; ++a) Z[a * r + jv] = 1.f / (1.f + (float)((a * 7 + jv * 13) % 17));
+      for (int a = 0; a < r; ++a) Z[a * r + jv] = start_value(a, jv);
     }
-    for (int itr = 0; itr < 2; ++itr) {
+    for (int itr = 0; itr < kInvIters; ++itr) {
       if (tid < r) {
         const int jv = tid;
         float* Zc = Z + jv;
@@ -958,7 +976,7 @@ size_t dense_work_doubles(int n) {
 }
 
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k, double* theta,
-               double* Y, int* rank, double* work, double* quality, cudaStream_t s) {
+               double* Y, int* rank, double* work, double* quality, double drop_tol, cudaStream_t s) {
   if (n < 1 || n > kMaxDense || k < 1 || k > n) fail(BMG_ERR_INVALID_ARG, "dense_eig: need 1 <= k <= n <= 224");
   prof_begin(KC_DENSE, s);
   DW w = carve(work, n);
@@ -966,7 +984,7 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
   const size_t smemS = (size_t)n * n * sizeof(double);
   const bool useS = smemS <= 200 * 1024;
   if (useS) BMG_CUDA(cudaFuncSetAttribute(basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemS));
-  basis_kernel<<<1, kBig, useS ? smemS : 0, s>>>(Mhat, n, w, useS ? 1 : 0);
+  basis_kernel<<<1, kBig, useS ? smemS : 0, s>>>(Mhat, n, w, useS ? 1 : 0, drop_tol);
   check_launch("basis_kernel");
   // 2. reduced standard matrix
   trsm_kernel<<<n, 32, 0, s>>>(Ahat, Mhat, n, sigma, 0, w);

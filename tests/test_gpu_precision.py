@@ -1,0 +1,175 @@
+"""Precision form (float32 blocks; float64 Grams, eigensolve and final cycles).
+
+Per-kernel parity of the float32 SpMM and smoothers against the FP64 oracle applied
+to the same float32-rounded inputs (tolerances from float32 rounding: at most a few
+units of 2^-24 of the magnitudes involved), accuracy of the compensated float32 Gram
+against the exact products, and end-to-end solves whose per-eigenvalue error
+against the FP64 oracle or dense LAPACK is checked."""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import bmg as obmg, certify, multilevel
+from paper_1511_07042_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+R = 4
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def env(gpu_bmg):
+    v, t = inputs.icosahedron()
+    prob = gpu_bmg.Problem(v, t, R)
+    prob.hierarchy(R)
+    H = obmg.build_hierarchy(v, t, R)
+    return gpu_bmg, prob, H
+
+
+def dev32(X, ld=None):
+    n, k = X.shape
+    ld = ld or (k + 3) // 4 * 4
+    T = torch.zeros((n, ld), dtype=torch.float32, device="cuda")
+    T[:, :k] = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+    return T
+
+
+def host(T, k):
+    torch.cuda.synchronize()
+    return T[:, :k].cpu().numpy().astype(np.float64)
+
+
+def f32(X):
+    return np.asarray(X, dtype=np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("k", [3, 20, 64, 130])
+@pytest.mark.parametrize("f,l", [(4, 4), (4, 2), (3, 1)])
+def test_spmm_f32(env, k, f, l):
+    bmg, prob, H = env
+    A = H.A[l] if f == l else H.GA[f][l]
+    M = H.M[l] if f == l else H.GM[f][l]
+    X = f32(np.random.default_rng(k + 10 * l).standard_normal((A.shape[0], k)))
+    Xd = dev32(X)
+    AX, MX = torch.empty_like(Xd), torch.empty_like(Xd)
+    prob.spmm_f32(f, l, Xd, k, AX, MX)
+    # float32 matrix values, products and at most 7 sums: 16 units of 2^-24 of |A||X|
+    for got, Op in ((host(AX, k), A), (host(MX, k), M)):
+        bound = 16 * 2.0 ** -24 * (abs(Op) @ np.abs(X)) + 1e-38
+        assert np.all(np.abs(got - Op @ X) <= bound)
+    assert torch.all(AX[:, k:] == 0) and torch.all(MX[:, k:] == 0)
+
+
+@pytest.mark.parametrize("k", [3, 20, 64])
+@pytest.mark.parametrize("smoother,nu,omega", [("jacobi", 2, 2 / 3), ("mcsgs", 1, 1.0)])
+@pytest.mark.parametrize("with_b", [True, False])
+def test_smoothers_f32(env, k, smoother, nu, omega, with_b):
+    bmg, prob, H = env
+    f = l = 4
+    A, M = H.A[l], H.M[l]
+    rng = np.random.default_rng(300 + k)
+    X = f32(rng.standard_normal((A.shape[0], k)))
+    B = f32(rng.standard_normal((A.shape[0], k))) if with_b else np.zeros_like(X)
+    s = f32(rng.uniform(0.0, 20.0, k))
+    Xd, Bd = dev32(X), dev32(B)
+    sd = torch.zeros(Xd.shape[1], dtype=torch.float32, device="cuda")
+    sd[:k] = torch.from_numpy(s.astype(np.float32)).cuda()
+    work = torch.empty_like(Xd)
+    prob.smooth_f32(f, l, Xd, Bd if with_b else None, sd, k, smoother, nu, omega, work)
+    if smoother == "jacobi":
+        ref = multilevel.jacobi(A, M, X, B, s, omega, nu)
+    else:
+        ref = multilevel.mc_gauss_seidel(A, M, X, B, s, H.colour[l], nu, symmetric=True)
+    # a sweep is a contraction of float32-rounded updates: relative 1e-5 of the block
+    assert np.max(np.abs(host(Xd, k) - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("k", [1, 3, 20, 64, 128, 130, 160])
+@pytest.mark.parametrize("n", [1, 1000, 200003])
+def test_gram_f32_compensated(gpu_bmg, k, n):
+    rng = np.random.default_rng(7 * k + n)
+    # rows spanning six decades, so that plain float32 sums would lose ~1e-5
+    scale = 10.0 ** rng.uniform(-3, 3, n)[:, None]
+    X = f32(rng.standard_normal((n, k)) * scale)
+    Y = f32(rng.standard_normal((n, k)) * scale)
+    G = torch.empty((k, k), dtype=torch.float64, device="cuda")
+    gpu_bmg.gram_f32(dev32(X), dev32(Y), k, G)
+    torch.cuda.synchronize()
+    G = G.cpu().numpy()
+    absdot = np.abs(X).T @ np.abs(Y)
+    # float32 products are exact in float64; float64 BLAS sums err by <~ 1e-14 here
+    assert np.all(np.abs(G - X.T @ Y) <= 1e-12 * absdot + 1e-300)
+    # a few entries against the correctly rounded sum of the exact products
+    for i, j in [(0, 0), (k - 1, 0), (k // 2, k - 1)]:
+        exact = math.fsum((X[:, i] * Y[:, j]).tolist())
+        assert abs(G[i, j] - exact) <= 1e-13 * absdot[i, j] + 1e-300
+
+
+def solve(bmg, R, k, nw, sigma, tol, colour=False, **kw):
+    v, t = inputs.icosahedron()
+    prob = bmg.Problem(v, t, R)
+    prob.hierarchy(R)
+    X0 = inputs.gaussian_block(inputs.n_vertices(2), k, 1001)
+    ev, U, rs, info = prob.solve(X0, k, nw, sigma, tol, bmg.options(precision="fp32", **kw))
+    return ev, U, rs, info, prob
+
+
+@pytest.mark.parametrize("kw", [dict(smoother="jacobi", nu=2, omega=2 / 3),
+                                dict(smoother="mcsgs", nu=1, omega=1.0)])
+def test_precision_form_sphere642_matches_dense(gpu_bmg, kw):
+    ev, U, rs, info, _ = solve(gpu_bmg, 3, 20, 16, 0.0, 1e-10, **kw)
+    assert info.converged == 1 and 0 < info.fp32_cycles < info.total_cycles
+    H = obmg.build_hierarchy(*inputs.icosahedron(), 3, colour=False)
+    A, M = H.A[3], H.M[3]
+    w, V = certify.dense_pencil_eigs(A, M)
+    err, ang = certify.compare_to_reference(M, ev, U, w[:16], V[:, :16])
+    assert err.max() <= 1e-10 and ang.max() <= 1e-8
+    assert np.all(obmg.residuals(A, M, U, ev) <= 1e-9)
+
+
+def test_precision_form_float32_only(gpu_bmg):
+    """A tolerance above the hand-over residual is met by float32 cycles alone."""
+    ev, U, rs, info, _ = solve(gpu_bmg, 3, 20, 16, 0.0, 1e-5, switch_tol=1e-6)
+    assert info.converged == 1 and info.fp32_cycles == info.total_cycles
+    H = obmg.build_hierarchy(*inputs.icosahedron(), 3, colour=False)
+    A, M = H.A[3], H.M[3]
+    w = certify.dense_pencil_eigs(A, M)[0]
+    assert np.all(obmg.residuals(A, M, U, ev) <= 2e-5)
+    assert np.max(np.abs(np.sort(ev) - w[:16]) / np.maximum(w[:16], 1)) <= 1e-5
+
+
+def test_precision_form_sphere40962(gpu_bmg):
+    """Full 6-level sphere in the precision form against the oracle's FP64 BFMG."""
+    ev, U, rs, info, _ = solve(gpu_bmg, 6, 64, 49, 0.0, 1e-10, smoother="mcsgs", nu=1, omega=1.0)
+    assert info.converged == 1 and info.fp32_cycles > 0
+    v, t = inputs.icosahedron()
+    H = obmg.build_hierarchy(v, t, 6)
+    A, M = H.A[6], H.M[6]
+    assert np.all(obmg.residuals(A, M, U, ev) <= 1e-9)
+    assert np.allclose(U.T @ (M @ U), np.eye(49), atol=1e-9)
+    X0 = inputs.gaussian_block(inputs.n_vertices(2), 64, 1001)
+    ref = obmg.bfmg(H, X0, 64, 49, 0.0, 1e-10, obmg.Options(smoother="mcsgs", nu=1, omega=1.0))
+    lam = np.sort(ev)
+    assert np.max(np.abs(lam - np.sort(ref.lam[:49])) / np.maximum(np.abs(lam), 1)) <= 1e-10
+
+
+def test_precision_form_sphere655362_k128(gpu_bmg):
+    """The 8-level, k=128 workload of the precision form: each of the 100 wanted
+    eigenvalues against the FP64 oracle's reference values (tests/golden)."""
+    path = os.path.join(GOLDEN, "sphere655362_k128_mixed_oracle_eigs.txt")
+    ref = np.loadtxt(path)[:, 1]
+    wl = inputs.WORKLOADS["sphere655362_k128_mixed"]
+    v, t = inputs.icosahedron()
+    prob = gpu_bmg.Problem(v, t, wl["refinements"])
+    prob.hierarchy(wl["refinements"])
+    X0 = inputs.gaussian_block(inputs.n_vertices(2), wl["k"], wl["seed"])
+    opt = gpu_bmg.options(smoother=wl["smoother"], nu=wl["nu"], omega=wl["omega"], precision="fp32")
+    ev, U, rs, info = prob.solve(X0, wl["k"], wl["n_wanted"], wl["sigma"], wl["tol"], opt, evecs=False)
+    assert info.converged == 1 and info.fp32_cycles > 0 and np.all(rs <= wl["tol"])
+    err = np.abs(np.sort(ev) - np.sort(ref)) / np.maximum(np.abs(ref), 1.0)
+    print("precision form, per-eigenvalue relative error vs FP64 oracle: max %.3e median %.3e"
+          % (err.max(), np.median(err)))
+    assert err.max() <= 1e-9
