@@ -84,7 +84,7 @@ typedef struct {
 
 /* Fills the defaults: Jacobi, nu=2, omega=2/3, shifted form, full depth,
  * 6 intermediate cycles, no intermediate tolerance, 200 finest cycles, float64,
- * switch_tol 1e-6.                                                              */
+ * switch_tol 1e-7 (near the float32 floor of the relative residual).           */
 void bmg_default_options(bmg_options* opt);
 
 typedef struct bmg_problem bmg_problem;
@@ -97,6 +97,10 @@ typedef struct {
   double max_resid;          /* largest wanted relative residual at exit          */
   double max_dense_err;      /* largest error estimate of the enriched eigensolve */
   int fp32_cycles;           /* cycles run with float32 blocks (all levels)       */
+  int n_history;             /* entries filled below (the first 256 cycles)       */
+  int history_level[256];    /* level of each cycle                               */
+  int history_fp32[256];     /* 1 if the cycle ran with float32 blocks            */
+  double history_resid[256]; /* largest wanted relative residual after the cycle  */
 } bmg_solve_info;
 
 /* ---------------------------------------------------------------- set-up ----- */
@@ -160,6 +164,25 @@ bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigma, double t
                      const bmg_options* opt, const double* X0, int x0_on_device,
                      double* evals, double* evecs, int evecs_on_device, double* resid,
                      bmg_solve_info* info);
+
+/* Batched form: n_jobs independent solves, job j = (problems[j], sigmas[j]), all with
+ * the same k, n_wanted, tol and options (Sec. 4.1 problem statement, once per job).
+ * The same problem may appear in several jobs (e.g. one per shift); problems of
+ * different sizes mix freely.  Jobs run concurrently on up to `concurrency` streams
+ * of the current device (<= 0: min(n_jobs, 64)), one host worker thread per stream,
+ * so that the single-block kernels of small levels and of the enriched eigensolves
+ * of different jobs overlap on the GPU.  Each job's results are those bmg_solve
+ * gives for it (the same kernels and reduction orders).
+ *   X0[j] [N_2][k] host; evals[j] [n_wanted] host; evecs[j] [N_L][n_wanted] host or
+ *   evecs == NULL; resid[j] [n_wanted] host or resid == NULL; infos [n_jobs] or NULL.
+ * Per-problem workspaces (one per job of that problem) are kept between calls.
+ * Synchronous.  Returns the first failing job's status (message names the job),
+ * else BMG_ERR_NOT_CONVERGED if a job hit its cycle cap, else BMG_OK.            */
+bmg_status bmg_solve_batched(int n_jobs, bmg_problem* const* problems, const double* sigmas,
+                             int k, int n_wanted, double tol, const bmg_options* opt,
+                             const double* const* X0, double* const* evals,
+                             double* const* evecs, double* const* resid,
+                             bmg_solve_info* infos, int concurrency);
 
 /* ---------------------------------------------- inspection (host outputs) --- */
 

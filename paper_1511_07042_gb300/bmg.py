@@ -41,7 +41,13 @@ class Options(C.Structure):
 class SolveInfo(C.Structure):
     _fields_ = [("levels", C.c_int), ("cycles", C.c_int * 32), ("total_cycles", C.c_int),
                 ("converged", C.c_int), ("max_resid", C.c_double), ("max_dense_err", C.c_double),
-                ("fp32_cycles", C.c_int)]
+                ("fp32_cycles", C.c_int), ("n_history", C.c_int), ("history_level", C.c_int * 256),
+                ("history_fp32", C.c_int * 256), ("history_resid", C.c_double * 256)]
+
+    def history(self):
+        """[(level, fp32, max wanted residual)] per cycle (first 256 cycles)."""
+        return [(self.history_level[q], self.history_fp32[q], self.history_resid[q])
+                for q in range(self.n_history)]
 
 
 def _load():
@@ -58,6 +64,8 @@ def _load():
         "bmg_assemble": (i, [vp, i, vp, i, i, d, vp, vp, P(vp)]),
         "bmg_hierarchy": (i, [vp, i]),
         "bmg_solve": (i, [vp, i, i, d, d, P(Options), vp, i, vp, vp, i, vp, P(SolveInfo)]),
+        "bmg_solve_batched": (i, [i, P(vp), P(C.c_double), i, i, d, P(Options), P(vp), P(vp), P(vp), P(vp),
+                                  P(SolveInfo), i]),
         "bmg_get_sizes": (i, [vp, i, P(C.c_int), P(C.c_int), P(C.c_int)]),
         "bmg_get_mesh": (i, [vp, i, vp, vp, vp]),
         "bmg_get_csr": (i, [vp, i, vp, vp, vp, vp]),
@@ -119,7 +127,7 @@ def _stream():
 
 def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_depth=99,
             cycles_intermediate=6, tol_intermediate=-1.0, max_cycles=200, precision="fp64",
-            switch_tol=1e-6) -> Options:
+            switch_tol=1e-7) -> Options:
     o = Options()
     LIB.bmg_default_options(C.byref(o))
     o.smoother = SMOOTHERS[smoother]
@@ -252,6 +260,27 @@ class Problem:
         if code not in (0, 5):
             _check(code)
         return ev, U, rs, info
+
+
+def solve_batched(problems, sigmas, X0s, k, n_wanted, tol, opt=None, evecs=False, concurrency=0):
+    """Batched form: job j solves problems[j] near sigmas[j] from X0s[j] (numpy
+    [N_2, k]).  Returns (evals list, evecs list or None, resid list, infos, status)
+    where status is 0 or 5 (some job hit its cycle cap)."""
+    n = len(problems)
+    x0 = [np.ascontiguousarray(x, dtype=np.float64) for x in X0s]
+    ev = [np.empty(n_wanted) for _ in range(n)]
+    rs = [np.empty(n_wanted) for _ in range(n)]
+    U = [np.empty((p.sizes(p.refinements)[0], n_wanted)) for p in problems] if evecs else None
+    infos = (SolveInfo * n)()
+    arr = lambda xs: (C.c_void_p * n)(*[_ptr(x) for x in xs])
+    o = opt if opt is not None else options()
+    code = LIB.bmg_solve_batched(n, (C.c_void_p * n)(*[p.h for p in problems]),
+                                 (C.c_double * n)(*[float(x) for x in sigmas]), k, n_wanted, float(tol),
+                                 C.byref(o), arr(x0), arr(ev), arr(U) if evecs else None, arr(rs), infos,
+                                 int(concurrency))
+    if code not in (0, 5):
+        _check(code)
+    return ev, U, rs, list(infos), code
 
 
 KERNEL_CLASSES = 8

@@ -12,10 +12,12 @@
 //      levels (Galerkin operators) prolonged back        (Alg. 3 step 3, Eq. pb-m-s)
 // Between levels the Ritz vectors are prolongated (Alg. 4 step 3, Eq. proj-1).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -108,7 +110,7 @@ extern "C" void bmg_default_options(bmg_options* o) {
   o->tol_intermediate = -1.0;
   o->max_cycles = 200;
   o->precision = BMG_PREC_FP64;
-  o->switch_tol = 1e-6;
+  o->switch_tol = 1e-7;
 }
 
 extern "C" const char* bmg_last_error(void) { return g_last_error.c_str(); }
@@ -446,7 +448,7 @@ Blocks<double> blocks64(SolveWork& w) {
 }
 
 Blocks<float> blocks32(bmg_problem* p, SolveWork& w) {
-  cudaStream_t s = p->stream;
+  cudaStream_t s = w.s;
   if (!w.ld32) {
     w.ld32 = (w.k + 3) & ~3;
     const size_t big = (size_t)p->meshOf(w.L).n * w.ld32;
@@ -560,15 +562,13 @@ void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, cons
   }
 }
 
-// Allocates (or reuses) the solve workspace for block size k.
-SolveWork& workspace(bmg_problem* p, int k) {
-  if (p->ws && p->ws->k == k) return *p->ws;
-  p->ws.reset();
-  cudaStream_t s = p->stream;
+// Allocates a solve workspace for block size k; its set-up work runs on stream s.
+std::unique_ptr<SolveWork> make_work(bmg_problem* p, int k, cudaStream_t s) {
   const int L = p->L;
   const int n1 = p->meshOf(1).n, nL = p->meshOf(L).n;
   std::unique_ptr<SolveWork> wp(new SolveWork());
   SolveWork& w = *wp;
+  w.s = s;
   w.k = k;
   w.ld = (k + 1) & ~1;
   w.n1 = n1;
@@ -626,8 +626,23 @@ SolveWork& workspace(bmg_problem* p, int k) {
       BMG_CUDA(cudaStreamSynchronize(s));
       std::memcpy(&w.ratio[f][j], &h, sizeof(double));
     }
-  p->ws = std::move(wp);
-  return *p->ws;
+  return wp;
+}
+
+// Workspace slot `slot` of problem p for block size k (slot 0 is the one of
+// bmg_solve), kept between calls; its solves run on stream s.
+SolveWork& workspace(bmg_problem* p, int k, int slot, cudaStream_t s) {
+  std::unique_ptr<SolveWork>* wp = &p->ws;
+  if (slot > 0) {
+    if ((int)p->ws_more.size() < slot) p->ws_more.resize(slot);
+    wp = &p->ws_more[slot - 1];
+  }
+  if (!*wp || (*wp)->k != k) {
+    wp->reset();
+    *wp = make_work(p, k, s);
+  }
+  (*wp)->s = s;
+  return **wp;
 }
 
 // Outcome of one cycle: Ritz values, residuals and convergence of the wanted pairs.
@@ -642,7 +657,7 @@ struct CycleState {
 template <typename T>
 bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_options& o, double sigma, int k,
                int n_wanted, double ftol, bool last, CycleState& cs) {
-  cudaStream_t s = p->stream;
+  cudaStream_t s = w.s;
   const int ld = b.ld, n1 = w.n1, nh = w.nh;
   const Mesh& mf = p->meshOf(f);
   const int nf = mf.n;
@@ -748,110 +763,216 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
 }  // namespace
 }  // namespace bmg
 
+namespace bmg {
+namespace {
+
+// Argument checks shared by bmg_solve and bmg_solve_batched.
+bmg_options checked_options(const bmg_problem* p, int k, int n_wanted, double sigma, double tol,
+                            const bmg_options* opt_in, const double* X0, const double* evals) {
+  if (!p) fail(BMG_ERR_INVALID_ARG, "null problem");
+  if (!p->L) fail(BMG_ERR_STATE, "bmg_hierarchy not called");
+  bmg_options o;
+  bmg_default_options(&o);
+  if (opt_in) o = *opt_in;
+  const int n1 = p->meshOf(1).n, n2 = p->meshOf(2).n;
+  if (k < 1 || k > 160 || n_wanted < 1 || n_wanted > k || k > n2 || n1 + k > 224)
+    fail(BMG_ERR_INVALID_ARG, "need 1 <= n_wanted <= k <= min(N_2, 160) and N_1 + k <= 224");
+  if (!X0 || !evals) fail(BMG_ERR_INVALID_ARG, "X0 and evals are required");
+  if (!(tol > 0.0) || !std::isfinite(sigma)) fail(BMG_ERR_INVALID_ARG, "bad tol or sigma");
+  if (o.nu < 1 || o.nu > 64 || o.smoother < 0 || o.smoother > 2 || o.form < 0 || o.form > 1 ||
+      o.max_cycles < 1 || o.cycles_intermediate < 1 || !(o.omega > 0.0) || o.precision < 0 ||
+      o.precision > 1 || !(o.switch_tol > 0.0))
+    fail(BMG_ERR_INVALID_ARG, "bad options");
+  return o;
+}
+
+// The BFMG solve (Alg. 4) of one problem and shift on the workspace w and its stream.
+// Returns whether every wanted pair met tol; throws BmgException on errors.
+bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma, double tol,
+                const bmg_options& o, const double* X0, int x0_on_device, double* evals, double* evecs,
+                int evecs_on_device, double* resid, bmg_solve_info* info) {
+  const int L = p->L;
+  const int n2 = p->meshOf(2).n, nL = p->meshOf(L).n;
+  cudaStream_t s = w.s;
+  const int ld = w.ld;
+  Blocks<double> b64 = blocks64(w);
+  Blocks<float> b32;
+  bool fp32 = o.precision == BMG_PREC_FP32;
+  if (fp32) {
+    ensure_ops32(p);
+    b32 = blocks32(p, w);
+  }
+  // X0 -> X on level 2 (ld-strided; padding columns stay zero)
+  BMG_CUDA(cudaMemsetAsync(w.X.get(), 0, sizeof(double) * (size_t)n2 * ld, s));
+  BMG_CUDA(cudaMemcpy2DAsync(w.X.get(), sizeof(double) * ld, X0, sizeof(double) * k, sizeof(double) * k, n2,
+                             x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (fp32) convert_block(w.X.get(), ld, b32.X, b32.ld, n2, k, s);
+
+  CycleState cs;
+  cs.rho.assign(k, 0.0);
+  cs.lamv.assign(k, 0.0);
+  int total_cycles = 0, fp32_cycles = 0;
+  bool converged = false;
+  std::vector<int> cyc(L + 1, 0);
+  std::vector<double> hist;   // finest-level FP32 max residuals
+  std::vector<int> hl, hp;     // per-cycle level and arithmetic (info history)
+  std::vector<double> hr;      // per-cycle largest wanted residual
+  for (int f = 2; f <= L; ++f) {
+    const Mesh& mf = p->meshOf(f);
+    if (f > 2) {
+      if (fp32) prolong<float>(mf, b32.U, b32.X, b32.ld, false, s);
+      else prolong<double>(mf, b64.U, b64.X, ld, false, s);
+    }
+    const int budget = (f == L) ? o.max_cycles : o.cycles_intermediate;
+    const double ftol = (f == L) ? tol : o.tol_intermediate;
+    for (int c = 0; c < budget; ++c) {
+      const bool last = c + 1 == budget;
+      const bool conv = fp32 ? run_cycle<float>(p, w, b32, f, o, sigma, k, n_wanted, ftol, last, cs)
+                             : run_cycle<double>(p, w, b64, f, o, sigma, k, n_wanted, ftol, last, cs);
+      if (total_cycles < 256) {
+        double mr = 0.0;
+        for (int i = 0; i < n_wanted; ++i) mr = std::max(mr, cs.rho[i]);
+        hl.push_back(f);
+        hp.push_back(fp32 ? 1 : 0);
+        hr.push_back(mr);
+      }
+      ++total_cycles;
+      if (fp32) ++fp32_cycles;
+      cyc[f] = c + 1;
+      if (f == L) converged = conv;
+      if (conv || last) break;
+      if (fp32 && f == L) {
+        // hand-over to FP64 cycles: the FP32 residual reached switch_tol, or it
+        // did not halve over the last three cycles
+        double mr = 0.0;
+        for (int i = 0; i < n_wanted; ++i) mr = std::max(mr, cs.rho[i]);
+        hist.push_back(mr);
+        const size_t h = hist.size();
+        if (mr <= o.switch_tol || (h >= 4 && mr > 0.5 * hist[h - 4])) {
+          convert_block(b32.X, b32.ld, w.X.get(), ld, nL, ld, s);
+          fp32 = false;
+        }
+      }
+    }
+  }
+  // outputs: the last Ritz pairs on level L
+  if (fp32) convert_block(b32.U, b32.ld, w.U.get(), ld, nL, ld, s);
+  for (int i = 0; i < n_wanted; ++i) evals[i] = cs.lamv[i];
+  if (resid) for (int i = 0; i < n_wanted; ++i) resid[i] = cs.rho[i];
+  if (evecs) {
+    BMG_CUDA(cudaMemcpy2DAsync(evecs, sizeof(double) * n_wanted, w.U.get(), sizeof(double) * ld,
+                               sizeof(double) * n_wanted, nL,
+                               evecs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  }
+  BMG_CUDA(cudaStreamSynchronize(s));
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->levels = L;
+    for (int f = 2; f <= L && f - 2 < 32; ++f) info->cycles[f - 2] = cyc[f];
+    info->total_cycles = total_cycles;
+    info->fp32_cycles = fp32_cycles;
+    info->n_history = (int)hr.size();
+    for (size_t q = 0; q < hr.size(); ++q) {
+      info->history_level[q] = hl[q];
+      info->history_fp32[q] = hp[q];
+      info->history_resid[q] = hr[q];
+    }
+    info->converged = converged ? 1 : 0;
+    double mx = 0.0;
+    for (int i = 0; i < n_wanted; ++i) mx = std::max(mx, cs.rho[i]);
+    info->max_resid = mx;
+    info->max_dense_err = cs.max_dense_err;
+  }
+  return converged;
+}
+
+}  // namespace
+}  // namespace bmg
+
 extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigma, double tol,
                                 const bmg_options* opt_in, const double* X0, int x0_on_device,
                                 double* evals, double* evecs, int evecs_on_device, double* resid,
                                 bmg_solve_info* info) {
-  bmg_status final_status = BMG_OK;
+  bool converged = false;
   bmg_status st = guarded([&] {
-    if (!p) fail(BMG_ERR_INVALID_ARG, "null problem");
-    if (!p->L) fail(BMG_ERR_STATE, "bmg_hierarchy not called");
-    bmg_options o;
-    bmg_default_options(&o);
-    if (opt_in) o = *opt_in;
-    const int L = p->L;
-    const int n2 = p->meshOf(2).n, nL = p->meshOf(L).n;
-    const int n1 = p->meshOf(1).n;
-    if (k < 1 || k > 160 || n_wanted < 1 || n_wanted > k || k > n2 || n1 + k > 224)
-      fail(BMG_ERR_INVALID_ARG, "need 1 <= n_wanted <= k <= min(N_2, 160) and N_1 + k <= 224");
-    if (!X0 || !evals) fail(BMG_ERR_INVALID_ARG, "X0 and evals are required");
-    if (!(tol > 0.0) || !std::isfinite(sigma)) fail(BMG_ERR_INVALID_ARG, "bad tol or sigma");
-    if (o.nu < 1 || o.nu > 64 || o.smoother < 0 || o.smoother > 2 || o.form < 0 || o.form > 1 ||
-        o.max_cycles < 1 || o.cycles_intermediate < 1 || !(o.omega > 0.0) || o.precision < 0 ||
-        o.precision > 1 || !(o.switch_tol > 0.0))
-      fail(BMG_ERR_INVALID_ARG, "bad options");
-    cudaStream_t s = p->stream;
-    SolveWork& w = workspace(p, k);
-    const int ld = w.ld;
-    Blocks<double> b64 = blocks64(w);
-    Blocks<float> b32;
-    bool fp32 = o.precision == BMG_PREC_FP32;
-    if (fp32) {
-      ensure_ops32(p);
-      b32 = blocks32(p, w);
-    }
-    // X0 -> X on level 2 (ld-strided; padding columns stay zero)
-    BMG_CUDA(cudaMemsetAsync(w.X.get(), 0, sizeof(double) * (size_t)n2 * ld, s));
-    BMG_CUDA(cudaMemcpy2DAsync(w.X.get(), sizeof(double) * ld, X0, sizeof(double) * k, sizeof(double) * k, n2,
-                               x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-    if (fp32) convert_block(w.X.get(), ld, b32.X, b32.ld, n2, k, s);
+    const bmg_options o = checked_options(p, k, n_wanted, sigma, tol, opt_in, X0, evals);
+    SolveWork& w = workspace(p, k, 0, p->stream);
+    converged = solve_impl(p, w, k, n_wanted, sigma, tol, o, X0, x0_on_device, evals, evecs, evecs_on_device,
+                           resid, info);
+  });
+  if (st != BMG_OK) return st;
+  if (!converged) {
+    set_error("cycle cap reached before every wanted pair met tol");
+    return BMG_ERR_NOT_CONVERGED;
+  }
+  return BMG_OK;
+}
 
-    CycleState cs;
-    cs.rho.assign(k, 0.0);
-    cs.lamv.assign(k, 0.0);
-    int total_cycles = 0, fp32_cycles = 0;
-    bool converged = false;
-    std::vector<int> cyc(L + 1, 0);
-    std::vector<double> hist;   // finest-level FP32 max residuals
-    for (int f = 2; f <= L; ++f) {
-      const Mesh& mf = p->meshOf(f);
-      if (f > 2) {
-        if (fp32) prolong<float>(mf, b32.U, b32.X, b32.ld, false, s);
-        else prolong<double>(mf, b64.U, b64.X, ld, false, s);
-      }
-      const int budget = (f == L) ? o.max_cycles : o.cycles_intermediate;
-      const double ftol = (f == L) ? tol : o.tol_intermediate;
-      for (int c = 0; c < budget; ++c) {
-        const bool last = c + 1 == budget;
-        const bool conv = fp32 ? run_cycle<float>(p, w, b32, f, o, sigma, k, n_wanted, ftol, last, cs)
-                               : run_cycle<double>(p, w, b64, f, o, sigma, k, n_wanted, ftol, last, cs);
-        ++total_cycles;
-        if (fp32) ++fp32_cycles;
-        cyc[f] = c + 1;
-        if (f == L) converged = conv;
-        if (conv || last) break;
-        if (fp32 && f == L) {
-          // hand-over to FP64 cycles: the FP32 residual reached switch_tol, or it
-          // did not halve over the last three cycles
-          double mr = 0.0;
-          for (int i = 0; i < n_wanted; ++i) mr = std::max(mr, cs.rho[i]);
-          hist.push_back(mr);
-          const size_t h = hist.size();
-          if (mr <= o.switch_tol || (h >= 4 && mr > 0.5 * hist[h - 4])) {
-            convert_block(b32.X, b32.ld, w.X.get(), ld, nL, ld, s);
-            fp32 = false;
-          }
+extern "C" bmg_status bmg_solve_batched(int n_jobs, bmg_problem* const* problems, const double* sigmas, int k,
+                                        int n_wanted, double tol, const bmg_options* opt_in,
+                                        const double* const* X0, double* const* evals, double* const* evecs,
+                                        double* const* resid, bmg_solve_info* infos, int concurrency) {
+  struct Result { bmg_status code = BMG_OK; std::string msg; bool converged = false; };
+  std::vector<Result> res;
+  bmg_status st = guarded([&] {
+    if (n_jobs < 1 || !problems || !sigmas || !X0 || !evals) fail(BMG_ERR_INVALID_ARG, "bad batch arrays");
+    std::vector<bmg_options> opts(n_jobs);
+    std::vector<int> slot(n_jobs, 0);
+    for (int j = 0; j < n_jobs; ++j) {
+      opts[j] = checked_options(problems[j], k, n_wanted, sigmas[j], tol, opt_in, X0[j], evals[j]);
+      for (int q = 0; q < j; ++q) slot[j] += problems[q] == problems[j];
+    }
+    for (int j = 0; j < n_jobs; ++j)
+      if (opts[j].precision == BMG_PREC_FP32) ensure_ops32(problems[j]);
+    int dev = 0;
+    BMG_CUDA(cudaGetDevice(&dev));
+    const int nthreads = std::max(1, std::min(n_jobs, concurrency > 0 ? concurrency : 64));
+    std::vector<cudaStream_t> streams(nthreads, nullptr);
+    for (auto& st_ : streams) BMG_CUDA(cudaStreamCreateWithFlags(&st_, cudaStreamNonBlocking));
+    // workspaces are made (or found) up front: allocation and release synchronise the device
+    std::vector<SolveWork*> works(n_jobs);
+    for (int j = 0; j < n_jobs; ++j) {
+      works[j] = &workspace(problems[j], k, slot[j], streams[j % nthreads]);
+      if (opts[j].precision == BMG_PREC_FP32) blocks32(problems[j], *works[j]);
+    }
+    for (auto& st_ : streams) BMG_CUDA(cudaStreamSynchronize(st_));
+    res.assign(n_jobs, Result());
+    std::atomic<int> next{0};
+    auto worker = [&](int t) {
+      cudaSetDevice(dev);
+      for (int j = next.fetch_add(1); j < n_jobs; j = next.fetch_add(1)) {
+        try {
+          works[j]->s = streams[t];
+          res[j].converged = solve_impl(problems[j], *works[j], k, n_wanted, sigmas[j], tol, opts[j], X0[j], 0,
+                                        evals[j], evecs ? evecs[j] : nullptr, 0, resid ? resid[j] : nullptr,
+                                        infos ? infos + j : nullptr);
+        } catch (const BmgException& e) {
+          res[j].code = e.code;
+          res[j].msg = e.msg;
+        } catch (...) {
+          res[j].code = BMG_ERR_CUDA;
+          res[j].msg = "unknown error";
         }
       }
-    }
-    // outputs: the last Ritz pairs on level L
-    if (fp32) convert_block(b32.U, b32.ld, w.U.get(), ld, nL, ld, s);
-    for (int i = 0; i < n_wanted; ++i) evals[i] = cs.lamv[i];
-    if (resid) for (int i = 0; i < n_wanted; ++i) resid[i] = cs.rho[i];
-    if (evecs) {
-      BMG_CUDA(cudaMemcpy2DAsync(evecs, sizeof(double) * n_wanted, w.U.get(), sizeof(double) * ld,
-                                 sizeof(double) * n_wanted, nL,
-                                 evecs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-    }
-    BMG_CUDA(cudaStreamSynchronize(s));
-    if (info) {
-      std::memset(info, 0, sizeof(*info));
-      info->levels = L;
-      for (int f = 2; f <= L && f - 2 < 32; ++f) info->cycles[f - 2] = cyc[f];
-      info->total_cycles = total_cycles;
-      info->fp32_cycles = fp32_cycles;
-      info->converged = converged ? 1 : 0;
-      double mx = 0.0;
-      for (int i = 0; i < n_wanted; ++i) mx = std::max(mx, cs.rho[i]);
-      info->max_resid = mx;
-      info->max_dense_err = cs.max_dense_err;
-    }
-    if (!converged) {
-      final_status = BMG_ERR_NOT_CONVERGED;
-      set_error("cycle cap reached before every wanted pair met tol");
-    }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker, t);
+    worker(0);
+    for (auto& th : pool) th.join();
+    for (auto& st_ : streams) cudaStreamDestroy(st_);
   });
-  return st != BMG_OK ? st : final_status;
+  if (st != BMG_OK) return st;
+  for (int j = 0; j < n_jobs; ++j)
+    if (res[j].code != BMG_OK) {
+      set_error("job " + std::to_string(j) + ": " + res[j].msg);
+      return res[j].code;
+    }
+  for (int j = 0; j < n_jobs; ++j)
+    if (!res[j].converged) {
+      set_error("job " + std::to_string(j) + ": cycle cap reached before every wanted pair met tol");
+      return BMG_ERR_NOT_CONVERGED;
+    }
+  return BMG_OK;
 }
 
 // ---------------------------------------------- precision-form step entries ---

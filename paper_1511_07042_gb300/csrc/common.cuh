@@ -119,6 +119,7 @@ void count_launch();
 
 // Workspace of bmg_solve, kept in the problem between calls with the same k.
 struct SolveWork {
+  cudaStream_t s = nullptr;                 // stream of the solve using it
   int ld = 0, k = 0, n1 = 0, nh = 0, L = 0, parts = 0;
   DBuf<double> X, AX, MX, U, AU, MU, B, W, Zf;
   std::vector<DBuf<double>> cA, cB, cC, cD;  // per coarse level j < L: [N_j][ld]
@@ -152,7 +153,8 @@ struct bmg_problem {
   // float32 copies of every operator set, ops32[f][j] for j <= f (j == f: the
   // assembled matrices); built on the first precision-form call.
   std::vector<std::vector<bmg::OpSet32>> ops32;
-  std::unique_ptr<bmg::SolveWork> ws;  // cached solve workspace
+  std::unique_ptr<bmg::SolveWork> ws;  // cached solve workspace (bmg_solve; batch slot 0)
+  std::vector<std::unique_ptr<bmg::SolveWork>> ws_more;  // batch slots 1, 2, ...
   bmg::Mesh& meshOf(int level) { return mesh[r0 + level - 1]; }
   const bmg::Mesh& meshOf(int level) const { return mesh[r0 + level - 1]; }
   const double* opA(int f, int j) const {

@@ -25,16 +25,17 @@ struct Totals {
   long long launches = 0;
 };
 
+// Pools and totals are shared (guarded by mu); the open bracket of a launch belongs
+// to the host thread that issued it, so concurrent solves on several threads (the
+// batched entry point) time their own launches.
 struct Profiler {
   std::mutex mu;
-  bool enabled = false;
+  std::atomic<bool> enabled{false};
   std::vector<cudaEvent_t> pool;
   std::vector<Pending> pending;
-  cudaEvent_t open = nullptr;
-  int open_cls = -1;
   Totals tot[KC_COUNT];
 
-  cudaEvent_t get() {
+  cudaEvent_t get() {  // with mu held
     if (!pool.empty()) {
       cudaEvent_t e = pool.back();
       pool.pop_back();
@@ -52,6 +53,8 @@ Profiler& prof() {
 }
 
 std::atomic<long long> g_launches{0};
+thread_local cudaEvent_t t_open = nullptr;
+thread_local int t_open_cls = -1;
 
 const char* kNames[KC_COUNT] = {"spmm_am", "smooth_sweep", "residual", "transfer",
                                 "gram", "dense_eig", "expand", "small"};
@@ -63,23 +66,34 @@ void count_launch() { g_launches.fetch_add(1); }
 void prof_begin(int cls, cudaStream_t s) {
   Profiler& p = prof();
   if (!p.enabled) return;
-  p.open = p.get();
-  p.open_cls = cls;
-  check_cuda(cudaEventRecord(p.open, s), "cudaEventRecord");
+  {
+    std::lock_guard<std::mutex> lock(p.mu);
+    t_open = p.get();
+  }
+  t_open_cls = cls;
+  check_cuda(cudaEventRecord(t_open, s), "cudaEventRecord");
 }
 
 void prof_end(int cls, cudaStream_t s, double bytes, double flops) {
   Profiler& p = prof();
-  if (!p.enabled || !p.open || p.open_cls != cls) return;
-  cudaEvent_t e1 = p.get();
+  if (!p.enabled || !t_open || t_open_cls != cls) return;
+  cudaEvent_t e1;
+  {
+    std::lock_guard<std::mutex> lock(p.mu);
+    e1 = p.get();
+  }
   check_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
-  p.pending.push_back({cls, p.open, e1, bytes, flops});
-  p.open = nullptr;
-  p.open_cls = -1;
+  {
+    std::lock_guard<std::mutex> lock(p.mu);
+    p.pending.push_back({cls, t_open, e1, bytes, flops});
+  }
+  t_open = nullptr;
+  t_open_cls = -1;
 }
 
 void prof_flush() {
   Profiler& p = prof();
+  std::lock_guard<std::mutex> lock(p.mu);
   for (const Pending& q : p.pending) {
     check_cuda(cudaEventSynchronize(q.e1), "cudaEventSynchronize");
     float ms = 0.f;
@@ -115,6 +129,7 @@ extern "C" bmg_status bmg_profile_reset(void) {
   try {
     Profiler& p = prof();
     prof_flush();
+    std::lock_guard<std::mutex> lock(p.mu);
     for (auto& t : p.tot) t = Totals();
     return BMG_OK;
   } catch (...) {
