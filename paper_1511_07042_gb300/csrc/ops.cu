@@ -33,11 +33,67 @@ __device__ __forceinline__ void ldv(const float* p, size_t i, float (&v)[4]) {
   const float4 t = reinterpret_cast<const float4*>(p)[i];
   v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
 }
+// Gathers of X through the read-only path (X is not written by other threads during
+// a launch: Jacobi and the residual write another block, a Gauss-Seidel sweep writes
+// only rows of the current colour, which are never neighbours of each other).
+__device__ __forceinline__ void ldv_ro(const double* p, size_t i, double (&v)[2]) {
+  const double2 t = __ldg(reinterpret_cast<const double2*>(p) + i);
+  v[0] = t.x; v[1] = t.y;
+}
+__device__ __forceinline__ void ldv_ro(const float* p, size_t i, float (&v)[4]) {
+  const float4 t = __ldg(reinterpret_cast<const float4*>(p) + i);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+// Output rows are written once and not read again in the launch: streaming stores,
+// so that they do not evict the gathered block from L2.
+__device__ __forceinline__ void stv_cs(double* p, size_t i, const double (&v)[2]) {
+  __stcs(reinterpret_cast<double2*>(p) + i, make_double2(v[0], v[1]));
+}
+__device__ __forceinline__ void stv_cs(float* p, size_t i, const float (&v)[4]) {
+  __stcs(reinterpret_cast<float4*>(p) + i, make_float4(v[0], v[1], v[2], v[3]));
+}
 __device__ __forceinline__ void stv(double* p, size_t i, const double (&v)[2]) {
   reinterpret_cast<double2*>(p)[i] = make_double2(v[0], v[1]);
 }
 __device__ __forceinline__ void stv(float* p, size_t i, const float (&v)[4]) {
   reinterpret_cast<float4*>(p)[i] = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// aa += A_row X, mm += M_row X for one CSR row owned by a warp.  The row's pattern and
+// values are loaded once, one entry per lane (one coalesced load per array), and
+// broadcast by shuffles, so that the gathers of the neighbour rows of X do not wait
+// for the column indices one by one: the unrolled loop issues them back to back.
+template <typename T, int CPL>
+__device__ __forceinline__ void gather_row(const int* __restrict__ col, const T* __restrict__ va,
+                                           const T* __restrict__ vm, const T* __restrict__ X, int b, int e,
+                                           int nch, int lane, T (&aa)[CPL][Chunk<T>::W],
+                                           T (&mm)[CPL][Chunk<T>::W]) {
+  constexpr int W = Chunk<T>::W;
+  for (int p0 = b; p0 < e; p0 += 32) {
+    const int len = min(32, e - p0);
+    int jl = 0;
+    T al = T(0), ml = T(0);
+    if (lane < len) {
+      jl = __ldcs(col + p0 + lane);
+      al = __ldcs(va + p0 + lane);
+      ml = __ldcs(vm + p0 + lane);
+    }
+#pragma unroll 8
+    for (int q = 0; q < len; ++q) {
+      const int j = __shfl_sync(0xffffffffu, jl, q);
+      const T a = __shfl_sync(0xffffffffu, al, q), m = __shfl_sync(0xffffffffu, ml, q);
+#pragma unroll
+      for (int u = 0; u < CPL; ++u) {
+        const int c = lane + 32 * u;
+        if (c < nch) {
+          T x[W];
+          ldv_ro(X, (size_t)j * nch + c, x);
+#pragma unroll
+          for (int z = 0; z < W; ++z) { aa[u][z] = fma(a, x[z], aa[u][z]); mm[u][z] = fma(m, x[z], mm[u][z]); }
+        }
+      }
+    }
+  }
 }
 
 // ---- fused SpMM: AX = A X, MX = M X  (one pass over the shared pattern) ----
@@ -56,27 +112,13 @@ spmm_am_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
   for (int u = 0; u < CPL; ++u)
 #pragma unroll
     for (int q = 0; q < W; ++q) { aa[u][q] = T(0); mm[u][q] = T(0); }
-  const int b = row_ptr[row], e = row_ptr[row + 1];
-  for (int p = b; p < e; ++p) {
-    const int j = __ldg(col + p);
-    const T a = __ldg(va + p), m = __ldg(vm + p);
-#pragma unroll
-    for (int u = 0; u < CPL; ++u) {
-      const int c = lane + 32 * u;
-      if (c < nch) {
-        T x[W];
-        ldv(X, (size_t)j * nch + c, x);
-#pragma unroll
-        for (int q = 0; q < W; ++q) { aa[u][q] = fma(a, x[q], aa[u][q]); mm[u][q] = fma(m, x[q], mm[u][q]); }
-      }
-    }
-  }
+  gather_row<T, CPL>(col, va, vm, X, row_ptr[row], row_ptr[row + 1], nch, lane, aa, mm);
 #pragma unroll
   for (int u = 0; u < CPL; ++u) {
     const int c = lane + 32 * u;
     if (c < nch) {
-      stv(AX, (size_t)row * nch + c, aa[u]);
-      stv(MX, (size_t)row * nch + c, mm[u]);
+      stv_cs(AX, (size_t)row * nch + c, aa[u]);
+      stv_cs(MX, (size_t)row * nch + c, mm[u]);
     }
   }
 }
@@ -104,21 +146,7 @@ row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
   for (int u = 0; u < CPL; ++u)
 #pragma unroll
     for (int q = 0; q < W; ++q) { aa[u][q] = T(0); mm[u][q] = T(0); }
-  const int b = row_ptr[row], e = row_ptr[row + 1];
-  for (int p = b; p < e; ++p) {
-    const int j = __ldg(col + p);
-    const T a = __ldg(va + p), m = __ldg(vm + p);
-#pragma unroll
-    for (int u = 0; u < CPL; ++u) {
-      const int c = lane + 32 * u;
-      if (c < nch) {
-        T x[W];
-        ldv(X, (size_t)j * nch + c, x);
-#pragma unroll
-        for (int q = 0; q < W; ++q) { aa[u][q] = fma(a, x[q], aa[u][q]); mm[u][q] = fma(m, x[q], mm[u][q]); }
-      }
-    }
-  }
+  gather_row<T, CPL>(col, va, vm, X, row_ptr[row], row_ptr[row + 1], nch, lane, aa, mm);
   const T dai = da[row], dmi = dm[row];
 #pragma unroll
   for (int u = 0; u < CPL; ++u) {
@@ -136,7 +164,7 @@ row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
       for (int q = 0; q < W; ++q) r[q] += bb[q];
     }
     if (MODE == 2) {
-      stv(Out, idx, r);
+      stv_cs(Out, idx, r);
     } else {
       T x[W], o[W];
       ldv(X, idx, x);
@@ -146,7 +174,7 @@ row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
         o[q] = (MODE == 0) ? x[q] + omega * r[q] / d : x[q] + r[q] / d;
       }
       // padding columns carry zero shift, zero data and stay zero
-      stv(Out, idx, o);
+      if (MODE == 0) stv_cs(Out, idx, o); else stv(Out, idx, o);
     }
   }
 }
