@@ -184,6 +184,7 @@ extern "C" bmg_status bmg_hierarchy(bmg_problem* p, int levels) {
     for (int l = 1; l <= L; ++l) {
       p->lev[l].refinement = p->r0 + l - 1;
       colour_level(p->meshOf(l), p->lev[l], s);
+      locality_order(p->meshOf(l), p->lev[l], s);
     }
     p->ops.clear();
     p->ops.resize(L + 1);

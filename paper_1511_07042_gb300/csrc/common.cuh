@@ -78,6 +78,9 @@ struct Mesh {
   DBuf<int> mid;         // [nnz] fine index of the midpoint of edge (i, col) (-1 on diag);
                          //       filled when the next refinement exists
   DBuf<double> valA, valM;  // [nnz] assembled P1 stiffness / mass (refinement >= 1)
+  DBuf<int> row_order;   // [n] processing order of rows for the row kernels: vertices
+                         //     sorted by the Morton code of their position, so that
+                         //     warps running together gather nearby rows (hierarchy levels)
 };
 
 // Operators of one level l of the hierarchy, for one finest level f.
@@ -175,6 +178,7 @@ void refine_mesh(const Mesh& c, Mesh& f, double amplitude, const double* sh_cons
                  const double* coefs_dev, cudaStream_t s);
 void assemble_p1(Mesh& m, cudaStream_t s);
 void colour_level(const Mesh& m, Level& lv, cudaStream_t s);
+void locality_order(Mesh& m, Level& lv, cudaStream_t s);
 void galerkin(const Mesh& fine, const Mesh& coarse, const double* fa, const double* fm,
               double* ca, double* cm, cudaStream_t s);
 void extract_diag(const Mesh& m, const double* a, const double* mm, double* da, double* dm,

@@ -288,12 +288,22 @@ eig32_kernel(int n, int zsmem, DW w) {
   for (int i = wid; i < r; i += nwarps)
     for (int j = lane; j < r; j += 32) A[i * r + j] = (float)(0.5 * (w.T[i * n + j] + w.T[j * n + i]));
   __syncthreads();
-  // --- Householder tridiagonalisation, v_j stored in column j below the subdiagonal
+  // --- Householder tridiagonalisation, v_j stored in column j below the subdiagonal.
+  // The squared norm of the next column below its subdiagonal is summed per warp
+  // while the rank-2 update of the current step writes it (colsq, double-buffered),
+  // so a step needs no separate block reduction.
+  __shared__ float colsq[2][32];
   for (int j = 0; j + 2 < r; ++j) {
     const float a0 = A[(j + 1) * r + j];
-    float part = 0.f;
-    for (int i = j + 2 + tid; i < r; i += kBig) part += A[i * r + j] * A[i * r + j];
-    const float xn2 = block_sum<float>(part, redf);
+    float xn2;
+    if (j == 0) {
+      float part = 0.f;
+      for (int i = j + 2 + tid; i < r; i += kBig) part += A[i * r + j] * A[i * r + j];
+      xn2 = block_sum<float>(part, redf);
+    } else {
+      xn2 = 0.f;
+      for (int q = 0; q < nwarps; ++q) xn2 += colsq[j & 1][q];
+    }
     float beta = a0, t = 0.f, scale = 0.f;
     if (xn2 > 0.f) {
       beta = -copysignf(sqrtf(a0 * a0 + xn2), a0);
@@ -320,11 +330,19 @@ eig32_kernel(int n, int zsmem, DW w) {
       float kk = 0.f;                                 // K = (t/2) p.v, per warp
       for (int a = lane; a < m; a += 32) kk += pv[a] * vb[a];
       kk = 0.5f * t * warp_sumf(kk);
+      float sq = 0.f;                                 // next column, rows a >= 2
       for (int a = wid; a < m; a += nwarps) {        // A22 -= v w^T + w v^T, w = p - K v
         float* Ar = A + (j + 1 + a) * r + (j + 1);
         const float va = vb[a], wa = pv[a] - kk * va;
         for (int b = lane; b < m; b += 32) Ar[b] -= va * (pv[b] - kk * vb[b]) + wa * vb[b];
+        if (lane == 0 && a >= 2) sq += Ar[0] * Ar[0];
       }
+      if (lane == 0) colsq[(j + 1) & 1][wid] = sq;
+    } else {
+      float sq = 0.f;
+      for (int a = wid; a < m; a += nwarps)
+        if (lane == 0 && a >= 2) sq += A[(j + 1 + a) * r + (j + 1)] * A[(j + 1 + a) * r + (j + 1)];
+      if (lane == 0) colsq[(j + 1) & 1][wid] = sq;
     }
     __syncthreads();
   }
@@ -398,7 +416,7 @@ eig32_kernel(int n, int zsmem, DW w) {
   // factors in global scratch, planes [5][row][j]) and solves for column j of Z; after
   // each of the kInvIters solves the columns are scaled by their largest entry, and
   // one warp per cluster orthonormalises the members in order (modified
-  // Gram-Schmidt).  All eigenvectors advance together, so the sequential work is one
+  // Gram-Schmidt, in blocks of 8, twice).  All eigenvectors advance together, so the sequential work is one
   // factorisation and kInvIters solves of length r, not one per member of the
   // largest cluster.
   __shared__ int cst[kMaxN + 1];
@@ -527,12 +545,35 @@ eig32_kernel(int n, int zsmem, DW w) {
       __syncthreads();
       for (int c = wid; c < s_ncl; c += nwarps) {
         for (int jv = cst[c]; jv < cst[c + 1]; ++jv) {
-          for (int q = cst[c]; q < jv; ++q) {
-            float dot = 0.f;
-            for (int a = lane; a < r; a += 32) dot += Z[a * r + q] * Z[a * r + jv];
-            dot = warp_sumf(dot);
-            for (int a = lane; a < r; a += 32) Z[a * r + jv] -= dot * Z[a * r + q];
-            __syncwarp();
+          // orthogonalise against the earlier members: blocks of 8 at a time
+          // (independent dot products, then one combined update), two passes
+          for (int pass = 0; pass < 2; ++pass) {
+            for (int q0 = cst[c]; q0 < jv; q0 += 8) {
+              const int nq = min(8, jv - q0);
+              // slots beyond nq read column q0 and get weight 0
+              float dot[8];
+#pragma unroll
+              for (int u = 0; u < 8; ++u) dot[u] = 0.f;
+              for (int a = lane; a < r; a += 32) {
+                const float zj = Z[a * r + jv];
+                const float* zr = Z + a * r + q0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) dot[u] = fmaf(zr[u < nq ? u : 0], zj, dot[u]);
+              }
+#pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                const float t = warp_sumf(dot[u]);
+                dot[u] = (u < nq) ? t : 0.f;
+              }
+              for (int a = lane; a < r; a += 32) {
+                float zj = Z[a * r + jv];
+                const float* zr = Z + a * r + q0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) zj = fmaf(-dot[u], zr[u < nq ? u : 0], zj);
+                Z[a * r + jv] = zj;
+              }
+              __syncwarp();
+            }
           }
           float nrm = 0.f;
           for (int a = lane; a < r; a += 32) nrm += Z[a * r + jv] * Z[a * r + jv];

@@ -59,38 +59,25 @@ __device__ __forceinline__ void stv(float* p, size_t i, const float (&v)[4]) {
   reinterpret_cast<float4*>(p)[i] = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// aa += A_row X, mm += M_row X for one CSR row owned by a warp.  The row's pattern and
-// values are loaded once, one entry per lane (one coalesced load per array), and
-// broadcast by shuffles, so that the gathers of the neighbour rows of X do not wait
-// for the column indices one by one: the unrolled loop issues them back to back.
+// aa += A_row X, mm += M_row X for one CSR row owned by a warp (pattern and values
+// streamed, neighbour rows of X gathered through the read-only path).
 template <typename T, int CPL>
 __device__ __forceinline__ void gather_row(const int* __restrict__ col, const T* __restrict__ va,
                                            const T* __restrict__ vm, const T* __restrict__ X, int b, int e,
                                            int nch, int lane, T (&aa)[CPL][Chunk<T>::W],
                                            T (&mm)[CPL][Chunk<T>::W]) {
   constexpr int W = Chunk<T>::W;
-  for (int p0 = b; p0 < e; p0 += 32) {
-    const int len = min(32, e - p0);
-    int jl = 0;
-    T al = T(0), ml = T(0);
-    if (lane < len) {
-      jl = __ldcs(col + p0 + lane);
-      al = __ldcs(va + p0 + lane);
-      ml = __ldcs(vm + p0 + lane);
-    }
-#pragma unroll 8
-    for (int q = 0; q < len; ++q) {
-      const int j = __shfl_sync(0xffffffffu, jl, q);
-      const T a = __shfl_sync(0xffffffffu, al, q), m = __shfl_sync(0xffffffffu, ml, q);
+  for (int p = b; p < e; ++p) {
+    const int j = __ldcs(col + p);
+    const T a = __ldcs(va + p), m = __ldcs(vm + p);
 #pragma unroll
-      for (int u = 0; u < CPL; ++u) {
-        const int c = lane + 32 * u;
-        if (c < nch) {
-          T x[W];
-          ldv_ro(X, (size_t)j * nch + c, x);
+    for (int u = 0; u < CPL; ++u) {
+      const int c = lane + 32 * u;
+      if (c < nch) {
+        T x[W];
+        ldv_ro(X, (size_t)j * nch + c, x);
 #pragma unroll
-          for (int z = 0; z < W; ++z) { aa[u][z] = fma(a, x[z], aa[u][z]); mm[u][z] = fma(m, x[z], mm[u][z]); }
-        }
+        for (int z = 0; z < W; ++z) { aa[u][z] = fma(a, x[z], aa[u][z]); mm[u][z] = fma(m, x[z], mm[u][z]); }
       }
     }
   }
@@ -102,11 +89,12 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 spmm_am_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
                const T* __restrict__ va, const T* __restrict__ vm,
                const T* __restrict__ X, int n, int nch, T* __restrict__ AX,
-               T* __restrict__ MX) {
+               T* __restrict__ MX, const int* __restrict__ order) {
   constexpr int W = Chunk<T>::W;
-  const int row = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
-  if (row >= n) return;
+  if (w >= n) return;
+  const int row = order ? order[w] : w;
   T aa[CPL][W], mm[CPL][W];
 #pragma unroll
   for (int u = 0; u < CPL; ++u)
@@ -481,9 +469,9 @@ void spmm_am(const Mesh& m, const T* a, const T* mm, const T* X, int ld, T* AX, 
   prof_begin(KC_SPMM, s);
   const int grid = blocks_for(m.n, kWarpsPerBlock);
   switch (cpl_for(nch)) {
-    case 1: spmm_am_kernel<T, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX); break;
-    case 2: spmm_am_kernel<T, 2><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX); break;
-    default: spmm_am_kernel<T, 4><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX); break;
+    case 1: spmm_am_kernel<T, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX, m.row_order.get()); break;
+    case 2: spmm_am_kernel<T, 2><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX, m.row_order.get()); break;
+    default: spmm_am_kernel<T, 4><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX, m.row_order.get()); break;
   }
   check_launch("spmm_am_kernel");
   prof_end(KC_SPMM, s, (4.0 + 2.0 * tb<T>()) * m.nnz + 4.0 * (m.n + 1) + 3.0 * tb<T>() * m.n * ld,
@@ -514,7 +502,7 @@ static void row_update(const Mesh& m, const T* a, const T* mm, const T* da, cons
 template <typename T>
 void jacobi_sweep(const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const T* X,
                   T* Xout, const T* B, const T* shift, int ld, double omega, cudaStream_t s) {
-  row_update<T, 0>(m, a, mm, da, dm, nullptr, m.n, m.nnz, X, Xout, B, shift, ld, omega, s);
+  row_update<T, 0>(m, a, mm, da, dm, m.row_order.get(), m.n, m.nnz, X, Xout, B, shift, ld, omega, s);
 }
 
 template <typename T>
@@ -529,7 +517,7 @@ template <typename T>
 void residual(const Mesh& m, const T* a, const T* mm, const T* X, const T* B, const T* shift, int ld,
               T* R, cudaStream_t s) {
   // the diagonal is not used in residual mode; pass the matrix values as placeholders
-  row_update<T, 2>(m, a, mm, a, mm, nullptr, m.n, m.nnz, X, R, B, shift, ld, 0.0, s);
+  row_update<T, 2>(m, a, mm, a, mm, m.row_order.get(), m.n, m.nnz, X, R, B, shift, ld, 0.0, s);
 }
 
 template <typename T>

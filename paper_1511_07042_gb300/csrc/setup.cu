@@ -555,6 +555,54 @@ void colour_level(const Mesh& m, Level& lv, cudaStream_t s) {
       lv.colour_nnz_host[c] += hrp[hrows[q] + 1] - hrp[hrows[q]];
 }
 
+// Processing order of the rows of mesh m for the row kernels: vertices sorted by the
+// 30-bit Morton code of their position in the bounding box (ties by index), and the
+// rows of each colour of lv in the same order.  Any order gives the same results
+// (every row is computed alone, rows of one colour are never neighbours); this one
+// makes warps that run together gather nearby rows of the vector block, so that the
+// gathers hit L2 instead of HBM.
+void locality_order(Mesh& m, Level& lv, cudaStream_t s) {
+  const int n = m.n;
+  std::vector<double> v(3 * (size_t)n);
+  std::vector<int> rows(n);
+  BMG_CUDA(cudaMemcpyAsync(v.data(), m.verts.get(), sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaMemcpyAsync(rows.data(), lv.colour_rows.get(), sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaStreamSynchronize(s));
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < n; ++i)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], v[3 * i + d]);
+      hi[d] = std::max(hi[d], v[3 * i + d]);
+    }
+  auto spread = [](uint32_t x) {   // 10 bits -> every third bit
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+  };
+  std::vector<uint32_t> key(n);
+  for (int i = 0; i < n; ++i) {
+    uint32_t q[3];
+    for (int d = 0; d < 3; ++d) {
+      const double w = hi[d] > lo[d] ? (v[3 * i + d] - lo[d]) / (hi[d] - lo[d]) : 0.0;
+      q[d] = (uint32_t)std::min(1023.0, std::max(0.0, w * 1024.0));
+    }
+    key[i] = (spread(q[0]) << 2) | (spread(q[1]) << 1) | spread(q[2]);
+  }
+  auto before = [&](int a, int b) { return key[a] < key[b] || (key[a] == key[b] && a < b); };
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), before);
+  for (int c = 0; c < lv.n_colours; ++c)
+    std::sort(rows.begin() + lv.colour_ptr_host[c], rows.begin() + lv.colour_ptr_host[c + 1], before);
+  m.row_order.alloc(n);
+  BMG_CUDA(cudaMemcpyAsync(m.row_order.get(), order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+  BMG_CUDA(cudaMemcpyAsync(lv.colour_rows.get(), rows.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+  BMG_CUDA(cudaStreamSynchronize(s));
+}
+
 // ------------------------------------------------------------- Galerkin ----
 namespace {
 // Coarse row i of P^T G P: fine rows a with P[a,i] != 0 are i (weight 1) and the
