@@ -405,6 +405,7 @@ def run_ours(args):
                 "kernels": {n: {"ms": d["ms"], "launches": d["launches"]} for n, d in prof.items()},
                 "kernel_timing": "per-class CUDA events over a second pass of the same steps",
                 "smoother_spmm_gbs": smoother_spmm,
+                "autotuned_row_shapes": [" ".join(str(x) for x in t) for t in bmg.autotune_report()],
                 "cpu_baseline": cpu,
                 "clocks": clocks}
         line.update(extras)

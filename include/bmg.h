@@ -289,6 +289,12 @@ bmg_status bmg_profile_reset(void);
 bmg_status bmg_profile_read(int cls, double* total_ms, long long* launches, double* bytes,
                             double* flops);
 const char* bmg_kernel_class_name(int cls);
+/* Row-kernel shapes chosen by the autotuner so far (SpMM, Jacobi and residual
+ * kernels: lanes per row, 16-byte chunks per lane and warps per block, picked per
+ * arithmetic, block width and row count by timing the candidates on first use;
+ * environment BMG_AUTOTUNE=0 keeps the default shape).  Writes at most len-1 bytes
+ * of text and a terminating zero into buf; returns the full length.               */
+int bmg_autotune_report(char* buf, int len);
 /* Number of kernels libbmg has launched in this process.                         */
 long long bmg_launch_count(void);
 

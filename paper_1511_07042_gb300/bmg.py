@@ -86,6 +86,7 @@ def _load():
         "bmg_profile_read": (i, [i, P(C.c_double), P(C.c_longlong), P(C.c_double), P(C.c_double)]),
         "bmg_kernel_class_name": (C.c_char_p, [i]),
         "bmg_launch_count": (C.c_longlong, []),
+        "bmg_autotune_report": (i, [C.c_char_p, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -302,6 +303,20 @@ def profile_read():
         _check(LIB.bmg_profile_read(c, C.byref(ms), C.byref(n), C.byref(b), C.byref(f)))
         out[LIB.bmg_kernel_class_name(c).decode()] = dict(ms=ms.value, launches=n.value,
                                                           bytes=b.value, flops=f.value)
+    return out
+
+
+def autotune_report():
+    """Row-kernel shapes chosen so far: [(kind, bytes, nch, rows, lanes, chunks, warps)]."""
+    n = LIB.bmg_autotune_report(None, 0)
+    buf = C.create_string_buffer(n + 1)
+    LIB.bmg_autotune_report(buf, n + 1)
+    out = []
+    for line in buf.value.decode().splitlines():
+        a, b = line.split(" -> ")
+        k = a.split()
+        v = b.split()
+        out.append((k[0], int(k[1]), int(k[2]), int(k[3]), int(v[0]), int(v[1]), int(v[2])))
     return out
 
 

@@ -210,6 +210,7 @@ void gram(const double* X, const double* Y, int n, int k, int ld, double* G, dou
 void gram(const float* X, const float* Y, int n, int k, int ld, double* G, double* partial,
           int nparts, cudaStream_t s);
 int gram_parts(int n);
+std::string tuned_report();
 template <typename T>
 void eig_residuals(const T* AU, const T* MU, const T* U, const double* lam, int n, int k, int ld,
                    double* partial, int nparts, double* out, cudaStream_t s);

@@ -12,6 +12,11 @@
 // products of FP32 blocks are accumulated without rounding loss (exact products and
 // compensated sums), so their results carry FP64-class accuracy.
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "common.cuh"
 
@@ -61,10 +66,10 @@ __device__ __forceinline__ void stv(float* p, size_t i, const float (&v)[4]) {
 
 // aa += A_row X, mm += M_row X for one CSR row owned by a warp (pattern and values
 // streamed, neighbour rows of X gathered through the read-only path).
-template <typename T, int CPL>
+template <typename T, int LPR, int CPL>
 __device__ __forceinline__ void gather_row(const int* __restrict__ col, const T* __restrict__ va,
                                            const T* __restrict__ vm, const T* __restrict__ X, int b, int e,
-                                           int nch, int lane, T (&aa)[CPL][Chunk<T>::W],
+                                           int nch, int sl, T (&aa)[CPL][Chunk<T>::W],
                                            T (&mm)[CPL][Chunk<T>::W]) {
   constexpr int W = Chunk<T>::W;
   for (int p = b; p < e; ++p) {
@@ -72,7 +77,7 @@ __device__ __forceinline__ void gather_row(const int* __restrict__ col, const T*
     const T a = __ldcs(va + p), m = __ldcs(vm + p);
 #pragma unroll
     for (int u = 0; u < CPL; ++u) {
-      const int c = lane + 32 * u;
+      const int c = sl + LPR * u;
       if (c < nch) {
         T x[W];
         ldv_ro(X, (size_t)j * nch + c, x);
@@ -84,15 +89,19 @@ __device__ __forceinline__ void gather_row(const int* __restrict__ col, const T*
 }
 
 // ---- fused SpMM: AX = A X, MX = M X  (one pass over the shared pattern) ----
-template <typename T, int CPL>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+// Row tiling: LPR lanes per row (32 / LPR rows per warp), CPL 16-byte chunks per lane
+// (chunks sl, sl + LPR, ...), blockDim.x / 32 warps per block; picked per level size
+// and block width by the autotuner (tune_rows).
+template <typename T, int LPR, int CPL>
+__global__ void __launch_bounds__(512)
 spmm_am_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
                const T* __restrict__ va, const T* __restrict__ vm,
                const T* __restrict__ X, int n, int nch, T* __restrict__ AX,
                T* __restrict__ MX, const int* __restrict__ order) {
   constexpr int W = Chunk<T>::W;
-  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+  constexpr int RPW = 32 / LPR;
+  const int lane = threadIdx.x & 31, sl = lane % LPR;
+  const int w = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RPW + lane / LPR;
   if (w >= n) return;
   const int row = order ? order[w] : w;
   T aa[CPL][W], mm[CPL][W];
@@ -100,10 +109,10 @@ spmm_am_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
   for (int u = 0; u < CPL; ++u)
 #pragma unroll
     for (int q = 0; q < W; ++q) { aa[u][q] = T(0); mm[u][q] = T(0); }
-  gather_row<T, CPL>(col, va, vm, X, row_ptr[row], row_ptr[row + 1], nch, lane, aa, mm);
+  gather_row<T, LPR, CPL>(col, va, vm, X, row_ptr[row], row_ptr[row + 1], nch, sl, aa, mm);
 #pragma unroll
   for (int u = 0; u < CPL; ++u) {
-    const int c = lane + 32 * u;
+    const int c = sl + LPR * u;
     if (c < nch) {
       stv_cs(AX, (size_t)row * nch + c, aa[u]);
       stv_cs(MX, (size_t)row * nch + c, mm[u]);
@@ -116,8 +125,8 @@ spmm_am_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
 //   MODE 0 (Jacobi):   xout = x + omega r / d
 //   MODE 1 (GS):       x    = x + r / d          (in place, rows of one colour)
 //   MODE 2 (residual): out  = r
-template <typename T, int CPL, int MODE>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+template <typename T, int LPR, int CPL, int MODE>
+__global__ void __launch_bounds__(512)
 row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
                   const T* __restrict__ va, const T* __restrict__ vm,
                   const T* __restrict__ da, const T* __restrict__ dm,
@@ -125,8 +134,9 @@ row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
                   T* Out, const T* __restrict__ B, const T* __restrict__ shift,
                   int nch, T omega) {
   constexpr int W = Chunk<T>::W;
-  const int w = blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
+  constexpr int RPW = 32 / LPR;
+  const int lane = threadIdx.x & 31, sl = lane % LPR;
+  const int w = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RPW + lane / LPR;
   if (w >= nrows) return;
   const int row = rows ? rows[w] : w;
   T aa[CPL][W], mm[CPL][W];
@@ -134,11 +144,11 @@ row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
   for (int u = 0; u < CPL; ++u)
 #pragma unroll
     for (int q = 0; q < W; ++q) { aa[u][q] = T(0); mm[u][q] = T(0); }
-  gather_row<T, CPL>(col, va, vm, X, row_ptr[row], row_ptr[row + 1], nch, lane, aa, mm);
+  gather_row<T, LPR, CPL>(col, va, vm, X, row_ptr[row], row_ptr[row + 1], nch, sl, aa, mm);
   const T dai = da[row], dmi = dm[row];
 #pragma unroll
   for (int u = 0; u < CPL; ++u) {
-    const int c = lane + 32 * u;
+    const int c = sl + LPR * u;
     if (c >= nch) continue;
     T s[W], r[W];
     ldv(shift, c, s);
@@ -463,17 +473,140 @@ constexpr double tb() { return (double)sizeof(T); }
 }  // namespace
 
 // ------------------------------------------------------------------ host ----
+// Row-kernel shapes (lanes per row, chunks per lane) and the autotuner that picks one
+// (with the warps per block) per kernel kind, arithmetic, block width and row count.
+namespace {
+constexpr int kNumShapes = 8;
+constexpr int kShapeLPR[kNumShapes] = {32, 32, 32, 16, 16, 8, 8, 4};
+constexpr int kShapeCPL[kNumShapes] = {1, 2, 4, 1, 2, 1, 2, 1};
+constexpr int kWPB[3] = {4, 8, 16};
+
+struct RowCfg {
+  int shape, wpb;
+};
+
+int pow2_at_least(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+// shapes whose lanes x chunks cover the row without idling more than half
+bool shape_ok(int sh, int nch) {
+  const int tot = kShapeLPR[sh] * kShapeCPL[sh];
+  return tot >= nch && tot <= 2 * pow2_at_least(nch);
+}
+RowCfg default_cfg(int nch) {
+  const int cpl = nch <= 32 ? 1 : (nch <= 64 ? 2 : 4);
+  return {cpl == 1 ? 0 : (cpl == 2 ? 1 : 2), 8};
+}
+
+template <typename T, int LPR, int CPL>
+void spmm_shape(int wpb, const Mesh& m, const T* a, const T* mm, const T* X, int nch, T* AX, T* MX,
+                cudaStream_t s) {
+  const int per_block = wpb * (32 / LPR);
+  spmm_am_kernel<T, LPR, CPL><<<blocks_for(m.n, per_block), wpb * 32, 0, s>>>(
+      m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX, m.row_order.get());
+  check_launch("spmm_am_kernel");
+}
+template <typename T>
+void spmm_launch(RowCfg c, const Mesh& m, const T* a, const T* mm, const T* X, int nch, T* AX, T* MX,
+                 cudaStream_t s) {
+  switch (c.shape) {
+    case 0: spmm_shape<T, 32, 1>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
+    case 1: spmm_shape<T, 32, 2>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
+    case 2: spmm_shape<T, 32, 4>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
+    case 3: spmm_shape<T, 16, 1>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
+    case 4: spmm_shape<T, 16, 2>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
+    case 5: spmm_shape<T, 8, 1>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
+    case 6: spmm_shape<T, 8, 2>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
+    default: spmm_shape<T, 4, 1>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
+  }
+}
+
+template <typename T, int LPR, int CPL, int MODE>
+void row_shape(int wpb, const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const int* rows,
+               int nrows, const T* X, T* Out, const T* B, const T* shift, int nch, double omega, cudaStream_t s) {
+  const int per_block = wpb * (32 / LPR);
+  row_update_kernel<T, LPR, CPL, MODE><<<blocks_for(nrows, per_block), wpb * 32, 0, s>>>(
+      m.row_ptr.get(), m.col.get(), a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, (T)omega);
+  check_launch("row_update_kernel");
+}
+template <typename T, int MODE>
+void row_launch(RowCfg c, const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const int* rows,
+                int nrows, const T* X, T* Out, const T* B, const T* shift, int nch, double omega, cudaStream_t s) {
+  switch (c.shape) {
+    case 0: row_shape<T, 32, 1, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 1: row_shape<T, 32, 2, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 2: row_shape<T, 32, 4, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 3: row_shape<T, 16, 1, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 4: row_shape<T, 16, 2, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 5: row_shape<T, 8, 1, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 6: row_shape<T, 8, 2, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    default: row_shape<T, 4, 1, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+  }
+}
+
+// Tuned shapes, process-wide.  The candidates are timed on the call's own data and
+// stream (spmm, Jacobi and residual kernels are idempotent: they write a block they
+// do not read), three launches each after one warm-up, with CUDA events.  Set
+// BMG_AUTOTUNE=0 to use the default shape (32 lanes per row, 8 warps per block).
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, RowCfg> g_tuned;
+
+bool autotune_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("BMG_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+template <typename F>
+RowCfg tune_rows(int kind, int tsize, int nch, int n, cudaStream_t s, F&& launch) {
+  const auto key = std::make_tuple(kind, tsize, nch, n);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) return it->second;
+  }
+  RowCfg best = default_cfg(nch);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  check_cuda(cudaStreamIsCapturing(s, &cap), "cudaStreamIsCapturing");
+  if (!autotune_enabled() || cap != cudaStreamCaptureStatusNone) return best;
+  cudaEvent_t e0, e1;
+  check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+  check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+  float best_ms = 1e30f;
+  for (int sh = 0; sh < kNumShapes; ++sh) {
+    if (!shape_ok(sh, nch)) continue;
+    for (int wpb : kWPB) {
+      const RowCfg c{sh, wpb};
+      launch(c);
+      check_cuda(cudaEventRecord(e0, s), "cudaEventRecord");
+      for (int q = 0; q < 3; ++q) launch(c);
+      check_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
+      check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+      float ms = 0.f;
+      check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+      if (ms < best_ms) { best_ms = ms; best = c; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tuned[key] = best;
+  return best;
+}
+}  // namespace
+
 template <typename T>
 void spmm_am(const Mesh& m, const T* a, const T* mm, const T* X, int ld, T* AX, T* MX, cudaStream_t s) {
   const int nch = ld / Chunk<T>::W;
+  const RowCfg c = tune_rows(0, (int)sizeof(T), nch, m.n, s, [&](RowCfg q) {
+    spmm_launch<T>(q, m, a, mm, X, nch, AX, MX, s);
+  });
   prof_begin(KC_SPMM, s);
-  const int grid = blocks_for(m.n, kWarpsPerBlock);
-  switch (cpl_for(nch)) {
-    case 1: spmm_am_kernel<T, 1><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX, m.row_order.get()); break;
-    case 2: spmm_am_kernel<T, 2><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX, m.row_order.get()); break;
-    default: spmm_am_kernel<T, 4><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX, m.row_order.get()); break;
-  }
-  check_launch("spmm_am_kernel");
+  spmm_launch<T>(c, m, a, mm, X, nch, AX, MX, s);
   prof_end(KC_SPMM, s, (4.0 + 2.0 * tb<T>()) * m.nnz + 4.0 * (m.n + 1) + 3.0 * tb<T>() * m.n * ld,
            4.0 * m.nnz * ld);
 }
@@ -483,16 +616,26 @@ static void row_update(const Mesh& m, const T* a, const T* mm, const T* da, cons
                        const int* rows, int nrows, long long nnz_rows, const T* X, T* Out,
                        const T* B, const T* shift, int ld, double omega, cudaStream_t s) {
   const int nch = ld / Chunk<T>::W;
-  const int grid = blocks_for(nrows, kWarpsPerBlock);
   if (nrows == 0) return;
+  // Gauss-Seidel sweeps run in place and are not re-run for timing: they take the
+  // shape tuned for the residual (same gathers, out of place) or the Jacobi sweep of
+  // the same level
+  const int kind = (MODE == 2) ? 2 : 1;
+  RowCfg c = default_cfg(nch);
+  if (MODE == 1) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    for (int kd : {2, 1}) {
+      auto it = g_tuned.find(std::make_tuple(kd, (int)sizeof(T), nch, m.n));
+      if (it != g_tuned.end()) { c = it->second; break; }
+    }
+  } else {
+    c = tune_rows(kind, (int)sizeof(T), nch, nrows, s, [&](RowCfg q) {
+      row_launch<T, MODE>(q, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s);
+    });
+  }
   const int cls = (MODE == 2) ? KC_RESID : KC_SMOOTH;
   prof_begin(cls, s);
-  switch (cpl_for(nch)) {
-    case 1: row_update_kernel<T, 1, MODE><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, (T)omega); break;
-    case 2: row_update_kernel<T, 2, MODE><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, (T)omega); break;
-    default: row_update_kernel<T, 4, MODE><<<grid, kWarpsPerBlock * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, (T)omega); break;
-  }
-  check_launch("row_update_kernel");
+  row_launch<T, MODE>(c, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s);
   // matrix rows, diagonals, own-row read + write, one share of the gathered block, B
   const double bytes = (4.0 + 2.0 * tb<T>()) * nnz_rows + 2.0 * tb<T>() * nrows +
                        tb<T>() * nrows * ld * (B ? 4.0 : 3.0);
@@ -623,6 +766,23 @@ void scale_rhs(const T* MU, const double* theta, int n, int k, int ld, T* B, cud
   check_launch("scale_rhs_kernel");
 }
 
+// Text of the tuned row-kernel shapes, one line per entry:
+// "kind bytes nch rows -> lanes_per_row chunks_per_lane warps_per_block".
+std::string tuned_report() {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  std::string out;
+  static const char* kinds[3] = {"spmm", "jacobi", "residual"};
+  for (const auto& kv : g_tuned) {
+    const auto& k = kv.first;
+    const RowCfg c = kv.second;
+    out += std::string(kinds[std::get<0>(k)]) + " " + std::to_string(std::get<1>(k)) + " " +
+           std::to_string(std::get<2>(k)) + " " + std::to_string(std::get<3>(k)) + " -> " +
+           std::to_string(kShapeLPR[c.shape]) + " " + std::to_string(kShapeCPL[c.shape]) + " " +
+           std::to_string(c.wpb) + "\n";
+  }
+  return out;
+}
+
 #define BMG_OPS_INSTANTIATE(T)                                                                          \
   template void spmm_am<T>(const Mesh&, const T*, const T*, const T*, int, T*, T*, cudaStream_t);      \
   template void jacobi_sweep<T>(const Mesh&, const T*, const T*, const T*, const T*, const T*, T*,     \
@@ -643,3 +803,13 @@ BMG_OPS_INSTANTIATE(float)
 #undef BMG_OPS_INSTANTIATE
 
 }  // namespace bmg
+
+extern "C" int bmg_autotune_report(char* buf, int len) {
+  const std::string r = bmg::tuned_report();
+  if (buf && len > 0) {
+    const int nb = std::min((int)r.size(), len - 1);
+    std::memcpy(buf, r.data(), nb);
+    buf[nb] = 0;
+  }
+  return (int)r.size();
+}
