@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -652,6 +653,65 @@ struct CycleState {
   double max_dense_err = 0.0;
 };
 
+// Runs `body` (a sequence of asynchronous launches on w.s) either directly or as a
+// CUDA graph: the first time a key is met the body runs eagerly (the row-kernel
+// autotuner times its candidates then); the second time it is captured, instantiated
+// and replayed from then on.  Graphs are off while the kernel profiler runs (its
+// events must be recorded per launch) and when BMG_GRAPHS=0.
+bool graphs_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("BMG_GRAPHS");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+template <typename F>
+void run_graph(bmg_problem* p, SolveWork& w, const std::tuple<int, int, int, int>& key, F&& body) {
+  (void)p;
+  if (!graphs_enabled() || prof_enabled() || w.s != w.own) {
+    body();
+    return;
+  }
+  auto it = w.graphs.find(key);
+  if (it == w.graphs.end()) {
+    if (!w.seen.count(key)) {
+      w.seen.insert(key);
+      body();
+      return;
+    }
+    cudaGraph_t g = nullptr;
+    const long long before = launch_count();
+    BMG_CUDA(cudaStreamBeginCapture(w.s, cudaStreamCaptureModeRelaxed));
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(w.s, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    BMG_CUDA(cudaStreamEndCapture(w.s, &g));
+    count_launches(before - launch_count());   // captured launches did not run
+    // kernel nodes, for the launch counter
+    size_t nn = 0;
+    int kernels = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    for (size_t q = 0; q < nn; ++q) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nodes[q], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+    }
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    check_cuda(e, "cudaGraphInstantiate");
+    it = w.graphs.emplace(key, std::make_pair(ge, kernels)).first;
+  }
+  BMG_CUDA(cudaGraphLaunch(it->second.first, w.s));
+  count_launches(it->second.second);
+}
+
 // One BMG cycle on level f with blocks of arithmetic T (steps 1-5 of the file
 // header).  Smoothing (step 5) runs unless the wanted pairs met ftol or `last` is
 // set.  Returns whether every wanted pair met ftol.
@@ -667,47 +727,51 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
   double* hlam = w.hbuf + 2 * k;    // k Ritz values
   double* hqual = w.hbuf + 3 * k;   // error estimate of the enriched eigensolve
   int* hint = reinterpret_cast<int*>(w.hbuf + 3 * k + 1);  // rank
-  // 1-2: products, Grams, couplings Q^T AX, Q^T MX by the restriction chain
-  spmm_am<T>(mf, Af, Mf, b.X, ld, b.AX, b.MX, s);
-  gram(b.X, b.AX, nf, k, ld, w.GA.get(), w.partial.get(), gram_parts(nf), s);
-  gram(b.X, b.MX, nf, k, ld, w.GM.get(), w.partial.get(), gram_parts(nf), s);
-  const T* ca = b.AX;
-  const T* cm = b.MX;
-  for (int j = f; j >= 2; --j) {
-    restrict_<T>(p->meshOf(j - 1), ca, b.cA[j - 1], ld, s);
-    restrict_<T>(p->meshOf(j - 1), cm, b.cB[j - 1], ld, s);
-    ca = b.cA[j - 1];
-    cm = b.cB[j - 1];
-  }
-  prof_begin(KC_SMALL, s);
-  assemble_hat_kernel<T><<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.AQ[f].get(), ca, w.GA.get(), n1, k, ld, w.Ahat.get());
-  check_launch("assemble_hat_kernel");
-  assemble_hat_kernel<T><<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.MQ[f].get(), cm, w.GM.get(), n1, k, ld, w.Mhat.get());
-  check_launch("assemble_hat_kernel");
-  prof_end(KC_SMALL, s, 32.0 * nh * nh, 0.0);
-  // 3: enriched eigensolve
-  dense_eig(w.Ahat.get(), w.Mhat.get(), nh, sigma, k, w.theta.get(), w.Y.get(), w.rank.get(), w.dense.get(),
-            w.dquality.get(), sizeof(T) == sizeof(float) ? kDropFP32 : kDropFP64, s);
-  prof_begin(KC_SMALL, s);
-  shifts_kernel<T><<<grid_of(ld, 128), 128, 0, s>>>(w.theta.get(), k, ld, sigma, o.form, w.lam.get(), b.shift);
-  check_launch("shifts_kernel");
-  // 4: Ritz vectors U = Q Y_c + X Y_x
-  pack_coarse_kernel<T><<<grid_of((size_t)n1 * ld, 256), 256, 0, s>>>(w.Y.get(), n1, k, ld, b.cC[1]);
-  check_launch("pack_coarse_kernel");
-  prof_end(KC_SMALL, s, 8.0 * n1 * ld, 0.0);
-  const T* z = b.cC[1];
-  for (int j = 2; j < f; ++j) {
-    prolong<T>(p->meshOf(j), z, b.cC[j], ld, false, s);
-    z = b.cC[j];
-  }
-  prolong<T>(mf, z, b.Zf, ld, false, s);
-  expand<T>(b.Zf, b.X, w.Y.get() + (size_t)n1 * k, nf, k, ld, k, b.U, s);
-  spmm_am<T>(mf, Af, Mf, b.U, ld, b.AU, b.MU, s);
-  eig_residuals<T>(b.AU, b.MU, b.U, w.lam.get(), nf, k, ld, w.partial.get(), gram_parts(nf), w.res.get(), s);
-  BMG_CUDA(cudaMemcpyAsync(hres, w.res.get(), sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
-  BMG_CUDA(cudaMemcpyAsync(hlam, w.lam.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
-  BMG_CUDA(cudaMemcpyAsync(hint, w.rank.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
-  BMG_CUDA(cudaMemcpyAsync(hqual, w.dquality.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
+  // 1-4: products, Grams and couplings, enriched eigensolve, Ritz vectors, residuals
+  auto part_a = [&]() {
+    // 1-2: products, Grams, couplings Q^T AX, Q^T MX by the restriction chain
+    spmm_am<T>(mf, Af, Mf, b.X, ld, b.AX, b.MX, s);
+    gram(b.X, b.AX, nf, k, ld, w.GA.get(), w.partial.get(), gram_parts(nf), s);
+    gram(b.X, b.MX, nf, k, ld, w.GM.get(), w.partial.get(), gram_parts(nf), s);
+    const T* ca = b.AX;
+    const T* cm = b.MX;
+    for (int j = f; j >= 2; --j) {
+      restrict_<T>(p->meshOf(j - 1), ca, b.cA[j - 1], ld, s);
+      restrict_<T>(p->meshOf(j - 1), cm, b.cB[j - 1], ld, s);
+      ca = b.cA[j - 1];
+      cm = b.cB[j - 1];
+    }
+    prof_begin(KC_SMALL, s);
+    assemble_hat_kernel<T><<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.AQ[f].get(), ca, w.GA.get(), n1, k, ld, w.Ahat.get());
+    check_launch("assemble_hat_kernel");
+    assemble_hat_kernel<T><<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.MQ[f].get(), cm, w.GM.get(), n1, k, ld, w.Mhat.get());
+    check_launch("assemble_hat_kernel");
+    prof_end(KC_SMALL, s, 32.0 * nh * nh, 0.0);
+    // 3: enriched eigensolve
+    dense_eig(w.Ahat.get(), w.Mhat.get(), nh, sigma, k, w.theta.get(), w.Y.get(), w.rank.get(), w.dense.get(),
+              w.dquality.get(), sizeof(T) == sizeof(float) ? kDropFP32 : kDropFP64, s);
+    prof_begin(KC_SMALL, s);
+    shifts_kernel<T><<<grid_of(ld, 128), 128, 0, s>>>(w.theta.get(), k, ld, sigma, o.form, w.lam.get(), b.shift);
+    check_launch("shifts_kernel");
+    // 4: Ritz vectors U = Q Y_c + X Y_x
+    pack_coarse_kernel<T><<<grid_of((size_t)n1 * ld, 256), 256, 0, s>>>(w.Y.get(), n1, k, ld, b.cC[1]);
+    check_launch("pack_coarse_kernel");
+    prof_end(KC_SMALL, s, 8.0 * n1 * ld, 0.0);
+    const T* z = b.cC[1];
+    for (int j = 2; j < f; ++j) {
+      prolong<T>(p->meshOf(j), z, b.cC[j], ld, false, s);
+      z = b.cC[j];
+    }
+    prolong<T>(mf, z, b.Zf, ld, false, s);
+    expand<T>(b.Zf, b.X, w.Y.get() + (size_t)n1 * k, nf, k, ld, k, b.U, s);
+    spmm_am<T>(mf, Af, Mf, b.U, ld, b.AU, b.MU, s);
+    eig_residuals<T>(b.AU, b.MU, b.U, w.lam.get(), nf, k, ld, w.partial.get(), gram_parts(nf), w.res.get(), s);
+    BMG_CUDA(cudaMemcpyAsync(hres, w.res.get(), sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
+    BMG_CUDA(cudaMemcpyAsync(hlam, w.lam.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+    BMG_CUDA(cudaMemcpyAsync(hint, w.rank.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
+    BMG_CUDA(cudaMemcpyAsync(hqual, w.dquality.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
+  };
+  run_graph(p, w, std::make_tuple(0, f, (int)sizeof(T), 0), part_a);
   BMG_CUDA(cudaStreamSynchronize(s));
   if (hint[0] < k) fail(BMG_ERR_SINGULAR, "enriched space rank " + std::to_string(hint[0]) + " < k");
   if (!(*hqual <= 1e-6))
@@ -722,15 +786,6 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
   }
   if (!finite) fail(BMG_ERR_NONFINITE, "non-finite Ritz pair on level " + std::to_string(f));
   if (conv || last) return conv;
-  // 5: smoothing of the source problems from U, then the down-leg
-  const T* Bp = nullptr;
-  if (o.form == BMG_FORM_SHIFTED) {
-    prof_begin(KC_SMALL, s);
-    scale_rhs<T>(b.MU, w.theta.get(), nf, k, ld, b.B, s);
-    prof_end(KC_SMALL, s, 2.0 * sizeof(T) * nf * ld, 1.0 * nf * ld);
-    Bp = b.B;
-  }
-  smooth_level<T>(p, f, f, o, b.U, b.X, Bp, b.shift, ld, b.W, s);
   double smax = (o.form == BMG_FORM_SHIFTED) ? sigma : -1e300;
   if (o.form != BMG_FORM_SHIFTED) for (int i = 0; i < k; ++i) smax = std::max(smax, cs.lamv[i]);
   std::vector<int> legs;
@@ -738,35 +793,40 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
     if (!(smax * w.ratio[f][j] < 1.0 - 0.25)) break;
     legs.push_back(j);
   }
-  if (!legs.empty()) {
-    residual<T>(mf, Af, Mf, b.X, Bp, b.shift, ld, b.W, s);
-    const T* rprev = b.W;
-    for (size_t t = 0; t < legs.size(); ++t) {
-      const int j = legs[t];
-      const Mesh& mj = p->meshOf(j);
-      restrict_<T>(mj, rprev, b.cA[j], ld, s);
-      BMG_CUDA(cudaMemsetAsync(b.cB[j], 0, sizeof(T) * (size_t)mj.n * ld, s));
-      smooth_level<T>(p, f, j, o, b.cB[j], b.cB[j], b.cA[j], b.shift, ld, b.cD[j], s);
-      if (t + 1 < legs.size()) {
-        residual<T>(mj, Ops<T>::A(p, f, j), Ops<T>::M(p, f, j), b.cB[j], b.cA[j], b.shift, ld, b.cC[j], s);
-        rprev = b.cC[j];
+  auto part_b = [&]() {
+    // 5: smoothing of the source problems from U, then the down-leg
+    const T* Bp = nullptr;
+    if (o.form == BMG_FORM_SHIFTED) {
+      prof_begin(KC_SMALL, s);
+      scale_rhs<T>(b.MU, w.theta.get(), nf, k, ld, b.B, s);
+      prof_end(KC_SMALL, s, 2.0 * sizeof(T) * nf * ld, 1.0 * nf * ld);
+      Bp = b.B;
+    }
+    smooth_level<T>(p, f, f, o, b.U, b.X, Bp, b.shift, ld, b.W, s);
+    if (!legs.empty()) {
+      residual<T>(mf, Af, Mf, b.X, Bp, b.shift, ld, b.W, s);
+      const T* rprev = b.W;
+      for (size_t t = 0; t < legs.size(); ++t) {
+        const int j = legs[t];
+        const Mesh& mj = p->meshOf(j);
+        restrict_<T>(mj, rprev, b.cA[j], ld, s);
+        BMG_CUDA(cudaMemsetAsync(b.cB[j], 0, sizeof(T) * (size_t)mj.n * ld, s));
+        smooth_level<T>(p, f, j, o, b.cB[j], b.cB[j], b.cA[j], b.shift, ld, b.cD[j], s);
+        if (t + 1 < legs.size()) {
+          residual<T>(mj, Ops<T>::A(p, f, j), Ops<T>::M(p, f, j), b.cB[j], b.cA[j], b.shift, ld, b.cC[j], s);
+          rprev = b.cC[j];
+        }
       }
+      for (size_t t = legs.size() - 1; t >= 1; --t) {
+        const int j = legs[t];  // coarser; add into level j+1
+        prolong<T>(p->meshOf(j + 1), b.cB[j], b.cB[j + 1], ld, true, s);
+      }
+      prolong<T>(mf, b.cB[f - 1], b.X, ld, true, s);
     }
-    for (size_t t = legs.size() - 1; t >= 1; --t) {
-      const int j = legs[t];  // coarser; add into level j+1
-      prolong<T>(p->meshOf(j + 1), b.cB[j], b.cB[j + 1], ld, true, s);
-    }
-    prolong<T>(mf, b.cB[f - 1], b.X, ld, true, s);
-  }
+  };
+  run_graph(p, w, std::make_tuple(1, f, (int)sizeof(T), (int)legs.size()), part_b);
   return false;
 }
-
-}  // namespace
-}  // namespace bmg
-
-namespace bmg {
-namespace {
-
 // Argument checks shared by bmg_solve and bmg_solve_batched.
 bmg_options checked_options(const bmg_problem* p, int k, int n_wanted, double sigma, double tol,
                             const bmg_options* opt_in, const double* X0, const double* evals) {
@@ -794,8 +854,25 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
                 int evecs_on_device, double* resid, bmg_solve_info* info) {
   const int L = p->L;
   const int n2 = p->meshOf(2).n, nL = p->meshOf(L).n;
+  // the solve runs on the workspace's own non-blocking stream (capturable into CUDA
+  // graphs), ordered after the caller's stream; it returns after its work completes
+  if (!w.own) {
+    BMG_CUDA(cudaStreamCreateWithFlags(&w.own, cudaStreamNonBlocking));
+    BMG_CUDA(cudaEventCreateWithFlags(&w.ev, cudaEventDisableTiming));
+  }
+  BMG_CUDA(cudaEventRecord(w.ev, w.s));
+  BMG_CUDA(cudaStreamWaitEvent(w.own, w.ev, 0));
+  w.s = w.own;
   cudaStream_t s = w.s;
   const int ld = w.ld;
+  // the cycle graphs hold these values as launch arguments: recapture when they change
+  const std::vector<double> sig = {sigma, (double)o.form, (double)o.smoother, (double)o.nu, o.omega,
+                                   (double)o.vcycle_depth, (double)o.precision};
+  if (sig != w.gsig) {
+    BMG_CUDA(cudaStreamSynchronize(s));
+    w.drop_graphs();
+    w.gsig = sig;
+  }
   Blocks<double> b64 = blocks64(w);
   Blocks<float> b32;
   bool fp32 = o.precision == BMG_PREC_FP32;

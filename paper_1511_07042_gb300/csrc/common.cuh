@@ -3,8 +3,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <memory>
+#include <set>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/bmg.h"
@@ -117,8 +120,10 @@ enum KernelClass { KC_SPMM = 0, KC_SMOOTH, KC_RESID, KC_TRANSFER, KC_GRAM, KC_DE
 void prof_begin(int cls, cudaStream_t s);
 void prof_end(int cls, cudaStream_t s, double bytes, double flops);
 void prof_flush();
+bool prof_enabled();
 long long launch_count();
 void count_launch();
+void count_launches(long long n);
 
 // Workspace of bmg_solve, kept in the problem between calls with the same k.
 struct SolveWork {
@@ -136,7 +141,25 @@ struct SolveWork {
   std::vector<DBuf<double>> AQ, MQ;         // per f: dense n1 x n1 coarse blocks
   std::vector<std::vector<double>> ratio;   // [f][j] max_i dM_i / dA_i
   double* hbuf = nullptr;                   // pinned host staging (res, lam, quality, rank)
-  ~SolveWork() { if (hbuf) cudaFreeHost(hbuf); }
+  // CUDA graphs of the cycle: part A (steps 1-4) per (level, arithmetic), part B
+  // (step 5) per (level, arithmetic, down-leg depth); instantiated on the second cycle
+  // of a level on this workspace (the first runs eagerly, so the autotuner can time).
+  cudaStream_t own = nullptr;               // the library's non-blocking stream
+  cudaEvent_t ev = nullptr;                 // orders `own` after the caller's stream
+  std::map<std::tuple<int, int, int, int>, std::pair<cudaGraphExec_t, int>> graphs;  // exec, kernel nodes
+  std::set<std::tuple<int, int, int, int>> seen;
+  std::vector<double> gsig;                 // solve parameters the graphs were captured with
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.first);
+    graphs.clear();
+    seen.clear();
+  }
+  ~SolveWork() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second.first);
+    if (ev) cudaEventDestroy(ev);
+    if (own) cudaStreamDestroy(own);
+    if (hbuf) cudaFreeHost(hbuf);
+  }
 };
 }  // namespace bmg
 

@@ -61,7 +61,9 @@ const char* kNames[KC_COUNT] = {"spmm_am", "smooth_sweep", "residual", "transfer
 }  // namespace
 
 long long launch_count() { return g_launches.load(); }
+bool prof_enabled() { return prof().enabled; }
 void count_launch() { g_launches.fetch_add(1); }
+void count_launches(long long n) { g_launches.fetch_add(n); }
 
 void prof_begin(int cls, cudaStream_t s) {
   Profiler& p = prof();

@@ -1,8 +1,9 @@
-"""Autotuned row-kernel shapes: the tuner must not change results.
+"""Autotuned row-kernel shapes and CUDA-graph replay must not change results.
 
-Every shape computes each row's sums in the same order, so a solve with the tuned
-shapes and one with the default shape (BMG_AUTOTUNE=0, in a child process) give
-bit-identical eigenvalues and residuals, in both arithmetics."""
+Every shape computes each row's sums in the same order, and a replayed graph runs the
+launches it captured, so solves with the tuned shapes, with the default shape
+(BMG_AUTOTUNE=0) and with eager launches (BMG_GRAPHS=0), each in a child process,
+give bit-identical eigenvalues and residuals, in both arithmetics."""
 import json
 import os
 import subprocess
@@ -53,3 +54,12 @@ def test_tuned_shapes_give_identical_results(gpu_bmg):
     # every recorded shape covers its block width
     for kind, tb, nch, rows, lanes, chunks, warps in tuned["tuned"]:
         assert lanes * chunks >= nch and warps in (4, 8, 16) and rows > 0
+
+
+def test_graph_replay_gives_identical_results(gpu_bmg):
+    graphs = run_child({})
+    eager = run_child({"BMG_GRAPHS": "0"})
+    for prec in ("fp64", "fp32"):
+        a, b = graphs["res"][prec], eager["res"][prec]
+        assert np.array_equal(np.array(a[0]), np.array(b[0])) and np.array_equal(np.array(a[1]), np.array(b[1]))
+        assert a[2] == b[2]
