@@ -586,52 +586,72 @@ eig32_kernel(int n, int zsmem, DW w) {
       __syncthreads();
     }
   }
-  // --- back-transformation W = H_0 ... H_{r-3} Z.  A half-warp owns one column (two
-  // columns per warp); lane g of the half keeps rows g, g + 16, ... of it in
-  // registers, so applying a reflector takes one pass over the stored vector (kept
-  // in registers too) and a 4-step shuffle sum.  The result goes to W in FP64.
-  {
-    constexpr int RQ = kMaxDense / 16;
-    const int g = lane & 15, sub = lane >> 4;
-    for (int c0 = 2 * wid; c0 < r; c0 += 2 * nwarps) {
-      const int c = c0 + sub;
-      const bool cv = c < r;
-      float z[RQ];
+  // --- hand the back-transformation to backtr_kernel: the reflectors v_j as rows of
+  // A32 (row j = v_j, with the implicit 1 at j + 1 and zeros above), tau_j after them,
+  // and the eigenvectors of the tridiagonal matrix in Z32.
+  float* V = w.A32;
+  for (int q = tid; q < r * r; q += kBig) {
+    const int j = q / r, a = q % r;
+    float v = 0.f;
+    if (j + 2 < r && tau[j] != 0.f) v = (a == j + 1) ? 1.f : ((a > j + 1) ? A[a * r + j] : 0.f);
+    V[q] = v;
+  }
+  for (int j = tid; j < r; j += kBig) V[r * r + j] = (j + 2 < r) ? tau[j] : 0.f;
+  if (zsmem)
+    for (int q = tid; q < r * r; q += kBig) w.Z32[q] = Z[q];
+}
+
+// ------------------------------------- 3b. back-transformation (multi-CTA) ------
+// W = H_0 ... H_{r-3} Z with H_j = I - tau_j v_j v_j^T.  A half-warp owns one column
+// (two columns per warp, kBackWarps warps per CTA); lane g of the half keeps rows
+// g, g + 16, ... of the column in registers, reads v_j (a contiguous row of V) for its
+// rows, and a 4-step shuffle sum gives v_j . z.  The result goes to W in FP64.
+constexpr int kBackWarps = 4;
+__global__ void __launch_bounds__(kBackWarps * 32)
+backtr_kernel(int n, DW w) {
+  constexpr int RQ = kMaxDense / 16;
+  const int r = *w.rank;
+  const int lane = threadIdx.x & 31, g = lane & 15;
+  const int c = (blockIdx.x * kBackWarps + (threadIdx.x >> 5)) * 2 + (lane >> 4);
+  if (2 * (c / 2) >= r) return;                 // whole warp beyond the last column pair
+  const bool cv = c < r;
+  const float* __restrict__ V = w.A32;
+  const float* __restrict__ Z = w.Z32;
+  float z[RQ];
 #pragma unroll
-      for (int q = 0; q < RQ; ++q) {
+  for (int q = 0; q < RQ; ++q) {
+    const int a = g + 16 * q;
+    z[q] = (cv && a < r) ? Z[a * r + c] : 0.f;
+  }
+  for (int j = r - 3; j >= 0; --j) {
+    const float t = V[r * r + j];
+    if (t == 0.f) continue;
+    const float* vj = V + (size_t)j * r;
+    float s0 = 0.f, s1 = 0.f, v[RQ];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
+      v[q] = 0.f;
+      if (16 * q + 15 > j && 16 * q < r) {       // warp-uniform
         const int a = g + 16 * q;
-        z[q] = (cv && a < r) ? Z[a * r + c] : 0.f;
+        v[q] = (a < r) ? vj[a] : 0.f;
+        if (q & 1) s1 = fmaf(v[q], z[q], s1); else s0 = fmaf(v[q], z[q], s0);
       }
-      for (int j = r - 3; j >= 0; --j) {
-        const float t = tau[j];
-        if (t == 0.f) continue;
-        float s0 = 0.f, s1 = 0.f, v[RQ];
+    }
+    float s = s0 + s1;
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    s += __shfl_xor_sync(0xffffffffu, s, 8);
+    s *= t;
 #pragma unroll
-        for (int q = 0; q < RQ; ++q) {
-          v[q] = 0.f;
-          if (16 * q + 15 > j && 16 * q < r) {   // warp-uniform
-            const int a = g + 16 * q;
-            v[q] = (a == j + 1) ? 1.f : ((a > j + 1 && a < r) ? A[a * r + j] : 0.f);
-            if (q & 1) s1 = fmaf(v[q], z[q], s1); else s0 = fmaf(v[q], z[q], s0);
-          }
-        }
-        float s = s0 + s1;
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        s += __shfl_xor_sync(0xffffffffu, s, 4);
-        s += __shfl_xor_sync(0xffffffffu, s, 8);
-        s *= t;
+    for (int q = 0; q < RQ; ++q)
+      if (16 * q + 15 > j && 16 * q < r) z[q] = fmaf(-s, v[q], z[q]);
+  }
+  if (cv) {
 #pragma unroll
-        for (int q = 0; q < RQ; ++q)
-          if (16 * q + 15 > j && 16 * q < r) z[q] = fmaf(-s, v[q], z[q]);
-      }
-      if (cv) {
-#pragma unroll
-        for (int q = 0; q < RQ; ++q) {
-          const int a = g + 16 * q;
-          if (a < r) w.W[a * n + c] = (double)z[q];
-        }
-      }
+    for (int q = 0; q < RQ; ++q) {
+      const int a = g + 16 * q;
+      if (a < r) w.W[a * n + c] = (double)z[q];
     }
   }
 }
@@ -990,7 +1010,7 @@ DW carve(double* work, int n) {
   w.rl = p; p += n;
   w.lam = p; p += n;
   w.misc = p; p += 48;   // [0..8) scalars, [8..48) per-step norm accumulators
-  w.A32 = reinterpret_cast<float*>(p); p += nn / 2 + 1;
+  w.A32 = reinterpret_cast<float*>(p); p += (nn + n) / 2 + 1;
   w.Z32 = reinterpret_cast<float*>(p); p += nn / 2 + 1;
   w.LU32 = reinterpret_cast<float*>(p); p += (5 * nn + 1) / 2 + 1;
   w.perm = reinterpret_cast<int*>(p); p += n / 2 + 1;
@@ -1013,7 +1033,7 @@ void gemm(const GemmJob& j0, const GemmJob& j1, int nz, const DW& w, int n, doub
 
 size_t dense_work_doubles(int n) {
   const size_t nn = (size_t)n * n;
-  return 11 * nn + 3 * (size_t)n + 48 + 2 * (nn / 2 + 1) + (5 * nn + 1) / 2 + 1 + 4 * ((size_t)n / 2 + 2) + 1 + 16;
+  return 11 * nn + 3 * (size_t)n + 48 + (nn + n) / 2 + 1 + (nn / 2 + 1) + (5 * nn + 1) / 2 + 1 + 4 * ((size_t)n / 2 + 2) + 1 + 16;
 }
 
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k, double* theta,
@@ -1041,6 +1061,8 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
   BMG_CUDA(cudaFuncSetAttribute(eig32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
   eig32_kernel<<<1, kBig, esm, s>>>(n, zs ? 1 : 0, w);
   check_launch("eig32_kernel");
+  backtr_kernel<<<(n + 2 * kBackWarps - 1) / (2 * kBackWarps), kBackWarps * 32, 0, s>>>(n, w);
+  check_launch("backtr_kernel");
   // 4. refinement: steps separate pairs farther apart than a floor (relative to
   //    max|lam|); cluster steps diagonalise the groups below it exactly.  The floor
   //    starts at the resolution of the FP32 start and is lowered once the separated
