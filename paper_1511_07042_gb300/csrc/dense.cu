@@ -235,21 +235,30 @@ trsm_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mhat, in
     }
     acc[t] = v;
   }
+  // column i + 1 of L and its reciprocal pivot are loaded one step ahead
+  double lc[kRowsPerLane], lcn[kRowsPerLane], rli = 0.0, rln = w.rl[0];
+  auto load_col = [&](int i) {
+#pragma unroll
+    for (int t = 0; t < kRowsPerLane; ++t) {
+      const int q = lane + 32 * t;
+      lcn[t] = (i < r && q > i && q < r) ? w.Lt[i * n + q] : 0.0;
+    }
+  };
+  load_col(0);
   for (int i = 0; i < r; ++i) {
+#pragma unroll
+    for (int t = 0; t < kRowsPerLane; ++t) lc[t] = lcn[t];
+    rli = rln;
+    load_col(i + 1);
+    if (i + 1 < r) rln = w.rl[i + 1];
     const int ti = i >> 5, own = i & 31;
     double zi = 0.0;
 #pragma unroll
     for (int t = 0; t < kRowsPerLane; ++t)
-      if (t == ti && lane == own) { acc[t] *= w.rl[i]; zi = acc[t]; }
+      if (t == ti && lane == own) { acc[t] *= rli; zi = acc[t]; }
     zi = __shfl_sync(0xffffffffu, zi, own);
-    const double* Lc = w.Lt + i * n;   // column i of L
 #pragma unroll
-    for (int t = 0; t < kRowsPerLane; ++t) {
-      if (32 * t + 31 > i && 32 * t < r) {   // warp-uniform
-        const int q = lane + 32 * t;
-        if (q > i && q < r) acc[t] = fma(-Lc[q], zi, acc[t]);
-      }
-    }
+    for (int t = 0; t < kRowsPerLane; ++t) acc[t] = fma(-lc[t], zi, acc[t]);
   }
   double* out = pass == 0 ? w.Z : w.T;
 #pragma unroll
@@ -623,17 +632,28 @@ backtr_kernel(int n, DW w) {
     const int a = g + 16 * q;
     z[q] = (cv && a < r) ? Z[a * r + c] : 0.f;
   }
-  for (int j = r - 3; j >= 0; --j) {
-    const float t = V[r * r + j];
-    if (t == 0.f) continue;
-    const float* vj = V + (size_t)j * r;
-    float s0 = 0.f, s1 = 0.f, v[RQ];
+  // v_j and tau_j of the next reflector are loaded one step ahead
+  float vn[RQ], tn = 0.f;
+  auto load_v = [&](int j) {
+    tn = (j >= 0) ? V[r * r + j] : 0.f;
 #pragma unroll
     for (int q = 0; q < RQ; ++q) {
-      v[q] = 0.f;
+      const int a = g + 16 * q;
+      vn[q] = (j >= 0 && 16 * q + 15 > j && 16 * q < r && a < r) ? V[(size_t)j * r + a] : 0.f;
+    }
+  };
+  load_v(r - 3);
+  for (int j = r - 3; j >= 0; --j) {
+    float v[RQ];
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) v[q] = vn[q];
+    const float t = tn;
+    load_v(j - 1);
+    if (t == 0.f) continue;
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < RQ; ++q) {
       if (16 * q + 15 > j && 16 * q < r) {       // warp-uniform
-        const int a = g + 16 * q;
-        v[q] = (a < r) ? vj[a] : 0.f;
         if (q & 1) s1 = fmaf(v[q], z[q], s1); else s0 = fmaf(v[q], z[q], s0);
       }
     }
@@ -685,6 +705,7 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
   double* As = gsm;                 // kTile x r
   double* Bs = gsm + kTile * r;     // r x kTile
   const int tid = threadIdx.x;
+#pragma unroll 8
   for (int q = tid; q < kTile * r; q += kTile * kTile) {
     const int a = q / r, kq = q % r;
     const int row = row0 + a;
@@ -696,6 +717,7 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
     __syncthreads();
   }
   const double thr = (jb.bmode == 1) ? s_thr : 0.0;
+#pragma unroll 4
   for (int q = tid; q < r * kTile; q += kTile * kTile) {
     const int kq = q / kTile, b = q % kTile;
     const int col = col0 + b;
@@ -959,21 +981,30 @@ backsub_kernel(int n, int k, DW w, double* __restrict__ Y) {
     const int q = lane + 32 * t;
     acc[t] = (q < r) ? w.W[q * n + oc] : 0.0;
   }
+  // row i - 1 of L and its reciprocal pivot are loaded one step ahead
+  double li[kRowsPerLane], lin[kRowsPerLane], rli = 0.0, rln = (r > 0) ? w.rl[r - 1] : 0.0;
+  auto load_row = [&](int i) {
+#pragma unroll
+    for (int t = 0; t < kRowsPerLane; ++t) {
+      const int q = lane + 32 * t;
+      lin[t] = (i >= 0 && q < i) ? w.L[i * n + q] : 0.0;
+    }
+  };
+  load_row(r - 1);
   for (int i = r - 1; i >= 0; --i) {
+#pragma unroll
+    for (int t = 0; t < kRowsPerLane; ++t) li[t] = lin[t];
+    rli = rln;
+    load_row(i - 1);
+    if (i > 0) rln = w.rl[i - 1];
     const int ti = i >> 5, own = i & 31;
     double zi = 0.0;
 #pragma unroll
     for (int t = 0; t < kRowsPerLane; ++t)
-      if (t == ti && lane == own) { acc[t] *= w.rl[i]; zi = acc[t]; }
+      if (t == ti && lane == own) { acc[t] *= rli; zi = acc[t]; }
     zi = __shfl_sync(0xffffffffu, zi, own);
-    const double* Li = w.L + i * n;   // row i of L
 #pragma unroll
-    for (int t = 0; t < kRowsPerLane; ++t) {
-      if (32 * t < i) {   // warp-uniform
-        const int q = lane + 32 * t;
-        if (q < i) acc[t] = fma(-Li[q], zi, acc[t]);
-      }
-    }
+    for (int t = 0; t < kRowsPerLane; ++t) acc[t] = fma(-li[t], zi, acc[t]);
   }
   const int* perm = w.perm;
 #pragma unroll
