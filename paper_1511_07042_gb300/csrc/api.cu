@@ -731,8 +731,8 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
   auto part_a = [&]() {
     // 1-2: products, Grams, couplings Q^T AX, Q^T MX by the restriction chain
     spmm_am<T>(mf, Af, Mf, b.X, ld, b.AX, b.MX, s);
-    gram(b.X, b.AX, nf, k, ld, w.GA.get(), w.partial.get(), gram_parts(nf), s);
-    gram(b.X, b.MX, nf, k, ld, w.GM.get(), w.partial.get(), gram_parts(nf), s);
+    gram(b.X, b.AX, nf, k, ld, w.GA.get(), w.partial.get(), gram_parts(nf), s, true);
+    gram(b.X, b.MX, nf, k, ld, w.GM.get(), w.partial.get(), gram_parts(nf), s, true);
     const T* ca = b.AX;
     const T* cm = b.MX;
     for (int j = f; j >= 2; --j) {

@@ -228,10 +228,12 @@ template <typename T>
 void prolong(const Mesh& fine, const T* Xc, T* Y, int ld, bool add, cudaStream_t s);
 template <typename T>
 void restrict_(const Mesh& coarse, const T* R, T* Zc, int ld, cudaStream_t s);
+// sym: Y = S X with S symmetric, so G is symmetric: only the 4x4 tiles on and above
+// the diagonal are formed (half the products) and the rest mirrored.
 void gram(const double* X, const double* Y, int n, int k, int ld, double* G, double* partial,
-          int nparts, cudaStream_t s);
+          int nparts, cudaStream_t s, bool sym = false);
 void gram(const float* X, const float* Y, int n, int k, int ld, double* G, double* partial,
-          int nparts, cudaStream_t s);
+          int nparts, cudaStream_t s, bool sym = false);
 int gram_parts(int n);
 std::string tuned_report();
 template <typename T>

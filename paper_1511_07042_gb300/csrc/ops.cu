@@ -233,15 +233,29 @@ __global__ void restrict_kernel(const int* __restrict__ row_ptr, const int* __re
 constexpr int kGramRows = 16;
 constexpr int kGramThreads = 256;
 
+// Output tile t of a Gram product with tk x tk tiles of 4 x 4: all tiles, or (sym)
+// only the tiles on and above the diagonal, numbered row by row.
+__device__ __forceinline__ void gram_tile(int t, int tk, int sym, int& ti, int& tj) {
+  if (!sym) {
+    ti = (t / tk) * 4;
+    tj = (t % tk) * 4;
+    return;
+  }
+  int I = 0, rem = t;
+  while (rem >= tk - I) { rem -= tk - I; ++I; }
+  ti = I * 4;
+  tj = (I + rem) * 4;
+}
+
 template <int NT>
 __global__ void __launch_bounds__(kGramThreads)
 gram_kernel(const double* __restrict__ X, const double* __restrict__ Y, int n, int k, int ld,
-            int rows_per_part, double* __restrict__ partial) {
+            int rows_per_part, double* __restrict__ partial, int sym) {
   extern __shared__ double sh[];
   double* sx = sh;
   double* sy = sh + kGramRows * ld;
   const int tk = (k + 3) / 4;
-  const int ntiles = tk * tk;
+  const int ntiles = sym ? tk * (tk + 1) / 2 : tk * tk;
   double acc[NT][4][4];
 #pragma unroll
   for (int t = 0; t < NT; ++t)
@@ -265,7 +279,8 @@ gram_kernel(const double* __restrict__ X, const double* __restrict__ Y, int n, i
     for (int t = 0; t < NT; ++t) {
       const int tile = threadIdx.x + t * kGramThreads;
       if (tile >= ntiles) continue;
-      const int ti = (tile / tk) * 4, tj = (tile % tk) * 4;
+      int ti, tj;
+      gram_tile(tile, tk, sym, ti, tj);
       for (int r = 0; r < kGramRows; ++r) {
         double xv[4], yv[4];
 #pragma unroll
@@ -285,7 +300,8 @@ gram_kernel(const double* __restrict__ X, const double* __restrict__ Y, int n, i
   for (int t = 0; t < NT; ++t) {
     const int tile = threadIdx.x + t * kGramThreads;
     if (tile >= ntiles) continue;
-    const int ti = (tile / tk) * 4, tj = (tile % tk) * 4;
+    int ti, tj;
+    gram_tile(tile, tk, sym, ti, tj);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -304,15 +320,16 @@ gram_kernel(const double* __restrict__ X, const double* __restrict__ Y, int n, i
 constexpr int kGram32Threads = 512;
 __global__ void __launch_bounds__(kGram32Threads)
 gram_f32_kernel(const float* __restrict__ X, const float* __restrict__ Y, int n, int k, int ld,
-                int rows_per_part, double* __restrict__ partial) {
+                int rows_per_part, double* __restrict__ partial, int sym) {
   extern __shared__ __align__(16) float shf[];
   float* sx = shf;
   float* sy = shf + kGramRows * ld;
   const int tk = (k + 3) / 4;
-  const int ntiles = tk * tk;
+  const int ntiles = sym ? tk * (tk + 1) / 2 : tk * tk;
   const int tile = threadIdx.x + blockIdx.y * kGram32Threads;
   const bool active = tile < ntiles;
-  const int ti = active ? (tile / tk) * 4 : 0, tj = active ? (tile % tk) * 4 : 0;
+  int ti = 0, tj = 0;
+  if (active) gram_tile(tile, tk, sym, ti, tj);
   float s[4][4], c[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -359,12 +376,20 @@ gram_f32_kernel(const float* __restrict__ X, const float* __restrict__ Y, int n,
       if (ti + a < k && tj + b < k) out[(ti + a) * k + tj + b] = (double)s[a][b] + (double)c[a][b];
 }
 
+// G[q] = sum of the block partials in block order.  With sym (a k x k Gram of which
+// only the tiles on and above the diagonal were formed) an entry below the diagonal
+// tiles takes its mirror.
 __global__ void gram_reduce_kernel(const double* __restrict__ partial, int nparts, int kk,
-                                   double* __restrict__ G) {
+                                   double* __restrict__ G, int k = 0, int sym = 0) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= kk) return;
+  int src = q;
+  if (sym) {
+    const int i = q / k, j = q % k;
+    if (i / 4 > j / 4) src = j * k + i;
+  }
   double s = 0.0;
-  for (int b = 0; b < nparts; ++b) s += partial[(size_t)b * kk + q];
+  for (int b = 0; b < nparts; ++b) s += partial[(size_t)b * kk + src];
   G[q] = s;
 }
 
@@ -689,35 +714,36 @@ void restrict_(const Mesh& coarse, const T* R, T* Zc, int ld, cudaStream_t s) {
 int gram_parts(int n) { return std::max(1, std::min(304, (n + 63) / 64)); }
 
 void gram(const double* X, const double* Y, int n, int k, int ld, double* G, double* partial,
-          int nparts, cudaStream_t s) {
+          int nparts, cudaStream_t s, bool sym) {
   const int rows_per_part = (n + nparts - 1) / nparts;
   const int tk = (k + 3) / 4;
-  const int ntiles = tk * tk;
+  const int ntiles = sym ? tk * (tk + 1) / 2 : tk * tk;
   const size_t smem = 2 * kGramRows * ld * sizeof(double);
   prof_begin(KC_GRAM, s);
-  if (ntiles <= kGramThreads) gram_kernel<1><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial);
-  else if (ntiles <= 2 * kGramThreads) gram_kernel<2><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial);
-  else if (ntiles <= 4 * kGramThreads) gram_kernel<4><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial);
-  else if (ntiles <= 8 * kGramThreads) gram_kernel<8><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial);
+  if (ntiles <= kGramThreads) gram_kernel<1><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial, sym ? 1 : 0);
+  else if (ntiles <= 2 * kGramThreads) gram_kernel<2><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial, sym ? 1 : 0);
+  else if (ntiles <= 4 * kGramThreads) gram_kernel<4><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial, sym ? 1 : 0);
+  else if (ntiles <= 8 * kGramThreads) gram_kernel<8><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial, sym ? 1 : 0);
   else fail(BMG_ERR_INVALID_ARG, "gram: k too large (k <= 180)");
   check_launch("gram_kernel");
-  gram_reduce_kernel<<<blocks_for(k * k, 256), 256, 0, s>>>(partial, nparts, k * k, G);
+  gram_reduce_kernel<<<blocks_for(k * k, 256), 256, 0, s>>>(partial, nparts, k * k, G, k, sym ? 1 : 0);
   check_launch("gram_reduce_kernel");
-  prof_end(KC_GRAM, s, 16.0 * n * ld + 16.0 * nparts * k * k + 8.0 * k * k, 2.0 * n * k * k);
+  prof_end(KC_GRAM, s, 16.0 * n * ld + 16.0 * nparts * k * k + 8.0 * k * k,
+           (sym ? 1.0 : 2.0) * n * k * k + (sym ? 4.0 * n * k : 0.0));
 }
 
 void gram(const float* X, const float* Y, int n, int k, int ld, double* G, double* partial,
-          int nparts, cudaStream_t s) {
+          int nparts, cudaStream_t s, bool sym) {
   if (ld % 4) fail(BMG_ERR_INVALID_ARG, "gram: FP32 blocks need ld % 4 == 0");
   const int rows_per_part = (n + nparts - 1) / nparts;
   const int tk = (k + 3) / 4;
-  const int ntiles = tk * tk;
+  const int ntiles = sym ? tk * (tk + 1) / 2 : tk * tk;
   const size_t smem = 2 * kGramRows * ld * sizeof(float);
   prof_begin(KC_GRAM, s);
   const dim3 grid(nparts, (ntiles + kGram32Threads - 1) / kGram32Threads);
-  gram_f32_kernel<<<grid, kGram32Threads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial);
+  gram_f32_kernel<<<grid, kGram32Threads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial, sym ? 1 : 0);
   check_launch("gram_f32_kernel");
-  gram_reduce_kernel<<<blocks_for(k * k, 256), 256, 0, s>>>(partial, nparts, k * k, G);
+  gram_reduce_kernel<<<blocks_for(k * k, 256), 256, 0, s>>>(partial, nparts, k * k, G, k, sym ? 1 : 0);
   check_launch("gram_reduce_kernel");
   prof_end(KC_GRAM, s, 8.0 * n * ld + 16.0 * nparts * k * k + 8.0 * k * k, 2.0 * n * k * k);
 }
