@@ -558,9 +558,9 @@ void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, cons
   if (Xin != Xout) BMG_CUDA(cudaMemcpyAsync(Xout, Xin, bytes, cudaMemcpyDeviceToDevice, s));
   const Level& lv = p->lev[j];
   for (int it = 0; it < o.nu; ++it) {
-    for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s);
+    for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s, work);
     if (o.smoother == BMG_SMOOTH_MCSGS)
-      for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s);
+      for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s, work);
   }
 }
 

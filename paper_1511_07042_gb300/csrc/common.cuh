@@ -217,10 +217,12 @@ void spmm_am(const Mesh& m, const T* a, const T* mm, const T* X, int ld, T* AX, 
 template <typename T>
 void jacobi_sweep(const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const T* X,
                   T* Xout, const T* B, const T* shift, int ld, double omega, cudaStream_t s);
+// scratch: a free [N][ld] block of the level, used to time shape candidates on the
+// colour's rows (the sweep itself runs in place), or nullptr
 template <typename T>
 void gs_colour_sweep(const Mesh& m, const Level& lv, int colour, const T* a, const T* mm,
                      const T* da, const T* dm, T* X, const T* B, const T* shift, int ld,
-                     cudaStream_t s);
+                     cudaStream_t s, T* scratch = nullptr);
 template <typename T>
 void residual(const Mesh& m, const T* a, const T* mm, const T* X, const T* B, const T* shift,
               int ld, T* R, cudaStream_t s);

@@ -88,6 +88,19 @@ __device__ __forceinline__ void gather_row(const int* __restrict__ col, const T*
   }
 }
 
+// 1/d for the smoother update.  FP64: an FP32 seed refined by two Newton-Raphson
+// steps y <- y (2 - d y) in FP64 (the relative error squares: 2^-23 -> 2^-46 -> below
+// rounding), a handful of FP64 operations instead of a full-precision division.  The
+// shifted diagonal d is far inside the FP32 range.  FP32: the correctly rounded
+// reciprocal.
+__device__ __forceinline__ double recip(double d) {
+  double y = (double)__frcp_rn((float)d);
+  y = y * fma(-d, y, 2.0);
+  y = y * fma(-d, y, 2.0);
+  return y;
+}
+__device__ __forceinline__ float recip(float d) { return __frcp_rn(d); }
+
 // ---- fused SpMM: AX = A X, MX = M X  (one pass over the shared pattern) ----
 // Row tiling: LPR lanes per row (32 / LPR rows per warp), CPL 16-byte chunks per lane
 // (chunks sl, sl + LPR, ...), blockDim.x / 32 warps per block; picked per level size
@@ -169,7 +182,8 @@ row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
 #pragma unroll
       for (int q = 0; q < W; ++q) {
         const T d = dai - s[q] * dmi;
-        o[q] = (MODE == 0) ? x[q] + omega * r[q] / d : x[q] + r[q] / d;
+        const T rd = recip(d);
+        o[q] = (MODE == 0) ? x[q] + omega * (r[q] * rd) : x[q] + r[q] * rd;
       }
       // padding columns carry zero shift, zero data and stay zero
       if (MODE == 0) stv_cs(Out, idx, o); else stv(Out, idx, o);
@@ -639,15 +653,21 @@ void spmm_am(const Mesh& m, const T* a, const T* mm, const T* X, int ld, T* AX, 
 template <typename T, int MODE>
 static void row_update(const Mesh& m, const T* a, const T* mm, const T* da, const T* dm,
                        const int* rows, int nrows, long long nnz_rows, const T* X, T* Out,
-                       const T* B, const T* shift, int ld, double omega, cudaStream_t s) {
+                       const T* B, const T* shift, int ld, double omega, cudaStream_t s,
+                       T* scratch = nullptr) {
   const int nch = ld / Chunk<T>::W;
   if (nrows == 0) return;
-  // Gauss-Seidel sweeps run in place and are not re-run for timing: they take the
-  // shape tuned for the residual (same gathers, out of place) or the Jacobi sweep of
-  // the same level
+  // Gauss-Seidel sweeps run in place and are not re-run for timing: with a scratch
+  // block they take the shape tuned for the residual kernel on the same rows (same
+  // gathers, written to the scratch block), else the one of the level's residual or
+  // Jacobi sweep
   const int kind = (MODE == 2) ? 2 : 1;
   RowCfg c = default_cfg(nch);
-  if (MODE == 1) {
+  if (MODE == 1 && scratch) {
+    c = tune_rows(3, (int)sizeof(T), nch, nrows, s, [&](RowCfg q) {
+      row_launch<T, 2>(q, m, a, mm, da, dm, rows, nrows, X, scratch, B, shift, nch, omega, s);
+    });
+  } else if (MODE == 1) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     for (int kd : {2, 1}) {
       auto it = g_tuned.find(std::make_tuple(kd, (int)sizeof(T), nch, m.n));
@@ -675,10 +695,10 @@ void jacobi_sweep(const Mesh& m, const T* a, const T* mm, const T* da, const T* 
 
 template <typename T>
 void gs_colour_sweep(const Mesh& m, const Level& lv, int c, const T* a, const T* mm, const T* da,
-                     const T* dm, T* X, const T* B, const T* shift, int ld, cudaStream_t s) {
+                     const T* dm, T* X, const T* B, const T* shift, int ld, cudaStream_t s, T* scratch) {
   const int b = lv.colour_ptr_host[c], e = lv.colour_ptr_host[c + 1];
   row_update<T, 1>(m, a, mm, da, dm, lv.colour_rows.get() + b, e - b, lv.colour_nnz_host[c], X, X, B,
-                   shift, ld, 1.0, s);
+                   shift, ld, 1.0, s, scratch);
 }
 
 template <typename T>
@@ -797,7 +817,7 @@ void scale_rhs(const T* MU, const double* theta, int n, int k, int ld, T* B, cud
 std::string tuned_report() {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   std::string out;
-  static const char* kinds[3] = {"spmm", "jacobi", "residual"};
+  static const char* kinds[4] = {"spmm", "jacobi", "residual", "gs_colour"};
   for (const auto& kv : g_tuned) {
     const auto& k = kv.first;
     const RowCfg c = kv.second;
@@ -814,7 +834,7 @@ std::string tuned_report() {
   template void jacobi_sweep<T>(const Mesh&, const T*, const T*, const T*, const T*, const T*, T*,     \
                                 const T*, const T*, int, double, cudaStream_t);                        \
   template void gs_colour_sweep<T>(const Mesh&, const Level&, int, const T*, const T*, const T*,       \
-                                   const T*, T*, const T*, const T*, int, cudaStream_t);               \
+                                   const T*, T*, const T*, const T*, int, cudaStream_t, T*);           \
   template void residual<T>(const Mesh&, const T*, const T*, const T*, const T*, const T*, int, T*,    \
                             cudaStream_t);                                                             \
   template void prolong<T>(const Mesh&, const T*, T*, int, bool, cudaStream_t);                        \
