@@ -225,9 +225,11 @@ def precision_form_extra(bmg, inputs, np, torch, hbm_peak, steps):
     X0 = inputs.gaussian_block(inputs.n_vertices(2), wl["k"], wl["seed"])
     ref = np.loadtxt(os.path.join(ROOT, "tests", "golden", "sphere655362_k128_mixed_oracle_eigs.txt"))[:, 1]
     out = {"workload": "sphere655362_k128_jacobi", "vertices": inputs.n_vertices(wl["refinements"]),
-           "levels": wl["refinements"], "k": wl["k"], "n_wanted": wl["n_wanted"], "tol": wl["tol"]}
+           "levels": wl["refinements"], "k": wl["k"], "n_wanted": wl["n_wanted"], "tol": wl["tol"],
+           "cycles_intermediate": 8}
     for prec in ("fp32", "fp64"):
-        opt = bmg.options(smoother=wl["smoother"], nu=wl["nu"], omega=wl["omega"], precision=prec)
+        opt = bmg.options(smoother=wl["smoother"], nu=wl["nu"], omega=wl["omega"], precision=prec,
+                          cycles_intermediate=8)
         prob.solve(X0, wl["k"], wl["n_wanted"], wl["sigma"], wl["tol"], opt, evecs=False)   # warm-up
         bmg.profile_reset()
         bmg.profile_enable(prec == "fp32")

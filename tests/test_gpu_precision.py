@@ -166,7 +166,8 @@ def test_precision_form_sphere655362_k128(gpu_bmg):
     prob = gpu_bmg.Problem(v, t, wl["refinements"])
     prob.hierarchy(wl["refinements"])
     X0 = inputs.gaussian_block(inputs.n_vertices(2), wl["k"], wl["seed"])
-    opt = gpu_bmg.options(smoother=wl["smoother"], nu=wl["nu"], omega=wl["omega"], precision="fp32")
+    opt = gpu_bmg.options(smoother=wl["smoother"], nu=wl["nu"], omega=wl["omega"], precision="fp32",
+                          cycles_intermediate=8)
     ev, U, rs, info = prob.solve(X0, wl["k"], wl["n_wanted"], wl["sigma"], wl["tol"], opt, evecs=False)
     assert info.converged == 1 and info.fp32_cycles > 0 and np.all(rs <= wl["tol"])
     err = np.abs(np.sort(ev) - np.sort(ref)) / np.maximum(np.abs(ref), 1.0)
