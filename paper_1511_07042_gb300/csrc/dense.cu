@@ -42,7 +42,8 @@ constexpr int kTile = 8;                 // output tile of the refinement produc
 // Scratch carved from one device allocation; n x n blocks row-major with stride n.
 struct DW {
   double *S, *L, *Lt, *T, *Z, *W, *W2, *G, *SS, *P, *E, *d, *rl, *lam, *misc;
-  float *A32, *Z32, *LU32;
+  float *A32, *Z32, *LU32, *T3;   // T3: d, e, shifts of the tridiagonal problem, tiny
+  int *cls;                        // cls[0] = cluster count, cls[1..] = cluster starts
   int *perm, *order, *rank, *srt, *cl;
 };
 
@@ -285,7 +286,7 @@ __device__ __forceinline__ float start_value(int a, int j) {
 // Solves per eigenvector (each followed by orthonormalisation inside the clusters).
 constexpr int kInvIters = 3;
 __global__ void __launch_bounds__(kBig)
-eig32_kernel(int n, int zsmem, DW w) {
+eig32_kernel(int n, DW w) {
   extern __shared__ float fsm[];
   __shared__ float d[kMaxN], e[kMaxN], e2[kMaxN], tau[kMaxN], vb[kMaxN], pv[kMaxN], lam[kMaxN];
   __shared__ float redf[32], slo[32], shi[32];
@@ -293,7 +294,6 @@ eig32_kernel(int n, int zsmem, DW w) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = kBig / 32;
   float* A = fsm;                                   // r x r
-  float* Z = zsmem ? fsm + r * r : w.Z32;           // r x r eigenvectors (columns)
   for (int i = wid; i < r; i += nwarps)
     for (int j = lane; j < r; j += 32) A[i * r + j] = (float)(0.5 * (w.T[i * n + j] + w.T[j * n + i]));
   __syncthreads();
@@ -419,15 +419,9 @@ eig32_kernel(int n, int zsmem, DW w) {
     }
   }
   __syncthreads();
-  // --- inverse iteration, block form of the scheme of LAPACK's stein.  Clusters are
+  // --- clusters and shifts for the inverse iteration (invit_kernel): clusters are
   // chains of eigenvalues closer than 1e-4 span; members of a cluster get shifts at
-  // least 10 ulps apart.  Thread j factors T3 - x_j I (LU with partial pivoting, the
-  // factors in global scratch, planes [5][row][j]) and solves for column j of Z; after
-  // each of the kInvIters solves the columns are scaled by their largest entry, and
-  // one warp per cluster orthonormalises the members in order (modified
-  // Gram-Schmidt, in blocks of 8, twice).  All eigenvectors advance together, so the sequential work is one
-  // factorisation and kInvIters solves of length r, not one per member of the
-  // largest cluster.
+  // least 10 ulps apart.
   __shared__ int cst[kMaxN + 1];
   __shared__ int s_ncl;
   const float ortol = 1e-4f * span;
@@ -452,152 +446,18 @@ eig32_kernel(int n, int zsmem, DW w) {
     s_ncl = nc;
   }
   __syncthreads();
-  {
-    const size_t pl = (size_t)r * r;
-    float* __restrict__ LU = w.LU32;
-    if (tid < r) {
-      const int jv = tid;
-      const float x = shift[jv];
-      float p0 = d[0] - x, p1 = (r > 1) ? e[0] : 0.f;
-      for (int jj = 0; jj + 1 < r; ++jj) {
-        const float bsub = e[jj], anext = d[jj + 1] - x, cnext = (jj + 2 < r) ? e[jj + 1] : 0.f;
-        float a0, a1, a2, m, sw;
-        if (fabsf(bsub) > fabsf(p0)) {
-          a0 = bsub; a1 = anext; a2 = cnext; sw = 1.f;
-          m = __fdividef(p0, bsub);
-          p0 = p1 - m * anext;
-          p1 = -m * cnext;
-        } else {
-          a0 = p0; a1 = p1; a2 = 0.f; sw = 0.f;
-          m = (p0 != 0.f) ? __fdividef(bsub, p0) : 0.f;
-          p0 = anext - m * p1;
-          p1 = cnext;
-        }
-        if (fabsf(a0) < tiny) a0 = (a0 < 0.f) ? -tiny : tiny;
-        const size_t o = (size_t)jj * r + jv;
-        LU[o] = __frcp_rn(a0);
-        LU[pl + o] = a1;
-        LU[2 * pl + o] = a2;
-        LU[3 * pl + o] = m;
-        LU[4 * pl + o] = sw;
-      }
-      const size_t o = (size_t)(r - 1) * r + jv;
-      LU[o] = __frcp_rn((fabsf(p0) < tiny) ? ((p0 < 0.f) ? -tiny : tiny) : p0);
-      LU[pl + o] = 0.f;
-      LU[2 * pl + o] = 0.f;
-      for (int a = 0; a < r; ++a) Z[a * r + jv] = start_value(a, jv);
-    }
-    for (int itr = 0; itr < kInvIters; ++itr) {
-      if (tid < r) {
-        const int jv = tid;
-        float* Zc = Z + jv;
-        // forward elimination with the row swaps; cur carries the updated z[jj]
-        float cur = Zc[0];
-        for (int j0 = 0; j0 + 1 < r; j0 += 8) {
-          float mv[8], sv[8], nx[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int jj = j0 + u;
-            if (jj + 1 < r) {
-              const size_t o = (size_t)jj * r + jv;
-              mv[u] = LU[3 * pl + o];
-              sv[u] = LU[4 * pl + o];
-              nx[u] = Zc[(jj + 1) * r];
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int jj = j0 + u;
-            if (jj + 1 < r) {
-              if (sv[u] != 0.f) {
-                Zc[jj * r] = nx[u];
-                cur = cur - mv[u] * nx[u];
-              } else {
-                Zc[jj * r] = cur;
-                cur = nx[u] - mv[u] * cur;
-              }
-            }
-          }
-        }
-        Zc[(r - 1) * r] = cur;
-        // back substitution with the upper factor (three diagonals)
-        float z1 = 0.f, z2 = 0.f, mx = 0.f;
-        for (int a1 = r - 1; a1 >= 0; a1 -= 4) {
-          float u0v[4], u1v[4], u2v[4], zv[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int a = a1 - u;
-            if (a >= 0) {
-              const size_t o = (size_t)a * r + jv;
-              u0v[u] = LU[o];
-              u1v[u] = LU[pl + o];
-              u2v[u] = LU[2 * pl + o];
-              zv[u] = Zc[a * r];
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int a = a1 - u;
-            if (a >= 0) {
-              const float t = (zv[u] - u1v[u] * z1 - u2v[u] * z2) * u0v[u];
-              Zc[a * r] = t;
-              z2 = z1;
-              z1 = t;
-              mx = fmaxf(mx, fabsf(t));
-            }
-          }
-        }
-        // scale first (the solve can grow the vector by 1/tiny)
-        const float inv = (mx > 0.f) ? 1.f / mx : 0.f;
-        for (int a = 0; a < r; ++a) Zc[a * r] *= inv;
-      }
-      __syncthreads();
-      for (int c = wid; c < s_ncl; c += nwarps) {
-        for (int jv = cst[c]; jv < cst[c + 1]; ++jv) {
-          // orthogonalise against the earlier members: blocks of 8 at a time
-          // (independent dot products, then one combined update), two passes
-          for (int pass = 0; pass < 2; ++pass) {
-            for (int q0 = cst[c]; q0 < jv; q0 += 8) {
-              const int nq = min(8, jv - q0);
-              // slots beyond nq read column q0 and get weight 0
-              float dot[8];
-#pragma unroll
-              for (int u = 0; u < 8; ++u) dot[u] = 0.f;
-              for (int a = lane; a < r; a += 32) {
-                const float zj = Z[a * r + jv];
-                const float* zr = Z + a * r + q0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) dot[u] = fmaf(zr[u < nq ? u : 0], zj, dot[u]);
-              }
-#pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                const float t = warp_sumf(dot[u]);
-                dot[u] = (u < nq) ? t : 0.f;
-              }
-              for (int a = lane; a < r; a += 32) {
-                float zj = Z[a * r + jv];
-                const float* zr = Z + a * r + q0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) zj = fmaf(-dot[u], zr[u < nq ? u : 0], zj);
-                Z[a * r + jv] = zj;
-              }
-              __syncwarp();
-            }
-          }
-          float nrm = 0.f;
-          for (int a = lane; a < r; a += 32) nrm += Z[a * r + jv] * Z[a * r + jv];
-          nrm = warp_sumf(nrm);
-          nrm = (nrm > 0.f) ? rsqrtf(nrm) : 0.f;
-          for (int a = lane; a < r; a += 32) Z[a * r + jv] *= nrm;
-          __syncwarp();
-        }
-      }
-      __syncthreads();
-    }
+  for (int i = tid; i < r; i += kBig) {
+    w.T3[i] = d[i];
+    w.T3[n + i] = e[i];
+    w.T3[2 * n + i] = shift[i];
   }
+  if (tid == 0) {
+    w.T3[3 * n] = tiny;
+    w.cls[0] = s_ncl;
+  }
+  for (int c = tid; c <= s_ncl; c += kBig) w.cls[1 + c] = cst[c];
   // --- hand the back-transformation to backtr_kernel: the reflectors v_j as rows of
-  // A32 (row j = v_j, with the implicit 1 at j + 1 and zeros above), tau_j after them,
-  // and the eigenvectors of the tridiagonal matrix in Z32.
+  // A32 (row j = v_j, with the implicit 1 at j + 1 and zeros above), tau_j after them.
   float* V = w.A32;
   for (int q = tid; q < r * r; q += kBig) {
     const int j = q / r, a = q % r;
@@ -606,8 +466,180 @@ eig32_kernel(int n, int zsmem, DW w) {
     V[q] = v;
   }
   for (int j = tid; j < r; j += kBig) V[r * r + j] = (j + 2 < r) ? tau[j] : 0.f;
-  if (zsmem)
-    for (int q = tid; q < r * r; q += kBig) w.Z32[q] = Z[q];
+}
+
+// ------------------------------------- 3a. inverse iteration (one CTA per cluster) --
+// Block form of the scheme of LAPACK's stein on T3 = tridiag(d, e): member j of the
+// cluster factors T3 - x_j I (LU with partial pivoting, factors in global scratch,
+// planes [5][row][j]) and solves for its column; after each of the kInvIters solves the
+// columns are scaled by their largest entry and one warp orthonormalises the members
+// in order (Gram-Schmidt in blocks of 8 projections, two passes).  The cluster's columns
+// live in shared memory (row stride odd, no bank conflicts) when it has at most
+// kInvSmemMembers members, else in the global eigenvector block.  All clusters run at
+// once, so the sequential work is one factorisation and kInvIters solves of length r.
+constexpr int kInvThreads = 64;
+constexpr int kInvSmemMembers = 63;
+__global__ void __launch_bounds__(kInvThreads)
+invit_kernel(int n, DW w) {
+  extern __shared__ float zsh[];
+  const int r = *w.rank;
+  const int ncl = w.cls[0];
+  const int c = blockIdx.x;
+  if (c >= ncl) return;
+  const int c0 = w.cls[1 + c], m = w.cls[2 + c] - c0;
+  const float* __restrict__ d = w.T3;
+  const float* __restrict__ e = w.T3 + n;
+  const float* __restrict__ shift = w.T3 + 2 * n;
+  const float tiny = w.T3[3 * n];
+  const bool insm = m <= kInvSmemMembers;
+  const int zld = insm ? (m | 1) : r;
+  float* Z = insm ? zsh : w.Z32 + c0;            // Z[a * zld + t], member t = jv - c0
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const size_t pl = (size_t)r * r;
+  float* __restrict__ LU = w.LU32;
+  for (int t = tid; t < m; t += kInvThreads) {
+    const int jv = c0 + t;
+    const float x = shift[jv];
+    float p0 = d[0] - x, p1 = (r > 1) ? e[0] : 0.f;
+    for (int jj = 0; jj + 1 < r; ++jj) {
+      const float bsub = e[jj], anext = d[jj + 1] - x, cnext = (jj + 2 < r) ? e[jj + 1] : 0.f;
+      float a0, a1, a2, mm, sw;
+      if (fabsf(bsub) > fabsf(p0)) {
+        a0 = bsub; a1 = anext; a2 = cnext; sw = 1.f;
+        mm = __fdividef(p0, bsub);
+        p0 = p1 - mm * anext;
+        p1 = -mm * cnext;
+      } else {
+        a0 = p0; a1 = p1; a2 = 0.f; sw = 0.f;
+        mm = (p0 != 0.f) ? __fdividef(bsub, p0) : 0.f;
+        p0 = anext - mm * p1;
+        p1 = cnext;
+      }
+      if (fabsf(a0) < tiny) a0 = (a0 < 0.f) ? -tiny : tiny;
+      const size_t o = (size_t)jj * r + jv;
+      LU[o] = __frcp_rn(a0);
+      LU[pl + o] = a1;
+      LU[2 * pl + o] = a2;
+      LU[3 * pl + o] = mm;
+      LU[4 * pl + o] = sw;
+    }
+    const size_t o = (size_t)(r - 1) * r + jv;
+    LU[o] = __frcp_rn((fabsf(p0) < tiny) ? ((p0 < 0.f) ? -tiny : tiny) : p0);
+    LU[pl + o] = 0.f;
+    LU[2 * pl + o] = 0.f;
+    for (int a = 0; a < r; ++a) Z[a * zld + t] = start_value(a, jv);
+  }
+  for (int itr = 0; itr < kInvIters; ++itr) {
+    for (int t = tid; t < m; t += kInvThreads) {
+      const int jv = c0 + t;
+      float* Zc = Z + t;
+      // forward elimination with the row swaps; cur carries the updated z[jj]
+      float cur = Zc[0];
+      for (int j0 = 0; j0 + 1 < r; j0 += 8) {
+        float mv[8], sv[8], nx[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int jj = j0 + u;
+          if (jj + 1 < r) {
+            const size_t o = (size_t)jj * r + jv;
+            mv[u] = LU[3 * pl + o];
+            sv[u] = LU[4 * pl + o];
+            nx[u] = Zc[(jj + 1) * zld];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int jj = j0 + u;
+          if (jj + 1 < r) {
+            if (sv[u] != 0.f) {
+              Zc[jj * zld] = nx[u];
+              cur = cur - mv[u] * nx[u];
+            } else {
+              Zc[jj * zld] = cur;
+              cur = nx[u] - mv[u] * cur;
+            }
+          }
+        }
+      }
+      Zc[(r - 1) * zld] = cur;
+      // back substitution with the upper factor (three diagonals)
+      float z1 = 0.f, z2 = 0.f, mx = 0.f;
+      for (int a1 = r - 1; a1 >= 0; a1 -= 4) {
+        float u0v[4], u1v[4], u2v[4], zv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int a = a1 - u;
+          if (a >= 0) {
+            const size_t o = (size_t)a * r + jv;
+            u0v[u] = LU[o];
+            u1v[u] = LU[pl + o];
+            u2v[u] = LU[2 * pl + o];
+            zv[u] = Zc[a * zld];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int a = a1 - u;
+          if (a >= 0) {
+            const float tv = (zv[u] - u1v[u] * z1 - u2v[u] * z2) * u0v[u];
+            Zc[a * zld] = tv;
+            z2 = z1;
+            z1 = tv;
+            mx = fmaxf(mx, fabsf(tv));
+          }
+        }
+      }
+      // scale first (the solve can grow the vector by 1/tiny)
+      const float inv = (mx > 0.f) ? 1.f / mx : 0.f;
+      for (int a = 0; a < r; ++a) Zc[a * zld] *= inv;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      for (int t = 0; t < m; ++t) {
+        // orthogonalise against the earlier members: blocks of 8 at a time
+        // (independent dot products, then one combined update), two passes
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int q0 = 0; q0 < t; q0 += 8) {
+            const int nq = min(8, t - q0);
+            float dot[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) dot[u] = 0.f;
+            for (int a = lane; a < r; a += 32) {
+              const float zj = Z[a * zld + t];
+              const float* zr = Z + a * zld + q0;
+#pragma unroll
+              for (int u = 0; u < 8; ++u) dot[u] = fmaf(zr[u < nq ? u : 0], zj, dot[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const float sm = warp_sumf(dot[u]);
+              dot[u] = (u < nq) ? sm : 0.f;
+            }
+            for (int a = lane; a < r; a += 32) {
+              float zj = Z[a * zld + t];
+              const float* zr = Z + a * zld + q0;
+#pragma unroll
+              for (int u = 0; u < 8; ++u) zj = fmaf(-dot[u], zr[u < nq ? u : 0], zj);
+              Z[a * zld + t] = zj;
+            }
+            __syncwarp();
+          }
+        }
+        float nrm = 0.f;
+        for (int a = lane; a < r; a += 32) nrm += Z[a * zld + t] * Z[a * zld + t];
+        nrm = warp_sumf(nrm);
+        nrm = (nrm > 0.f) ? rsqrtf(nrm) : 0.f;
+        for (int a = lane; a < r; a += 32) Z[a * zld + t] *= nrm;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  if (insm)
+    for (int q = tid; q < r * m; q += kInvThreads) {
+      const int a = q / m, t = q % m;
+      w.Z32[a * r + c0 + t] = Z[a * zld + t];
+    }
 }
 
 // ------------------------------------- 3b. back-transformation (multi-CTA) ------
@@ -1044,6 +1076,8 @@ DW carve(double* work, int n) {
   w.A32 = reinterpret_cast<float*>(p); p += (nn + n) / 2 + 1;
   w.Z32 = reinterpret_cast<float*>(p); p += nn / 2 + 1;
   w.LU32 = reinterpret_cast<float*>(p); p += (5 * nn + 1) / 2 + 1;
+  w.T3 = reinterpret_cast<float*>(p); p += (3 * (size_t)n + 5) / 2 + 1;
+  w.cls = reinterpret_cast<int*>(p); p += ((size_t)n + 3) / 2 + 1;
   w.perm = reinterpret_cast<int*>(p); p += n / 2 + 1;
   w.order = reinterpret_cast<int*>(p); p += n / 2 + 1;
   w.srt = reinterpret_cast<int*>(p); p += n / 2 + 1;
@@ -1064,7 +1098,7 @@ void gemm(const GemmJob& j0, const GemmJob& j1, int nz, const DW& w, int n, doub
 
 size_t dense_work_doubles(int n) {
   const size_t nn = (size_t)n * n;
-  return 11 * nn + 3 * (size_t)n + 48 + (nn + n) / 2 + 1 + (nn / 2 + 1) + (5 * nn + 1) / 2 + 1 + 4 * ((size_t)n / 2 + 2) + 1 + 16;
+  return 11 * nn + 3 * (size_t)n + 48 + (nn + n) / 2 + 1 + (nn / 2 + 1) + (5 * nn + 1) / 2 + 1 + (3 * (size_t)n + 5) / 2 + 1 + ((size_t)n + 3) / 2 + 1 + 4 * ((size_t)n / 2 + 2) + 1 + 16;
 }
 
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k, double* theta,
@@ -1083,15 +1117,16 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
   check_launch("trsm_kernel");
   trsm_kernel<<<n, 32, 0, s>>>(Ahat, Mhat, n, sigma, 1, w);
   check_launch("trsm_kernel");
-  // 3. FP32 eigensolve (A in shared memory; Z too when both fit)
-  //    (T in shared memory; the eigenvector block too when it fits; the rest of the
-  //    shared memory holds the LU factorisations of the inverse iteration)
-  const size_t a32 = (size_t)n * n * sizeof(float);
-  const bool zs = 2 * a32 <= 210 * 1024;
-  const size_t esm = zs ? 2 * a32 : a32;
+  // 3. FP32 start: tridiagonalisation and eigenvalues (T in shared memory), inverse
+  //    iteration (one CTA per cluster), back-transformation
+  const size_t esm = (size_t)n * n * sizeof(float);
   BMG_CUDA(cudaFuncSetAttribute(eig32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
-  eig32_kernel<<<1, kBig, esm, s>>>(n, zs ? 1 : 0, w);
+  eig32_kernel<<<1, kBig, esm, s>>>(n, w);
   check_launch("eig32_kernel");
+  const size_t ism = sizeof(float) * (size_t)n * (kInvSmemMembers | 1);
+  BMG_CUDA(cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
+  invit_kernel<<<n, kInvThreads, ism, s>>>(n, w);
+  check_launch("invit_kernel");
   backtr_kernel<<<(n + 2 * kBackWarps - 1) / (2 * kBackWarps), kBackWarps * 32, 0, s>>>(n, w);
   check_launch("backtr_kernel");
   // 4. refinement: steps separate pairs farther apart than a floor (relative to
