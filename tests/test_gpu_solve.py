@@ -93,3 +93,36 @@ def test_invalid_arguments_and_nonfinite(gpu_bmg):
     with pytest.raises(gpu_bmg.BmgError) as e:
         prob.solve(X0, 20, 16, 0.0, 1e-10)
     assert e.value.code in (4, 6)                   # singular or non-finite, never a silent answer
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_largest_block_k160(gpu_bmg, precision):
+    """The largest block (k = 160, enriched problems of 42 + 160 = 202): the 120 lowest
+    pairs of the 2562-vertex sphere against dense LAPACK."""
+    v, t = inputs.icosahedron()
+    prob = gpu_bmg.Problem(v, t, 4)
+    prob.hierarchy(4)
+    X0 = inputs.gaussian_block(inputs.n_vertices(2), 160, 31)
+    ev, U, rs, info = prob.solve(X0, 160, 120, 0.0, 1e-9, gpu_bmg.options(precision=precision))
+    assert info.converged == 1
+    H = obmg.build_hierarchy(v, t, 4, colour=False)
+    A, M = H.A[4], H.M[4]
+    w = certify.dense_pencil_eigs(A, M)[0]
+    assert np.max(np.abs(np.sort(ev) - w[:120]) / np.maximum(w[:120], 1)) <= 1e-9
+    assert np.all(obmg.residuals(A, M, U, ev) <= 1e-8)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_single_vector(gpu_bmg, precision):
+    """k = 1, one wanted pair: the constant eigenvector, lambda = 0, M-normalised."""
+    v, t = inputs.icosahedron()
+    prob = gpu_bmg.Problem(v, t, 3)
+    prob.hierarchy(3)
+    X0 = inputs.gaussian_block(inputs.n_vertices(2), 1, 5)
+    ev, U, rs, info = prob.solve(X0, 1, 1, 0.0, 1e-10, gpu_bmg.options(precision=precision))
+    assert info.converged == 1 and ev.shape == (1,)
+    assert abs(ev[0]) <= 1e-10
+    u = U[:, 0]
+    assert np.max(np.abs(u - u.mean())) <= 1e-8 * np.max(np.abs(u))
+    M = obmg.build_hierarchy(v, t, 3, colour=False).M[3]
+    assert abs(u @ (M @ u) - 1.0) <= 1e-12
