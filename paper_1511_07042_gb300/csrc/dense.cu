@@ -84,29 +84,52 @@ __device__ T block_sum(T v, T* red) {
 }
 
 // ------------------------------------------------ 1. basis (pivoted Cholesky) --
-// Symmetric pivoting is done physically on the upper triangle of S (row j holds
-// S[j][j..n)), so every step reads and writes contiguous rows.  The factor is written
-// in pivot order twice, as L (row i holds L[i][0..i]) and as Lt (row q holds column q
-// of L), with the reciprocal pivots 1 / L[q][q] in rl; rows of the part computed so
-// far are swapped with the pivots.  FP64 arithmetic is scarce on this GPU, so the
-// pivot search compares the bit patterns of the (non-negative) diagonal as integers
-// and one thread computes the square root and the reciprocal of each pivot.
+// Symmetric pivoting is done physically: the trailing matrix lives in the upper
+// triangle of S (row a holds S[a][a..n)) and the factor computed so far in the strict
+// lower triangle and the diagonal (L[i][q] at S[i][q], q <= i), so a pivot's row swap
+// moves both.  A step is two block barriers:
+//   warp 0: the pivot (largest remaining diagonal), its root and reciprocal, the
+//           symmetric swap and the new column l_j of L;
+//   all warps: the rank-1 update of the trailing upper triangle, each warp owning
+//           whole rows, and the per-warp candidates for the next pivot from the
+//           updated diagonal of its rows.
+// FP64 arithmetic is scarce on this GPU: the pivot search compares the bit patterns
+// of the (non-negative) diagonal as integers, and the reciprocal root comes from an
+// FP32 seed refined by Newton steps.  The factor is written out once at the end, as L
+// (row i holds L[i][0..i]) and as Lt (row q holds column q of L), with the reciprocal
+// pivots 1 / L[q][q] in rl.
 __device__ __forceinline__ unsigned long long pivot_key(double v) {
   const long long b = __double_as_longlong(v);
   // positive finite values and +inf order like their bit patterns; 0, negatives and
   // NaN get key 0 and are never chosen above a positive value
   return (b > 0 && b <= 0x7FF0000000000000LL) ? (unsigned long long)b : 0ull;
 }
-__global__ void __launch_bounds__(kBig)
+// 1/sqrt(x) for x in the FP32 normal range: FP32 seed (relative error below 1e-6)
+// and two Newton-Raphson steps y <- y (3 - x y^2) / 2 in FP64 (the error squares).
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  return y;
+}
+// the largest key with the smallest index among equal keys, over the warp
+__device__ __forceinline__ void warp_argmax(unsigned long long& best, int& bi) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, best, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (k2 > best || (k2 == best && i2 < bi)) { best = k2; bi = i2; }
+  }
+}
+__global__ void __launch_bounds__(kBig, 1)
 basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS, double drop_tol) {
   extern __shared__ double dsm[];
   double* S = smemS ? dsm : w.S;
   __shared__ unsigned long long wk[32];
   __shared__ int wi[32];
   __shared__ int perm[kMaxN];
-  __shared__ double d[kMaxN], lcol[kMaxN];
-  __shared__ int s_rank, s_p, s_go;
-  __shared__ double s_l, s_rl;
+  __shared__ double d[kMaxN], lcol[kMaxN], rls[kMaxN];
+  __shared__ int s_go;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = kBig / 32;
   for (int i = tid; i < n; i += kBig) {
@@ -116,91 +139,94 @@ basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS, double dro
   }
   __syncthreads();
   for (int i = wid; i < n; i += nwarps)
-    for (int j = lane; j < n; j += 32) {
-      S[i * n + j] = 0.5 * (Mhat[i * n + j] + Mhat[j * n + i]) * (d[i] * d[j]);
-      w.L[i * n + j] = 0.0;
-      w.Lt[i * n + j] = 0.0;
-    }
-  if (tid == 0) s_rank = n;
+    for (int j = lane; j < n; j += 32) S[i * n + j] = 0.5 * (Mhat[i * n + j] + Mhat[j * n + i]) * (d[i] * d[j]);
   __syncthreads();
-  for (int j = 0; j < n; ++j) {
+  // candidates for the first pivot: warp w owns rows w, w + 32, ...
+  {
     unsigned long long best = 0ull;
-    int bi = j;
-    for (int i = j + tid; i < n; i += kBig) {
-      const unsigned long long key = pivot_key(S[i * n + i]);
-      if (key > best) { best = key; bi = i; }
+    int bi = n;
+    for (int a = wid + 32 * lane; a < n; a += 32 * nwarps) {
+      const unsigned long long key = pivot_key(S[a * n + a]);
+      if (key > best || (key == best && a < bi)) { best = key; bi = a; }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, best, o);
-      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (k2 > best || (k2 == best && i2 < bi)) { best = k2; bi = i2; }
-    }
+    warp_argmax(best, bi);
     if (lane == 0) { wk[wid] = best; wi[wid] = bi; }
-    __syncthreads();
+  }
+  __syncthreads();
+  int rank = n;
+  for (int j = 0; j < n; ++j) {
     if (wid == 0) {
-      best = wk[lane];
-      bi = wi[lane];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, best, o);
-        const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (k2 > best || (k2 == best && i2 < bi)) { best = k2; bi = i2; }
-      }
-      if (lane == 0) {
-        const double piv = __longlong_as_double((long long)best);
-        const int go = piv > drop_tol;
-        s_go = go;
-        s_p = bi;
-        if (go) {
-          s_l = sqrt(piv);
-          s_rl = 1.0 / s_l;
-          w.rl[j] = s_rl;
-        } else {
-          s_rank = j;
+      unsigned long long best = wk[lane];
+      int bi = wi[lane];
+      warp_argmax(best, bi);
+      const double piv = __longlong_as_double((long long)best);
+      const int go = piv > drop_tol && bi < n;
+      if (lane == 0) s_go = go;
+      if (go) {
+        const int p = bi;
+        const double rl = rsqrt_nr(piv), l = piv * rl;
+        if (p != j) {
+          // symmetric swap of indices j < p: trailing upper triangle and the rows of L
+          for (int x = lane; x < n; x += 32) {
+            if (x < j) {
+              const double t = S[j * n + x]; S[j * n + x] = S[p * n + x]; S[p * n + x] = t;
+            } else if (x > j && x < p) {
+              const double t = S[j * n + x]; S[j * n + x] = S[x * n + p]; S[x * n + p] = t;
+            } else if (x > p) {
+              const double t = S[j * n + x]; S[j * n + x] = S[p * n + x]; S[p * n + x] = t;
+            } else if (x == j) {
+              const double t = S[j * n + j]; S[j * n + j] = S[p * n + p]; S[p * n + p] = t;
+            }
+          }
+          if (lane == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
+          __syncwarp();
         }
+        // column j of L: L[i][j] = S[j][i] / L[j][j] below the diagonal, L[j][j] on it
+        for (int i = j + 1 + lane; i < n; i += 32) {
+          const double v = S[j * n + i] * rl;
+          lcol[i] = v;
+          S[i * n + j] = v;
+        }
+        if (lane == 0) { S[j * n + j] = l; rls[j] = rl; }
       }
     }
     __syncthreads();
-    if (!s_go) break;
-    const int p = s_p;
-    if (p != j) {
-      // symmetric swap of indices j < p in upper-triangle storage
-      for (int x = tid; x < n; x += kBig) {
-        if (x < j) {
-          const double t = S[x * n + j]; S[x * n + j] = S[x * n + p]; S[x * n + p] = t;
-        } else if (x > j && x < p) {
-          const double t = S[j * n + x]; S[j * n + x] = S[x * n + p]; S[x * n + p] = t;
-        } else if (x > p) {
-          const double t = S[j * n + x]; S[j * n + x] = S[p * n + x]; S[p * n + x] = t;
-        } else if (x == j) {
-          const double t = S[j * n + j]; S[j * n + j] = S[p * n + p]; S[p * n + p] = t;
-        }
-        if (x < j) {   // rows j and p of the factor computed so far
-          const double t = w.L[j * n + x]; w.L[j * n + x] = w.L[p * n + x]; w.L[p * n + x] = t;
-          const double u = w.Lt[x * n + j]; w.Lt[x * n + j] = w.Lt[x * n + p]; w.Lt[x * n + p] = u;
-        }
-      }
-      if (tid == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
-    }
-    __syncthreads();
-    const double ljj = s_l, rl = s_rl;
-    for (int i = j + tid; i < n; i += kBig) {
-      const double v = (i == j) ? ljj : S[j * n + i] * rl;
-      lcol[i] = v;
-      w.L[i * n + j] = v;
-      w.Lt[j * n + i] = v;
-    }
-    __syncthreads();
-    for (int a = j + 1 + wid; a < n; a += nwarps) {   // upper triangle of the trailing block
+    if (!s_go) { rank = j; break; }
+    // rank-1 update of the trailing upper triangle; warp w owns rows j+1+w, j+1+w+32, ...
+    unsigned long long best = 0ull;
+    int bi = n;
+    for (int a = j + 1 + wid; a < n; a += nwarps) {
       const double la = lcol[a];
       double* Sa = S + a * n;
-      for (int b = a + lane; b < n; b += 32) Sa[b] -= la * lcol[b];
+      for (int b = a + lane; b < n; b += 32) Sa[b] = fma(-la, lcol[b], Sa[b]);
     }
+    __syncwarp();
+    for (int a = j + 1 + wid + 32 * lane; a < n; a += 32 * nwarps) {
+      const unsigned long long key = pivot_key(S[a * n + a]);
+      if (key > best || (key == best && a < bi)) { best = key; bi = a; }
+    }
+    warp_argmax(best, bi);
+    if (lane == 0) { wk[wid] = best; wi[wid] = bi; }
     __syncthreads();
   }
-  for (int i = tid; i < n; i += kBig) { w.perm[i] = perm[i]; w.d[i] = d[i]; }
-  if (tid == 0) *w.rank = s_rank;
+  // write the factor: L (lower, rows in pivot order) and Lt, zero outside the first
+  // rank columns and above the diagonal
+  for (int i = wid; i < n; i += nwarps)
+    for (int q = lane; q < n; q += 32) {
+      const double v = (q <= i && q < rank) ? S[i * n + q] : 0.0;
+      w.L[i * n + q] = v;
+    }
+  for (int q = wid; q < n; q += nwarps)
+    for (int i = lane; i < n; i += 32) {
+      const double v = (q <= i && q < rank) ? S[i * n + q] : 0.0;
+      w.Lt[q * n + i] = v;
+    }
+  for (int i = tid; i < n; i += kBig) {
+    w.perm[i] = perm[i];
+    w.d[i] = d[i];
+    if (i < rank) w.rl[i] = rls[i];
+  }
+  if (tid == 0) *w.rank = rank;
 }
 
 // ---------------------------------------- 2. T = L^{-1} C L^{-T} (FP64, warps) --
@@ -294,8 +320,19 @@ eig32_kernel(int n, DW w) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = kBig / 32;
   float* A = fsm;                                   // r x r
-  for (int i = wid; i < r; i += nwarps)
-    for (int j = lane; j < r; j += 32) A[i * r + j] = (float)(0.5 * (w.T[i * n + j] + w.T[j * n + i]));
+  // T is symmetric in exact arithmetic; its two triangular solves leave rounding
+  // asymmetry.  Symmetrise it in place (each pair i <= j by one thread) for the FP64
+  // refinement, whose symmetric products assume it, and take its FP32 copy.
+  for (int q = tid; q < r * r; q += kBig) {
+    const int i = q / r, j = q - (q / r) * r;
+    if (i <= j) {
+      const double v = 0.5 * (w.T[i * n + j] + w.T[j * n + i]);
+      w.T[i * n + j] = v;
+      w.T[j * n + i] = v;
+      A[i * r + j] = (float)v;
+      A[j * r + i] = (float)v;
+    }
+  }
   __syncthreads();
   // --- Householder tridiagonalisation, v_j stored in column j below the subdiagonal.
   // The squared norm of the next column below its subdiagonal is summed per warp
@@ -310,8 +347,7 @@ eig32_kernel(int n, DW w) {
       for (int i = j + 2 + tid; i < r; i += kBig) part += A[i * r + j] * A[i * r + j];
       xn2 = block_sum<float>(part, redf);
     } else {
-      xn2 = 0.f;
-      for (int q = 0; q < nwarps; ++q) xn2 += colsq[j & 1][q];
+      xn2 = warp_sumf(colsq[j & 1][lane]);   // nwarps == 32 partial sums
     }
     float beta = a0, t = 0.f, scale = 0.f;
     if (xn2 > 0.f) {
@@ -328,12 +364,19 @@ eig32_kernel(int n, DW w) {
     if (tid == 0) { d[j] = A[j * r + j]; e[j] = beta; tau[j] = t; }
     __syncthreads();
     if (t != 0.f) {
-      for (int a = wid; a < m; a += nwarps) {        // p = t A22 v
-        const float* Ar = A + (j + 1 + a) * r + (j + 1);
+      // p = t A22 v: 8 lanes per row, 4 rows per warp (the row loop is uniform over
+      // the warp, so every lane reaches the shuffles)
+      for (int a0 = 4 * wid; a0 < m; a0 += 4 * nwarps) {
+        const int a = a0 + (lane >> 3);
         float s = 0.f;
-        for (int b = lane; b < m; b += 32) s += Ar[b] * vb[b];
-        s = warp_sumf(s);
-        if (lane == 0) pv[a] = t * s;
+        if (a < m) {
+          const float* Ar = A + (j + 1 + a) * r + (j + 1);
+          for (int b = lane & 7; b < m; b += 8) s = fmaf(Ar[b], vb[b], s);
+        }
+        s += __shfl_xor_sync(0xffffffffu, s, 1);
+        s += __shfl_xor_sync(0xffffffffu, s, 2);
+        s += __shfl_xor_sync(0xffffffffu, s, 4);
+        if ((lane & 7) == 0 && a < m) pv[a] = t * s;
       }
       __syncthreads();
       float kk = 0.f;                                 // K = (t/2) p.v, per warp
@@ -718,6 +761,8 @@ backtr_kernel(int n, DW w) {
 //   acc_mode 2 (the S product): store lam_i = s_ii / (2 - g_ii), accumulate
 //   ||S - diag(lam)||_F^2 into acc[0] and max |lam| into acc[2] (as the bits of a
 //   non-negative double).
+//   Both accumulating products are symmetric (W^T W and W^T T W): only the tiles on
+//   and above the diagonal are formed, each written to both halves.
 struct GemmJob {
   const double* A; const double* B; double* C; const double* D;
   int ta, bmode, addD, acc_mode;
@@ -731,6 +776,7 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
   extern __shared__ double gsm[];
   __shared__ double red[2][2];
   const GemmJob jb = blockIdx.z == 0 ? j0 : j1;
+  if (jb.acc_mode && blockIdx.y > blockIdx.x) return;
   const int r = *w.rank;
   const int row0 = blockIdx.y * kTile, col0 = blockIdx.x * kTile;
   if (row0 >= r || col0 >= r) return;
@@ -760,6 +806,7 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
       } else if (jb.bmode == 2) {
         v = w.E[kq * n + col];
       } else {
+        // G and S hold both halves; averaging them keeps E_ij + E_ji = r_ij exact
         const double gs = 0.5 * (w.G[kq * n + col] + w.G[col * n + kq]);
         const double rij = (kq == col ? 1.0 : 0.0) - gs;
         v = 0.5 * rij;
@@ -782,6 +829,8 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
   for (int kq = 0; kq < r; ++kq) a_acc = fma(As[ty * r + kq], Bs[kq * kTile + tx], a_acc);
   const bool in = row < r && col < r;
   if (in) jb.C[row * n + col] = jb.addD ? jb.D[row * n + col] + a_acc : a_acc;
+  const bool offdiag = blockIdx.y != blockIdx.x;
+  if (in && jb.acc_mode && offdiag) jb.C[col * n + row] = a_acc;
   if (jb.acc_mode) {
     double c0 = 0.0, c1 = 0.0;
     if (in) {
@@ -805,7 +854,9 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
     if ((tid & 31) == 0) { red[tid >> 5][0] = c0; red[tid >> 5][1] = c1; }
     __syncthreads();
     if (tid == 0) {
-      const double s0 = red[0][0] + red[1][0], s1 = fmax(red[0][1], red[1][1]);
+      double s0 = red[0][0] + red[1][0];
+      const double s1 = fmax(red[0][1], red[1][1]);
+      if (offdiag) s0 *= 2.0;   // the mirrored tile
       if (jb.acc_mode == 1) {
         atomicAdd(acc + 1, s0);
       } else {
@@ -816,37 +867,64 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
   }
 }
 
+// Unsigned key with the order of the (finite) doubles: negative values' bits inverted,
+// the sign bit of non-negative ones set.
+__device__ __forceinline__ unsigned long long order_key(double v) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
 // Cluster formation for a cluster step: lam (Rayleigh quotients) sorted, chains of
-// gaps <= the threshold, E initialised to diag(r_ii / 2).
+// gaps <= the threshold, E initialised to diag(r_ii / 2).  The sort is by rank
+// counting in shared memory; the cluster starts are the sorted positions whose gap
+// to the previous value exceeds the threshold, numbered by a prefix count in warp 0.
 __global__ void __launch_bounds__(kBig)
 coeff_kernel(int n, const double* acc, double floor_rel, DW w) {
-  __shared__ double sl[kMaxN];
+  __shared__ double sl[kMaxN], ss[kMaxN];
+  __shared__ int srt[kMaxN];
+  __shared__ double s_thr;
   const int r = *w.rank;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = kBig / 32;
-  const double thr = thr_from(acc, floor_rel);
+  if (tid == 0) s_thr = thr_from(acc, floor_rel);
   for (int i = tid; i < r; i += kBig) sl[i] = w.lam[i];
   for (int i = wid; i < r; i += nwarps)
     for (int j = lane; j < r; j += 32) w.E[i * n + j] = (i == j) ? 0.5 * (1.0 - w.G[i * n + i]) : 0.0;
   __syncthreads();
   for (int i = tid; i < r; i += kBig) {
-    const double li = sl[i];
+    // FP64 compares run on the scarce FP64 pipe: rank by order-preserving integer keys
+    const unsigned long long ki = order_key(sl[i]);
     int rk = 0;
     for (int j = 0; j < r; ++j) {
-      const double lj = sl[j];
-      rk += (lj < li || (lj == li && j < i)) ? 1 : 0;
+      const unsigned long long kj = order_key(sl[j]);
+      rk += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
     }
-    w.srt[rk] = i;
+    srt[rk] = i;
+    ss[rk] = sl[i];
   }
   __syncthreads();
-  if (tid == 0) {
-    int nc = 0;
-    w.cl[1] = 0;
-    for (int t = 1; t < r; ++t)
-      if (!(sl[w.srt[t]] - sl[w.srt[t - 1]] <= thr)) w.cl[1 + (++nc)] = t;
-    ++nc;
-    w.cl[1 + nc] = r;
-    w.cl[0] = nc;
+  for (int t = tid; t < r; t += kBig) w.srt[t] = srt[t];
+  if (wid == 0) {
+    // lane l scans sorted positions [l * per, (l + 1) * per)
+    const double thr = s_thr;
+    const int per = (r + 31) / 32;
+    const int t0 = lane * per, t1 = min(r, t0 + per);
+    int cnt = 0;
+    for (int t = max(t0, 1); t < t1; ++t) cnt += !(ss[t] - ss[t - 1] <= thr);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    int c = incl - cnt;   // starts before this lane's range
+    for (int t = max(t0, 1); t < t1; ++t)
+      if (!(ss[t] - ss[t - 1] <= thr)) w.cl[1 + (++c)] = t;
+    if (lane == 31) {
+      const int nc = incl + 1;
+      w.cl[1] = 0;
+      w.cl[1 + nc] = r;
+      w.cl[0] = nc;
+    }
   }
 }
 
@@ -983,12 +1061,20 @@ __global__ void select_kernel(int k, int n, const double* acc, DW w, double* __r
     w.misc[1] = (amax > 0.0) ? sqrt(acc[0]) / amax + sqrt(acc[1]) : sqrt(acc[1]);
   }
   __syncthreads();
+  // order by (|lam|, lam, index) through integer keys: the magnitude's bits, then a
+  // bit that puts a negative value before a positive one of the same magnitude
+  __shared__ unsigned long long key[kMaxN];
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
-    const double li = w.lam[i];
+    const unsigned long long b = (unsigned long long)__double_as_longlong(w.lam[i]);
+    key[i] = ((b & 0x7FFFFFFFFFFFFFFFull) << 1) | ((b >> 63) ^ 1ull);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    const unsigned long long ki = key[i];
     int rk = 0;
     for (int j = 0; j < r; ++j) {
-      const double lj = w.lam[j];
-      rk += (fabs(lj) < fabs(li) || (fabs(lj) == fabs(li) && (lj < li || (lj == li && j < i)))) ? 1 : 0;
+      const unsigned long long kj = key[j];
+      rk += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
     }
     if (rk < k) w.order[rk] = i;
   }
