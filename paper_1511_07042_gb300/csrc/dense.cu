@@ -10,7 +10,7 @@
 //      which are dropped (rank r).
 //   2. trsm_kernel     [multi-CTA, FP64]  reduced standard matrix
 //      T = L^{-1} D P^T (Ahat - sigma Mhat) P D L^{-T}: two forward substitutions, one
-//      warp per column, the column kept in shared memory.
+//      warp per column, L staged in shared memory.
 //   3. eig32_kernel    [1 CTA, FP32]  Householder tridiagonalisation of T, bisection
 //      on Sturm counts for all eigenvalues, inverse iteration (with modified
 //      Gram-Schmidt inside clusters of close eigenvalues) for the eigenvectors, and
@@ -20,6 +20,8 @@
 //          G = W^T W, R = I - G, S = W^T T W, lt_i = s_ii / (1 - r_ii),
 //          E_ij = (s_ij + lt_j r_ij) / (lt_j - lt_i) for well separated pairs,
 //          r_ij / 2 otherwise,   W <- W (I + E);
+//      P = T W is carried along as P <- P (I + E), so a step is three launches (E,
+//      the two updates, G and S);
 //      clusters of nearly equal values are diagonalised exactly (FP64 Jacobi on the
 //      cluster block, one CTA per cluster) once the separated pairs converged.
 //   5. select / backsub  the k smallest |theta|; Y = D P L^{-T} W_sel.
@@ -230,24 +232,43 @@ basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS, double dro
 }
 
 // ---------------------------------------- 2. T = L^{-1} C L^{-T} (FP64, warps) --
-// Forward substitution, one warp (and one CTA, to spread the FP64 work over the SMs)
-// per right-hand side c; lane l keeps the running values of rows l, l + 32, ... in
-// registers and, once z_i is known, subtracts column i of L (a contiguous row of Lt)
-// times z_i from them.
+// Forward substitution, one warp per right-hand side c and kTriWarps columns per CTA.
+// The CTA first stages the strict lower triangle of L in shared memory, packed by
+// columns and each column pre-scaled by its reciprocal pivot (Ls[i][q] = L[q][i] /
+// L[i][i]), so that a step is: broadcast the unscaled running value of row i, and
+// subtract Ls[i][q] times it from the rows q > i.  Lane l keeps rows l, l + 32, ...
+// in NS register slots; slots below i / 32 are finished and skipped.  z_i = value_i /
+// L[i][i] is formed at the end.  Each FP64 instruction costs a warp tens of cycles on
+// this GPU, so a step issues only the FP64 updates of the live slots.
 // pass 0: Z = L^{-1} C, C[i][c] = d_a sym(Ahat - sigma Mhat)_ab d_b with a = perm[i],
 // b = perm[c];  pass 1: T = L^{-1} Z^T.
 constexpr int kRowsPerLane = kMaxDense / 32;   // rows per lane for rank <= 224
-__global__ void __launch_bounds__(32)
+constexpr int kTriWarps = 4;
+__host__ __device__ inline size_t tri_smem_bytes(int n) {
+  return sizeof(double) * ((size_t)n * (n - 1) / 2 + (size_t)kTriWarps * n);
+}
+__device__ __forceinline__ int col_off(int i, int r) { return i * r - i * (i + 1) / 2; }
+template <int NS>
+__global__ void __launch_bounds__(kTriWarps * 32)
 trsm_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mhat, int n, double sigma,
             int pass, DW w) {
+  extern __shared__ double tsm[];
   const int r = *w.rank;
-  const int lane = threadIdx.x;
-  const int c = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double* Ls = tsm;                                    // packed columns, r (r - 1) / 2
+  double* zs = tsm + (size_t)n * (n - 1) / 2 + (size_t)wid * n;
+  for (int i = wid; i < r; i += kTriWarps) {
+    const double rli = w.rl[i];
+    const int o = col_off(i, r) - i - 1;   // Ls[o + q] for q > i
+    for (int q = i + 1 + lane; q < r; q += 32) Ls[o + q] = w.Lt[i * n + q] * rli;
+  }
+  __syncthreads();
+  const int c = blockIdx.x * kTriWarps + wid;
   if (c >= r) return;
-  double acc[kRowsPerLane];
+  double acc[NS];
   const int* perm = w.perm;
 #pragma unroll
-  for (int t = 0; t < kRowsPerLane; ++t) {
+  for (int t = 0; t < NS; ++t) {
     const int q = lane + 32 * t;
     double v = 0.0;
     if (q < r) {
@@ -262,37 +283,27 @@ trsm_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mhat, in
     }
     acc[t] = v;
   }
-  // column i + 1 of L and its reciprocal pivot are loaded one step ahead
-  double lc[kRowsPerLane], lcn[kRowsPerLane], rli = 0.0, rln = w.rl[0];
-  auto load_col = [&](int i) {
-#pragma unroll
-    for (int t = 0; t < kRowsPerLane; ++t) {
-      const int q = lane + 32 * t;
-      lcn[t] = (i < r && q > i && q < r) ? w.Lt[i * n + q] : 0.0;
-    }
-  };
-  load_col(0);
   for (int i = 0; i < r; ++i) {
+    const int ti = i >> 5;
+    double a = acc[0];
 #pragma unroll
-    for (int t = 0; t < kRowsPerLane; ++t) lc[t] = lcn[t];
-    rli = rln;
-    load_col(i + 1);
-    if (i + 1 < r) rln = w.rl[i + 1];
-    const int ti = i >> 5, own = i & 31;
-    double zi = 0.0;
+    for (int t = 1; t < NS; ++t)
+      if (ti == t) a = acc[t];
+    a = __shfl_sync(0xffffffffu, a, i & 31);
+    if (lane == 0) zs[i] = a;
+    const int o = col_off(i, r) - i - 1;   // Ls[o + q] for q > i
 #pragma unroll
-    for (int t = 0; t < kRowsPerLane; ++t)
-      if (t == ti && lane == own) { acc[t] *= rli; zi = acc[t]; }
-    zi = __shfl_sync(0xffffffffu, zi, own);
-#pragma unroll
-    for (int t = 0; t < kRowsPerLane; ++t) acc[t] = fma(-lc[t], zi, acc[t]);
+    for (int t = 0; t < NS; ++t) {
+      if (t >= ti) {
+        const int q = lane + 32 * t;
+        const double l = (q > i && q < r) ? Ls[o + q] : 0.0;
+        acc[t] = fma(-l, a, acc[t]);
+      }
+    }
   }
+  __syncwarp();
   double* out = pass == 0 ? w.Z : w.T;
-#pragma unroll
-  for (int t = 0; t < kRowsPerLane; ++t) {
-    const int q = lane + 32 * t;
-    if (q < r) out[q * n + c] = acc[t];
-  }
+  for (int q = lane; q < r; q += 32) out[q * n + c] = zs[q] * w.rl[q];
 }
 
 // ---------------------------------------------- 3. FP32 eigensolve (1 CTA) -----
@@ -754,9 +765,7 @@ backtr_kernel(int n, DW w) {
 // ------------------------------------------------ 4. refinement (FP64) ---------
 // Products of r x r matrices (stride n) with kTile x kTile output tiles; the A row
 // panel and the B column panel are staged whole in shared memory.
-//   bmode 0: B read from memory;  1: B = E computed on the fly (Ogita-Aishima step;
-//   lam_i = s_ii / (2 - g_ii) and the threshold from the accumulated norms);
-//   2: B = E read from memory (cluster step).  With addD: C = D + op(A) B.
+//   bmode 0: B read from memory;  2: B = E read from memory.  With addD: C = D + op(A) B.
 //   acc_mode 1 (the G product): accumulate ||I - G||_F^2 into acc[1];
 //   acc_mode 2 (the S product): store lam_i = s_ii / (2 - g_ii), accumulate
 //   ||S - diag(lam)||_F^2 into acc[0] and max |lam| into acc[2] (as the bits of a
@@ -772,7 +781,7 @@ __device__ __forceinline__ double thr_from(const double* acc, double floor_rel) 
   return fmax(2.0 * (sqrt(acc[0]) + amax * sqrt(acc[1])), floor_rel * amax);
 }
 __global__ void __launch_bounds__(kTile * kTile)
-gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) {
+gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc) {
   extern __shared__ double gsm[];
   __shared__ double red[2][2];
   const GemmJob jb = blockIdx.z == 0 ? j0 : j1;
@@ -789,38 +798,12 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
     const int row = row0 + a;
     As[q] = (row < r) ? (jb.ta ? jb.A[kq * n + row] : jb.A[row * n + kq]) : 0.0;
   }
-  __shared__ double s_thr;
-  if (jb.bmode == 1) {
-    if (tid == 0) s_thr = thr_from(acc, floor_rel);
-    __syncthreads();
-  }
-  const double thr = (jb.bmode == 1) ? s_thr : 0.0;
+  const double* B = jb.bmode == 2 ? w.E : jb.B;
 #pragma unroll 4
   for (int q = tid; q < r * kTile; q += kTile * kTile) {
     const int kq = q / kTile, b = q % kTile;
     const int col = col0 + b;
-    double v = 0.0;
-    if (col < r) {
-      if (jb.bmode == 0) {
-        v = jb.B[kq * n + col];
-      } else if (jb.bmode == 2) {
-        v = w.E[kq * n + col];
-      } else {
-        // G and S hold both halves; averaging them keeps E_ij + E_ji = r_ij exact
-        const double gs = 0.5 * (w.G[kq * n + col] + w.G[col * n + kq]);
-        const double rij = (kq == col ? 1.0 : 0.0) - gs;
-        v = 0.5 * rij;
-        if (kq != col) {
-          const double li = w.lam[kq], lj = w.lam[col];
-          if (fabs(li - lj) > thr) {
-            const double ss = 0.5 * (w.SS[kq * n + col] + w.SS[col * n + kq]);
-            const double t = fma(lj, rij, ss) * rcp_nr(lj - li);
-            if (fabs(t) < kGuard) v = t;
-          }
-        }
-      }
-    }
-    Bs[q] = v;
+    Bs[q] = (col < r) ? B[kq * n + col] : 0.0;
   }
   __syncthreads();
   const int ty = tid / kTile, tx = tid % kTile;
@@ -838,7 +821,11 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
         const double rij = (row == col ? 1.0 : 0.0) - a_acc;
         c0 = rij * rij;
       } else if (row == col) {
-        const double lam = a_acc / (2.0 - w.G[row * n + row]);
+        // g_ii from the A panel (W^T rows), in the order of the G product, so that
+        // G and S can be formed in one launch
+        double gii = 0.0;
+        for (int kq = 0; kq < r; ++kq) gii = fma(As[ty * r + kq], As[ty * r + kq], gii);
+        const double lam = a_acc / (2.0 - gii);
         w.lam[row] = lam;
         c0 = (a_acc - lam) * (a_acc - lam);
         c1 = fabs(lam);
@@ -865,6 +852,34 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc, double floor_rel) 
       }
     }
   }
+}
+
+// E of an Ogita-Aishima step, once per step (the products then read it): with
+// r_ij = delta_ij - g_ij and the threshold from the accumulated norms,
+// E_ij = (s_ij + lam_j r_ij) / (lam_j - lam_i) for pairs farther apart than the
+// threshold (if below the guard), r_ij / 2 otherwise.  One thread per entry.
+__global__ void __launch_bounds__(256)
+e_kernel(int n, const double* acc, double floor_rel, DW w) {
+  __shared__ double s_thr;
+  const int r = *w.rank;
+  if (threadIdx.x == 0) s_thr = thr_from(acc, floor_rel);
+  __syncthreads();
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= r * r) return;
+  const int i = q / r, j = q - (q / r) * r;
+  // G and S hold both halves; averaging them keeps E_ij + E_ji = r_ij exact
+  const double gs = 0.5 * (w.G[i * n + j] + w.G[j * n + i]);
+  const double rij = (i == j ? 1.0 : 0.0) - gs;
+  double v = 0.5 * rij;
+  if (i != j) {
+    const double li = w.lam[i], lj = w.lam[j];
+    if (fabs(li - lj) > s_thr) {
+      const double ss = 0.5 * (w.SS[i * n + j] + w.SS[j * n + i]);
+      const double t = fma(lj, rij, ss) * rcp_nr(lj - li);
+      if (fabs(t) < kGuard) v = t;
+    }
+  }
+  w.E[i * n + j] = v;
 }
 
 // Unsigned key with the order of the (finite) doubles: negative values' bits inverted,
@@ -1082,56 +1097,59 @@ __global__ void select_kernel(int k, int n, const double* acc, DW w, double* __r
   for (int c = threadIdx.x; c < k; c += blockDim.x) theta[c] = w.lam[w.order[c]];
 }
 
-// z = L^{-T} w_sel by back substitution (one warp and one CTA per selected column;
-// lane l keeps rows l, l + 32, ...; once z_i is known, row i of L times z_i is
-// subtracted from the rows above), then Y[perm[i]][c] = d[perm[i]] z[i] for i < r and
-// 0 for the dropped rows.
-__global__ void __launch_bounds__(32)
+// z = L^{-T} w_sel by back substitution, one warp per selected column and kTriWarps
+// columns per CTA: the strict lower triangle of L is staged in shared memory packed
+// by rows, each row pre-scaled by its reciprocal pivot (Lr[i][q] = L[i][q] / L[i][i]);
+// from i = r - 1 down, the unscaled running value of row i is broadcast and Lr[i][q]
+// times it subtracted from the rows q < i (lane l keeps rows l, l + 32, ...; slots
+// above i / 32 are finished).  Then Y[perm[i]][c] = d[perm[i]] value_i / L[i][i] for
+// i < r and 0 for the dropped rows.
+template <int NS>
+__global__ void __launch_bounds__(kTriWarps * 32)
 backsub_kernel(int n, int k, DW w, double* __restrict__ Y) {
+  extern __shared__ double tsm[];
   const int r = *w.rank;
-  const int lane = threadIdx.x;
-  const int c = blockIdx.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double* Lr = tsm;                                    // packed rows, r (r - 1) / 2
+  double* zs = tsm + (size_t)n * (n - 1) / 2 + (size_t)wid * n;
+  for (int i = 1 + wid; i < r; i += kTriWarps) {
+    const double rli = w.rl[i];
+    double* dst = Lr + i * (i - 1) / 2;
+    for (int q = lane; q < i; q += 32) dst[q] = w.L[i * n + q] * rli;
+  }
+  __syncthreads();
+  const int c = blockIdx.x * kTriWarps + wid;
   if (c >= k) return;
   const int oc = w.order[c];
-  double acc[kRowsPerLane];
+  double acc[NS];
 #pragma unroll
-  for (int t = 0; t < kRowsPerLane; ++t) {
+  for (int t = 0; t < NS; ++t) {
     const int q = lane + 32 * t;
     acc[t] = (q < r) ? w.W[q * n + oc] : 0.0;
   }
-  // row i - 1 of L and its reciprocal pivot are loaded one step ahead
-  double li[kRowsPerLane], lin[kRowsPerLane], rli = 0.0, rln = (r > 0) ? w.rl[r - 1] : 0.0;
-  auto load_row = [&](int i) {
-#pragma unroll
-    for (int t = 0; t < kRowsPerLane; ++t) {
-      const int q = lane + 32 * t;
-      lin[t] = (i >= 0 && q < i) ? w.L[i * n + q] : 0.0;
-    }
-  };
-  load_row(r - 1);
   for (int i = r - 1; i >= 0; --i) {
+    const int ti = i >> 5;
+    double a = acc[0];
 #pragma unroll
-    for (int t = 0; t < kRowsPerLane; ++t) li[t] = lin[t];
-    rli = rln;
-    load_row(i - 1);
-    if (i > 0) rln = w.rl[i - 1];
-    const int ti = i >> 5, own = i & 31;
-    double zi = 0.0;
+    for (int t = 1; t < NS; ++t)
+      if (ti == t) a = acc[t];
+    a = __shfl_sync(0xffffffffu, a, i & 31);
+    if (lane == 0) zs[i] = a;
+    const double* li = Lr + i * (i - 1) / 2;        // li[q] for q < i
 #pragma unroll
-    for (int t = 0; t < kRowsPerLane; ++t)
-      if (t == ti && lane == own) { acc[t] *= rli; zi = acc[t]; }
-    zi = __shfl_sync(0xffffffffu, zi, own);
-#pragma unroll
-    for (int t = 0; t < kRowsPerLane; ++t) acc[t] = fma(-li[t], zi, acc[t]);
-  }
-  const int* perm = w.perm;
-#pragma unroll
-  for (int t = 0; t < kRowsPerLane; ++t) {
-    const int i = lane + 32 * t;
-    if (i < n) {
-      const int row = perm[i];
-      Y[row * k + c] = (i < r) ? w.d[row] * acc[t] : 0.0;
+    for (int t = 0; t < NS; ++t) {
+      if (t <= ti) {
+        const int q = lane + 32 * t;
+        const double l = (q < i) ? li[q] : 0.0;
+        acc[t] = fma(-l, a, acc[t]);
+      }
     }
+  }
+  __syncwarp();
+  const int* perm = w.perm;
+  for (int i = lane; i < n; i += 32) {
+    const int row = perm[i];
+    Y[row * k + c] = (i < r) ? w.d[row] * (zs[i] * w.rl[i]) : 0.0;
   }
 }
 
@@ -1172,12 +1190,49 @@ DW carve(double* work, int n) {
   return w;
 }
 
-void gemm(const GemmJob& j0, const GemmJob& j1, int nz, const DW& w, int n, double* acc, double floor_rel,
-          cudaStream_t s) {
+void gemm(const GemmJob& j0, const GemmJob& j1, int nz, const DW& w, int n, double* acc, cudaStream_t s) {
   dim3 grid((n + kTile - 1) / kTile, (n + kTile - 1) / kTile, nz);
   const size_t smem = 2 * (size_t)kTile * n * sizeof(double);
-  gemm_kernel<<<grid, kTile * kTile, smem, s>>>(j0, j1, n, w, acc, floor_rel);
+  gemm_kernel<<<grid, kTile * kTile, smem, s>>>(j0, j1, n, w, acc);
   check_launch("gemm_kernel");
+}
+
+// Triangular-solve launches: NS = ceil(n / 32) register slots per lane.
+template <int NS>
+void trsm_ns(const double* Ahat, const double* Mhat, int n, double sigma, int pass, const DW& w, cudaStream_t s) {
+  const size_t sm = tri_smem_bytes(n);
+  BMG_CUDA(cudaFuncSetAttribute(trsm_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  trsm_kernel<NS><<<(n + kTriWarps - 1) / kTriWarps, kTriWarps * 32, sm, s>>>(Ahat, Mhat, n, sigma, pass, w);
+  check_launch("trsm_kernel");
+}
+template <int NS>
+void backsub_ns(int n, int k, const DW& w, double* Y, cudaStream_t s) {
+  const size_t sm = tri_smem_bytes(n);
+  BMG_CUDA(cudaFuncSetAttribute(backsub_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  backsub_kernel<NS><<<(k + kTriWarps - 1) / kTriWarps, kTriWarps * 32, sm, s>>>(n, k, w, Y);
+  check_launch("backsub_kernel");
+}
+void trsm(const double* Ahat, const double* Mhat, int n, double sigma, int pass, const DW& w, cudaStream_t s) {
+  switch ((n + 31) / 32) {
+    case 1: trsm_ns<1>(Ahat, Mhat, n, sigma, pass, w, s); break;
+    case 2: trsm_ns<2>(Ahat, Mhat, n, sigma, pass, w, s); break;
+    case 3: trsm_ns<3>(Ahat, Mhat, n, sigma, pass, w, s); break;
+    case 4: trsm_ns<4>(Ahat, Mhat, n, sigma, pass, w, s); break;
+    case 5: trsm_ns<5>(Ahat, Mhat, n, sigma, pass, w, s); break;
+    case 6: trsm_ns<6>(Ahat, Mhat, n, sigma, pass, w, s); break;
+    default: trsm_ns<kRowsPerLane>(Ahat, Mhat, n, sigma, pass, w, s); break;
+  }
+}
+void backsub(int n, int k, const DW& w, double* Y, cudaStream_t s) {
+  switch ((n + 31) / 32) {
+    case 1: backsub_ns<1>(n, k, w, Y, s); break;
+    case 2: backsub_ns<2>(n, k, w, Y, s); break;
+    case 3: backsub_ns<3>(n, k, w, Y, s); break;
+    case 4: backsub_ns<4>(n, k, w, Y, s); break;
+    case 5: backsub_ns<5>(n, k, w, Y, s); break;
+    case 6: backsub_ns<6>(n, k, w, Y, s); break;
+    default: backsub_ns<kRowsPerLane>(n, k, w, Y, s); break;
+  }
 }
 
 }  // namespace
@@ -1199,10 +1254,8 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
   basis_kernel<<<1, kBig, useS ? smemS : 0, s>>>(Mhat, n, w, useS ? 1 : 0, drop_tol);
   check_launch("basis_kernel");
   // 2. reduced standard matrix
-  trsm_kernel<<<n, 32, 0, s>>>(Ahat, Mhat, n, sigma, 0, w);
-  check_launch("trsm_kernel");
-  trsm_kernel<<<n, 32, 0, s>>>(Ahat, Mhat, n, sigma, 1, w);
-  check_launch("trsm_kernel");
+  trsm(Ahat, Mhat, n, sigma, 0, w, s);
+  trsm(Ahat, Mhat, n, sigma, 1, w, s);
   // 3. FP32 start: tridiagonalisation and eigenvalues (T in shared memory), inverse
   //    iteration (one CTA per cluster), back-transformation
   const size_t esm = (size_t)n * n * sizeof(float);
@@ -1228,27 +1281,31 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
   const double floors[nsteps] = {kClusterFloor, kClusterFloor, kClusterFloor, 1e-7, 1e-7, 1e-7, 1e-10};
   double* accs = w.misc + 8;   // 3 doubles per step
   BMG_CUDA(cudaMemsetAsync(accs, 0, sizeof(double) * 3 * (nsteps + 1), s));
-  for (int it = 0; it <= nsteps; ++it) {
+  // W_0: P = T W, G = W^T W, then S = W^T P.  Each step: E, then W <- W + W E with
+  // P <- P + P E (T W + T W E, so T is not applied again), then G and S together.
+  gemm({w.T, w.W, w.P, nullptr, 0, 0, 0, 0}, {w.W, w.W, w.G, nullptr, 1, 0, 0, 1}, 2, w, n, accs, s);
+  gemm({w.W, w.P, w.SS, nullptr, 1, 0, 0, 2}, {}, 1, w, n, accs, s);
+  for (int it = 0; it < nsteps; ++it) {
     double* acc = accs + 3 * it;
-    // P = T W and G = W^T W in one launch (G accumulates ||I - G||), then SS = W^T P
-    gemm({w.T, w.W, w.P, nullptr, 0, 0, 0, 0}, {w.W, w.W, w.G, nullptr, 1, 0, 0, 1}, 2, w, n, acc, 0.0, s);
-    gemm({w.W, w.P, w.SS, nullptr, 1, 0, 0, 2}, {}, 1, w, n, acc, 0.0, s);
-    if (it == nsteps) break;
     if (modes[it] == 1) {
       coeff_kernel<<<1, kBig, 0, s>>>(n, acc, floors[it], w);
       check_launch("coeff_kernel");
       cluster_kernel<<<n, kClThreads, 0, s>>>(n, w);
       check_launch("cluster_kernel");
+    } else {
+      e_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, acc, floors[it], w);
+      check_launch("e_kernel");
     }
-    // W2 = W + W E  (E on the fly, or from the cluster step)
-    gemm({w.W, nullptr, w.W2, w.W, 0, modes[it] == 1 ? 2 : 1, 1, 0}, {}, 1, w, n, acc, floors[it], s);
+    gemm({w.W, nullptr, w.W2, w.W, 0, 2, 1, 0}, {w.P, nullptr, w.Z, w.P, 0, 2, 1, 0}, 2, w, n, acc, s);
     std::swap(w.W, w.W2);
+    std::swap(w.P, w.Z);
+    double* nacc = accs + 3 * (it + 1);
+    gemm({w.W, w.W, w.G, nullptr, 1, 0, 0, 1}, {w.W, w.P, w.SS, nullptr, 1, 0, 0, 2}, 2, w, n, nacc, s);
   }
   // 5. selection and back-transform
   select_kernel<<<1, 512, 0, s>>>(k, n, accs + 3 * nsteps, w, theta);
   check_launch("select_kernel");
-  backsub_kernel<<<k, 32, 0, s>>>(n, k, w, Y);
-  check_launch("backsub_kernel");
+  backsub(n, k, w, Y, s);
   copy_out_kernel<<<1, 1, 0, s>>>(w, rank, quality);
   check_launch("copy_out_kernel");
   const double nn = n;
