@@ -364,7 +364,7 @@ extern "C" bmg_status bmg_dense_eig(const double* Ahat, const double* Mhat, int 
     DBuf<double> work(dense_work_doubles(n));
     DBuf<int> rk(1);
     dense_eig(Ahat, Mhat, n, sigma, k, theta, Y, rank_out ? rank_out : rk.get(), work.get(), nullptr,
-              kDropFP64, (cudaStream_t)stream);
+              kDropFP64, 0, (cudaStream_t)stream);
     BMG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   });
 }
@@ -599,6 +599,7 @@ std::unique_ptr<SolveWork> make_work(bmg_problem* p, int k, cudaStream_t s) {
   w.GA.alloc((size_t)k * k);
   w.GM.alloc((size_t)k * k);
   w.dense.alloc(dense_work_doubles(w.nh));
+  BMG_CUDA(cudaMemsetAsync(w.dense.get(), 0, sizeof(double) * dense_work_doubles(w.nh), s));
   w.parts = gram_parts(nL);
   w.partial.alloc((size_t)w.parts * std::max(k * k, 2 * k));
   w.res.alloc(2 * k);
@@ -749,7 +750,7 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
     prof_end(KC_SMALL, s, 32.0 * nh * nh, 0.0);
     // 3: enriched eigensolve
     dense_eig(w.Ahat.get(), w.Mhat.get(), nh, sigma, k, w.theta.get(), w.Y.get(), w.rank.get(), w.dense.get(),
-              w.dquality.get(), sizeof(T) == sizeof(float) ? kDropFP32 : kDropFP64, s);
+              w.dquality.get(), sizeof(T) == sizeof(float) ? kDropFP32 : kDropFP64, n1, s);
     prof_begin(KC_SMALL, s);
     shifts_kernel<T><<<grid_of(ld, 128), 128, 0, s>>>(w.theta.get(), k, ld, sigma, o.form, w.lam.get(), b.shift);
     check_launch("shifts_kernel");

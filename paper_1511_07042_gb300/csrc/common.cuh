@@ -253,8 +253,11 @@ void scale_rhs(const T* MU, const double* theta, int n, int k, int ld, T* B, cud
 // entries carry relative errors near 1e-7 so that smaller pivots are noise).
 constexpr double kDropFP64 = 1e-12;
 constexpr double kDropFP32 = 1e-5;
+// nq > 0: the leading nq x nq block of Mhat repeats from call to call on the same
+// work buffer (the coarse space's mass matrix), whose factor is then kept in `work`
+// (zero-filled before its first use).
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k,
                double* theta, double* Y, int* rank, double* work, double* quality, double drop_tol,
-               cudaStream_t s);
+               int nq, cudaStream_t s);
 size_t dense_work_doubles(int n);
 }  // namespace bmg

@@ -38,6 +38,9 @@ constexpr double kGuard = 0.05;          // largest first-order correction accep
 constexpr int kMaxN = 320;
 constexpr int kMaxDense = 224;           // the FP32 stage keeps T (n^2 floats) in shared memory
 constexpr int kBig = 1024;               // threads of the single-CTA kernels
+constexpr int kFactorWarps = 32;         // warps of the pivoted Cholesky kernels (block form)
+constexpr int kBasisWarps = 32;          // warps of the whole-matrix pivoted Cholesky
+constexpr int kTriDiagWarps = 32;        // warps of the FP32 tridiagonal reduction
 constexpr int kMaxCluster = 40;          // larger clusters keep the orthonormalising step only
 constexpr int kTile = 8;                 // output tile of the refinement products
 
@@ -47,6 +50,9 @@ struct DW {
   float *A32, *Z32, *LU32, *T3;   // T3: d, e, shifts of the tridiagonal problem, tiny
   int *cls;                        // cls[0] = cluster count, cls[1..] = cluster starts
   int *perm, *order, *rank, *srt, *cl;
+  // kept across calls: factor of the repeating leading block of M-hat (block form)
+  double *qc, *qL, *qd, *qrl;      // block copy, L_Q (nq x nq), scaling, reciprocal pivots
+  int *qperm, *qflag;              // pivot order; qflag[0] = 1 valid / 2 deficient, qflag[1] = nq
 };
 
 // 1/x to about 1e-14 relative: an FP32 seed refined by one Newton-Raphson step
@@ -55,14 +61,6 @@ struct DW {
 __device__ __forceinline__ double rcp_nr(double x) {
   const double y = (double)(1.0f / (float)x);
   return y * fma(-x, y, 2.0);
-}
-// 1/sqrt(x) for x in [1, 2]: FP32 seed and two Newton-Raphson steps
-// y <- y (3 - x y^2) / 2 in FP64.
-__device__ __forceinline__ double rsqrt_nr12(double x) {
-  double y = (double)rsqrtf((float)x);
-  y = y * fma(-0.5 * x, y * y, 1.5);
-  y = y * fma(-0.5 * x, y * y, 1.5);
-  return y;
 }
 __device__ __forceinline__ float warp_sumf(float v) {
 #pragma unroll
@@ -84,6 +82,15 @@ __device__ T block_sum(T v, T* red) {
   __syncthreads();
   return s;
 }
+
+// Triangular solves by warps (one column each, kTriWarps per CTA) stage their factor in
+// shared memory packed by columns: column i (rows q > i of an r-row factor) starts at
+// col_off(i, r).
+constexpr int kTriWarps = 4;
+__host__ __device__ inline size_t tri_smem_bytes(int n) {
+  return sizeof(double) * ((size_t)n * (n - 1) / 2 + (size_t)kTriWarps * n);
+}
+__device__ __forceinline__ int col_off(int i, int r) { return i * r - i * (i + 1) / 2; }
 
 // ------------------------------------------------ 1. basis (pivoted Cholesky) --
 // Symmetric pivoting is done physically: the trailing matrix lives in the upper
@@ -123,32 +130,22 @@ __device__ __forceinline__ void warp_argmax(unsigned long long& best, int& bi) {
     if (k2 > best || (k2 == best && i2 < bi)) { best = k2; bi = i2; }
   }
 }
-__global__ void __launch_bounds__(kBig, 1)
-basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS, double drop_tol) {
-  extern __shared__ double dsm[];
-  double* S = smemS ? dsm : w.S;
-  __shared__ unsigned long long wk[32];
-  __shared__ int wi[32];
-  __shared__ int perm[kMaxN];
-  __shared__ double d[kMaxN], lcol[kMaxN], rls[kMaxN];
-  __shared__ int s_go;
+// Pivoted Cholesky in place on the symmetric S (n x n, row stride ld, upper triangle
+// read) by the whole CTA (NW warps); perm (identity on entry) receives the pivot
+// order, rls the reciprocal pivots, and the factor ends up in the lower triangle and
+// the diagonal of the first `rank` columns.  Returns the rank to every thread.  A step
+// is a latency chain; measured on this GPU, 32 warps sharing the update beat 8 or 16.
+template <int NW>
+__device__ int pchol(double* S, int n, int ld, double drop_tol, int* perm, double* lcol, double* rls,
+                     unsigned long long* wk, int* wi, int* s_go) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int nwarps = kBig / 32;
-  for (int i = tid; i < n; i += kBig) {
-    const double mii = Mhat[i * n + i];
-    d[i] = (mii > 0.0) ? 1.0 / sqrt(mii) : 0.0;
-    perm[i] = i;
-  }
-  __syncthreads();
-  for (int i = wid; i < n; i += nwarps)
-    for (int j = lane; j < n; j += 32) S[i * n + j] = 0.5 * (Mhat[i * n + j] + Mhat[j * n + i]) * (d[i] * d[j]);
-  __syncthreads();
-  // candidates for the first pivot: warp w owns rows w, w + 32, ...
+  constexpr int nwarps = NW;
+  // candidates for the first pivot: warp w owns rows w, w + NW, ...
   {
     unsigned long long best = 0ull;
     int bi = n;
-    for (int a = wid + 32 * lane; a < n; a += 32 * nwarps) {
-      const unsigned long long key = pivot_key(S[a * n + a]);
+    for (int a = wid + nwarps * lane; a < n; a += 32 * nwarps) {
+      const unsigned long long key = pivot_key(S[a * ld + a]);
       if (key > best || (key == best && a < bi)) { best = key; bi = a; }
     }
     warp_argmax(best, bi);
@@ -158,12 +155,12 @@ basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS, double dro
   int rank = n;
   for (int j = 0; j < n; ++j) {
     if (wid == 0) {
-      unsigned long long best = wk[lane];
-      int bi = wi[lane];
+      unsigned long long best = (lane < nwarps) ? wk[lane] : 0ull;
+      int bi = (lane < nwarps) ? wi[lane] : n;
       warp_argmax(best, bi);
       const double piv = __longlong_as_double((long long)best);
       const int go = piv > drop_tol && bi < n;
-      if (lane == 0) s_go = go;
+      if (lane == 0) *s_go = go;
       if (go) {
         const int p = bi;
         const double rl = rsqrt_nr(piv), l = piv * rl;
@@ -171,13 +168,13 @@ basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS, double dro
           // symmetric swap of indices j < p: trailing upper triangle and the rows of L
           for (int x = lane; x < n; x += 32) {
             if (x < j) {
-              const double t = S[j * n + x]; S[j * n + x] = S[p * n + x]; S[p * n + x] = t;
+              const double t = S[j * ld + x]; S[j * ld + x] = S[p * ld + x]; S[p * ld + x] = t;
             } else if (x > j && x < p) {
-              const double t = S[j * n + x]; S[j * n + x] = S[x * n + p]; S[x * n + p] = t;
+              const double t = S[j * ld + x]; S[j * ld + x] = S[x * ld + p]; S[x * ld + p] = t;
             } else if (x > p) {
-              const double t = S[j * n + x]; S[j * n + x] = S[p * n + x]; S[p * n + x] = t;
+              const double t = S[j * ld + x]; S[j * ld + x] = S[p * ld + x]; S[p * ld + x] = t;
             } else if (x == j) {
-              const double t = S[j * n + j]; S[j * n + j] = S[p * n + p]; S[p * n + p] = t;
+              const double t = S[j * ld + j]; S[j * ld + j] = S[p * ld + p]; S[p * ld + p] = t;
             }
           }
           if (lane == 0) { const int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
@@ -185,32 +182,59 @@ basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS, double dro
         }
         // column j of L: L[i][j] = S[j][i] / L[j][j] below the diagonal, L[j][j] on it
         for (int i = j + 1 + lane; i < n; i += 32) {
-          const double v = S[j * n + i] * rl;
+          const double v = S[j * ld + i] * rl;
           lcol[i] = v;
-          S[i * n + j] = v;
+          S[i * ld + j] = v;
         }
-        if (lane == 0) { S[j * n + j] = l; rls[j] = rl; }
+        if (lane == 0) { S[j * ld + j] = l; rls[j] = rl; }
       }
     }
     __syncthreads();
-    if (!s_go) { rank = j; break; }
-    // rank-1 update of the trailing upper triangle; warp w owns rows j+1+w, j+1+w+32, ...
+    if (!*s_go) { rank = j; break; }
+    // rank-1 update of the trailing upper triangle; warp w owns rows j+1+w, j+1+w+NW, ...
     unsigned long long best = 0ull;
     int bi = n;
     for (int a = j + 1 + wid; a < n; a += nwarps) {
       const double la = lcol[a];
-      double* Sa = S + a * n;
+      double* Sa = S + a * ld;
       for (int b = a + lane; b < n; b += 32) Sa[b] = fma(-la, lcol[b], Sa[b]);
     }
     __syncwarp();
-    for (int a = j + 1 + wid + 32 * lane; a < n; a += 32 * nwarps) {
-      const unsigned long long key = pivot_key(S[a * n + a]);
+    for (int a = j + 1 + wid + nwarps * lane; a < n; a += 32 * nwarps) {
+      const unsigned long long key = pivot_key(S[a * ld + a]);
       if (key > best || (key == best && a < bi)) { best = key; bi = a; }
     }
     warp_argmax(best, bi);
     if (lane == 0) { wk[wid] = best; wi[wid] = bi; }
     __syncthreads();
   }
+  return rank;
+}
+
+// The whole of M-hat: unit-diagonal scaling, pivoted Cholesky, factor written as L
+// (row i holds L[i][0..i], pivot order) and Lt (row q holds column q of L).
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, 1)
+basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS, double drop_tol) {
+  extern __shared__ double dsm[];
+  double* S = smemS ? dsm : w.S;
+  __shared__ unsigned long long wk[32];
+  __shared__ int wi[32];
+  __shared__ int perm[kMaxN];
+  __shared__ double d[kMaxN], lcol[kMaxN], rls[kMaxN];
+  __shared__ int s_go;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int nwarps = NW, NT = NW * 32;
+  for (int i = tid; i < n; i += NT) {
+    const double mii = Mhat[i * n + i];
+    d[i] = (mii > 0.0) ? 1.0 / sqrt(mii) : 0.0;
+    perm[i] = i;
+  }
+  __syncthreads();
+  for (int i = wid; i < n; i += nwarps)
+    for (int j = lane; j < n; j += 32) S[i * n + j] = 0.5 * (Mhat[i * n + j] + Mhat[j * n + i]) * (d[i] * d[j]);
+  __syncthreads();
+  const int rank = pchol<NW>(S, n, n, drop_tol, perm, lcol, rls, wk, wi, &s_go);
   // write the factor: L (lower, rows in pivot order) and Lt, zero outside the first
   // rank columns and above the diagonal
   for (int i = wid; i < n; i += nwarps)
@@ -223,10 +247,177 @@ basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS, double dro
       const double v = (q <= i && q < rank) ? S[i * n + q] : 0.0;
       w.Lt[q * n + i] = v;
     }
-  for (int i = tid; i < n; i += kBig) {
+  for (int i = tid; i < n; i += NT) {
     w.perm[i] = perm[i];
     w.d[i] = d[i];
     if (i < rank) w.rl[i] = rls[i];
+  }
+  if (tid == 0) *w.rank = rank;
+}
+
+// --- Block form for M-hat = [[M_Q, C], [C^T, G]] whose leading nq x nq block M_Q (the
+// coarse space's own mass matrix) repeats from call to call: its factor is kept in the
+// workspace and recomputed only when the block changes; the block's new columns are
+// factored through their Schur complement
+//     S_X = D_X G D_X - W^T W,   W = L_Q^{-1} P_Q^T D_Q C D_X,
+// so that L = [[L_Q, 0], [Pi^T W^T, L_X]] with L_X L_X^T = Pi^T S_X Pi (pivoted).  The
+// kept span is that of the full pivoted factorisation; the FP64 work per call drops
+// from n^3 / 6 to about nq^2 k / 2 + nq k^2 / 2 + k^3 / 6, spread over the SMs except
+// the last term.
+constexpr int kMaxQ = 64;
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, 1)
+qfactor_kernel(const double* __restrict__ Mhat, int n, int nq, DW w, double drop_tol) {
+  __shared__ double S[kMaxQ * kMaxQ];
+  __shared__ unsigned long long wk[32];
+  __shared__ int wi[32];
+  __shared__ int perm[kMaxQ];
+  __shared__ double d[kMaxQ], lcol[kMaxQ], rls[kMaxQ];
+  __shared__ int s_go;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int nwarps = NW, NT = NW * 32;
+  int diff = !(w.qflag[0] == 1 && w.qflag[1] == nq);
+  for (int q = tid; q < nq * nq && !diff; q += NT) {
+    const int i = q / nq, j = q - (q / nq) * nq;
+    diff = __double_as_longlong(Mhat[i * n + j]) != __double_as_longlong(w.qc[q]);
+  }
+  if (!__syncthreads_or(diff)) return;   // the cached factor is this block's
+  for (int i = tid; i < nq; i += NT) {
+    const double mii = Mhat[i * n + i];
+    d[i] = (mii > 0.0) ? 1.0 / sqrt(mii) : 0.0;
+    perm[i] = i;
+  }
+  __syncthreads();
+  for (int i = wid; i < nq; i += nwarps)
+    for (int j = lane; j < nq; j += 32) {
+      w.qc[i * nq + j] = Mhat[i * n + j];
+      S[i * nq + j] = 0.5 * (Mhat[i * n + j] + Mhat[j * n + i]) * (d[i] * d[j]);
+    }
+  __syncthreads();
+  const int rank = pchol<NW>(S, nq, nq, drop_tol, perm, lcol, rls, wk, wi, &s_go);
+  for (int q = tid; q < nq * nq; q += NT) {
+    const int i = q / nq, j = q - (q / nq) * nq;
+    w.qL[q] = (j <= i) ? S[q] : 0.0;
+  }
+  for (int i = tid; i < nq; i += NT) {
+    w.qperm[i] = perm[i];
+    w.qd[i] = d[i];
+    w.qrl[i] = (i < rank) ? rls[i] : 0.0;
+  }
+  if (tid == 0) { w.qflag[0] = (rank == nq) ? 1 : 2; w.qflag[1] = nq; }
+}
+
+// W = L_Q^{-1} P_Q^T D_Q C D_X, one warp per new column x (as in trsm_kernel, L_Q
+// staged in shared memory, pre-scaled), output W[q][x] (row stride kx) in w.Z, and the
+// scaling d_X = 1 / sqrt(G_xx) into w.d[nq + x].
+template <int NS>
+__global__ void __launch_bounds__(kTriWarps * 32)
+xsolve_kernel(const double* __restrict__ Mhat, int n, int nq, int kx, DW w) {
+  extern __shared__ double tsm[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double* Ls = tsm;                                    // packed columns, nq (nq - 1) / 2
+  double* zs = tsm + (size_t)nq * (nq - 1) / 2 + (size_t)wid * nq;
+  for (int i = wid; i < nq; i += kTriWarps) {
+    const double rli = w.qrl[i];
+    const int o = col_off(i, nq) - i - 1;
+    for (int q = i + 1 + lane; q < nq; q += 32) Ls[o + q] = w.qL[q * nq + i] * rli;
+  }
+  __syncthreads();
+  const int x = blockIdx.x * kTriWarps + wid;
+  if (x >= kx) return;
+  const double gxx = Mhat[(nq + x) * n + nq + x];
+  const double dx = (gxx > 0.0) ? 1.0 / sqrt(gxx) : 0.0;
+  if (lane == 0) w.d[nq + x] = dx;
+  double acc[NS];
+#pragma unroll
+  for (int t = 0; t < NS; ++t) {
+    const int q = lane + 32 * t;
+    double v = 0.0;
+    if (q < nq) {
+      const int a = w.qperm[q];
+      v = 0.5 * (Mhat[a * n + nq + x] + Mhat[(nq + x) * n + a]) * (w.qd[a] * dx);
+    }
+    acc[t] = v;
+  }
+  for (int i = 0; i < nq; ++i) {
+    const int ti = i >> 5;
+    double a = acc[0];
+#pragma unroll
+    for (int t = 1; t < NS; ++t)
+      if (ti == t) a = acc[t];
+    a = __shfl_sync(0xffffffffu, a, i & 31);
+    if (lane == 0) zs[i] = a;
+    const int o = col_off(i, nq) - i - 1;
+#pragma unroll
+    for (int t = 0; t < NS; ++t) {
+      if (t >= ti) {
+        const int q = lane + 32 * t;
+        const double l = (q > i && q < nq) ? Ls[o + q] : 0.0;
+        acc[t] = fma(-l, a, acc[t]);
+      }
+    }
+  }
+  __syncwarp();
+  for (int q = lane; q < nq; q += 32) w.Z[q * kx + x] = zs[q] * w.qrl[q];
+}
+
+// S_X = D_X sym(G) D_X - W^T W (kx x kx, row stride kx) into w.S; 8 x 8 output tiles on
+// and above the diagonal, each written to both halves.
+__global__ void __launch_bounds__(64)
+schur_kernel(const double* __restrict__ Mhat, int n, int nq, int kx, DW w) {
+  if (blockIdx.y > blockIdx.x) return;
+  const int a = blockIdx.y * 8 + (threadIdx.x >> 3), b = blockIdx.x * 8 + (threadIdx.x & 7);
+  if (a >= kx || b >= kx) return;
+  const double g = 0.5 * (Mhat[(nq + a) * n + nq + b] + Mhat[(nq + b) * n + nq + a]) * (w.d[nq + a] * w.d[nq + b]);
+  double s = 0.0;
+  for (int q = 0; q < nq; ++q) s = fma(w.Z[q * kx + a], w.Z[q * kx + b], s);
+  const double v = g - s;
+  w.S[a * kx + b] = v;
+  w.S[b * kx + a] = v;
+}
+
+// Pivoted Cholesky of S_X and assembly of the factor of the whole of M-hat in the
+// layout basis_kernel writes (L, Lt, rl, perm, d, rank).  A deficient M_Q gives rank 0.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32, 1)
+xfactor_kernel(int n, int nq, int kx, DW w, int smemS, double drop_tol) {
+  extern __shared__ double dsm[];
+  double* S = smemS ? dsm : w.S;
+  __shared__ unsigned long long wk[32];
+  __shared__ int wi[32];
+  __shared__ int perm[kMaxN];
+  __shared__ double lcol[kMaxN], rls[kMaxN];
+  __shared__ int s_go;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int nwarps = NW, NT = NW * 32;
+  if (w.qflag[0] != 1) {
+    if (tid == 0) *w.rank = 0;
+    return;
+  }
+  if (smemS)
+    for (int q = tid; q < kx * kx; q += NT) S[q] = w.S[q];
+  for (int i = tid; i < kx; i += NT) perm[i] = i;
+  __syncthreads();
+  const int rx = pchol<NW>(S, kx, kx, drop_tol, perm, lcol, rls, wk, wi, &s_go);
+  const int rank = nq + rx;
+  // L[i][q]: the cached L_Q (i, q < nq); W^T in X pivot order (i >= nq, q < nq);
+  // L_X (i, q >= nq, q - nq < rx)
+  auto entry = [&](int i, int q) -> double {
+    if (q > i) return 0.0;
+    if (i < nq) return w.qL[i * nq + q];
+    const int a = i - nq;
+    if (q < nq) return w.Z[q * kx + perm[a]];
+    const int b = q - nq;
+    return (b < rx) ? S[a * kx + b] : 0.0;
+  };
+  for (int i = wid; i < n; i += nwarps)
+    for (int q = lane; q < n; q += 32) w.L[i * n + q] = entry(i, q);
+  for (int q = wid; q < n; q += nwarps)
+    for (int i = lane; i < n; i += 32) w.Lt[q * n + i] = entry(i, q);
+  for (int i = tid; i < n; i += NT) {
+    w.perm[i] = (i < nq) ? w.qperm[i] : nq + perm[i - nq];
+    if (i < nq) w.d[i] = w.qd[i];
+    if (i < rank) w.rl[i] = (i < nq) ? w.qrl[i] : rls[i - nq];
   }
   if (tid == 0) *w.rank = rank;
 }
@@ -243,11 +434,6 @@ basis_kernel(const double* __restrict__ Mhat, int n, DW w, int smemS, double dro
 // pass 0: Z = L^{-1} C, C[i][c] = d_a sym(Ahat - sigma Mhat)_ab d_b with a = perm[i],
 // b = perm[c];  pass 1: T = L^{-1} Z^T.
 constexpr int kRowsPerLane = kMaxDense / 32;   // rows per lane for rank <= 224
-constexpr int kTriWarps = 4;
-__host__ __device__ inline size_t tri_smem_bytes(int n) {
-  return sizeof(double) * ((size_t)n * (n - 1) / 2 + (size_t)kTriWarps * n);
-}
-__device__ __forceinline__ int col_off(int i, int r) { return i * r - i * (i + 1) / 2; }
 template <int NS>
 __global__ void __launch_bounds__(kTriWarps * 32)
 trsm_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mhat, int n, double sigma,
@@ -307,6 +493,10 @@ trsm_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mhat, in
 }
 
 // ---------------------------------------------- 3. FP32 eigensolve (1 CTA) -----
+// Barrier among the first kTriDiagWarps warps of the block (named barrier 1).
+__device__ __forceinline__ void tridiag_sync() {
+  asm volatile("bar.sync 1, %0;" ::"r"(kTriDiagWarps * 32) : "memory");
+}
 // Start vectors of the inverse iteration: zero-mean pseudo-random values in [-1, 1)
 // from an integer hash of (row, column).  Vectors with a common positive component
 // project almost parallel onto a near-degenerate group, and the last member of the
@@ -326,7 +516,7 @@ __global__ void __launch_bounds__(kBig)
 eig32_kernel(int n, DW w) {
   extern __shared__ float fsm[];
   __shared__ float d[kMaxN], e[kMaxN], e2[kMaxN], tau[kMaxN], vb[kMaxN], pv[kMaxN], lam[kMaxN];
-  __shared__ float redf[32], slo[32], shi[32];
+  __shared__ float slo[32], shi[32];
   const int r = *w.rank;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = kBig / 32;
@@ -349,66 +539,78 @@ eig32_kernel(int n, DW w) {
   // The squared norm of the next column below its subdiagonal is summed per warp
   // while the rank-2 update of the current step writes it (colsq, double-buffered),
   // so a step needs no separate block reduction.
+  // The first kTriDiagWarps warps run the reduction, synchronised by a named barrier
+  // (the others, if any, wait at the block barrier after it; 32 warps measured faster
+  // than 8).  Warp 0 forms each reflector (norm, beta, tau, v) while the rest wait at
+  // the step's first barrier.
   __shared__ float colsq[2][32];
-  for (int j = 0; j + 2 < r; ++j) {
-    const float a0 = A[(j + 1) * r + j];
-    float xn2;
-    if (j == 0) {
-      float part = 0.f;
-      for (int i = j + 2 + tid; i < r; i += kBig) part += A[i * r + j] * A[i * r + j];
-      xn2 = block_sum<float>(part, redf);
-    } else {
-      xn2 = warp_sumf(colsq[j & 1][lane]);   // nwarps == 32 partial sums
-    }
-    float beta = a0, t = 0.f, scale = 0.f;
-    if (xn2 > 0.f) {
-      beta = -copysignf(sqrtf(a0 * a0 + xn2), a0);
-      t = (beta - a0) / beta;
-      scale = 1.f / (a0 - beta);
-    }
-    const int m = r - j - 1;
-    for (int q = tid; q < m; q += kBig) {
-      const float v = (q == 0) ? 1.f : A[(j + 1 + q) * r + j] * scale;
-      vb[q] = v;
-      if (q > 0) A[(j + 1 + q) * r + j] = v;
-    }
-    if (tid == 0) { d[j] = A[j * r + j]; e[j] = beta; tau[j] = t; }
-    __syncthreads();
-    if (t != 0.f) {
-      // p = t A22 v: 8 lanes per row, 4 rows per warp (the row loop is uniform over
-      // the warp, so every lane reaches the shuffles)
-      for (int a0 = 4 * wid; a0 < m; a0 += 4 * nwarps) {
-        const int a = a0 + (lane >> 3);
-        float s = 0.f;
-        if (a < m) {
-          const float* Ar = A + (j + 1 + a) * r + (j + 1);
-          for (int b = lane & 7; b < m; b += 8) s = fmaf(Ar[b], vb[b], s);
+  __shared__ float s_t;
+  constexpr int tdw = kTriDiagWarps;
+  if (wid < tdw) {
+    for (int j = 0; j + 2 < r; ++j) {
+      const int m = r - j - 1;
+      if (wid == 0) {
+        const float a0 = A[(j + 1) * r + j];
+        float xn2;
+        if (j == 0) {
+          float part = 0.f;
+          for (int i = j + 2 + lane; i < r; i += 32) part += A[i * r + j] * A[i * r + j];
+          xn2 = warp_sumf(part);
+        } else {
+          xn2 = warp_sumf(lane < tdw ? colsq[j & 1][lane] : 0.f);
         }
-        s += __shfl_xor_sync(0xffffffffu, s, 1);
-        s += __shfl_xor_sync(0xffffffffu, s, 2);
-        s += __shfl_xor_sync(0xffffffffu, s, 4);
-        if ((lane & 7) == 0 && a < m) pv[a] = t * s;
+        float beta = a0, tt = 0.f, scale = 0.f;
+        if (xn2 > 0.f) {
+          beta = -copysignf(sqrtf(a0 * a0 + xn2), a0);
+          tt = (beta - a0) / beta;
+          scale = 1.f / (a0 - beta);
+        }
+        for (int q = lane; q < m; q += 32) {
+          const float v = (q == 0) ? 1.f : A[(j + 1 + q) * r + j] * scale;
+          vb[q] = v;
+          if (q > 0) A[(j + 1 + q) * r + j] = v;
+        }
+        if (lane == 0) { d[j] = A[j * r + j]; e[j] = beta; tau[j] = tt; s_t = tt; }
       }
-      __syncthreads();
-      float kk = 0.f;                                 // K = (t/2) p.v, per warp
-      for (int a = lane; a < m; a += 32) kk += pv[a] * vb[a];
-      kk = 0.5f * t * warp_sumf(kk);
-      float sq = 0.f;                                 // next column, rows a >= 2
-      for (int a = wid; a < m; a += nwarps) {        // A22 -= v w^T + w v^T, w = p - K v
-        float* Ar = A + (j + 1 + a) * r + (j + 1);
-        const float va = vb[a], wa = pv[a] - kk * va;
-        for (int b = lane; b < m; b += 32) Ar[b] -= va * (pv[b] - kk * vb[b]) + wa * vb[b];
-        if (lane == 0 && a >= 2) sq += Ar[0] * Ar[0];
+      tridiag_sync();
+      const float t = s_t;
+      if (t != 0.f) {
+        // p = t A22 v: 8 lanes per row, 4 rows per warp (the row loop is uniform over
+        // the warp, so every lane reaches the shuffles)
+        for (int a0 = 4 * wid; a0 < m; a0 += 4 * tdw) {
+          const int a = a0 + (lane >> 3);
+          float sv = 0.f;
+          if (a < m) {
+            const float* Ar = A + (j + 1 + a) * r + (j + 1);
+            for (int b = lane & 7; b < m; b += 8) sv = fmaf(Ar[b], vb[b], sv);
+          }
+          sv += __shfl_xor_sync(0xffffffffu, sv, 1);
+          sv += __shfl_xor_sync(0xffffffffu, sv, 2);
+          sv += __shfl_xor_sync(0xffffffffu, sv, 4);
+          if ((lane & 7) == 0 && a < m) pv[a] = t * sv;
+        }
+        tridiag_sync();
+        float kk = 0.f;                                 // K = (t/2) p.v, per warp
+        for (int a = lane; a < m; a += 32) kk += pv[a] * vb[a];
+        kk = 0.5f * t * warp_sumf(kk);
+        float sq = 0.f;                                 // next column, rows a >= 2
+        for (int a = wid; a < m; a += tdw) {           // A22 -= v w^T + w v^T, w = p - K v
+          float* Ar = A + (j + 1 + a) * r + (j + 1);
+          const float va = vb[a], wa = pv[a] - kk * va;
+          for (int b = lane; b < m; b += 32) Ar[b] -= va * (pv[b] - kk * vb[b]) + wa * vb[b];
+          if (lane == 0 && a >= 2) sq += Ar[0] * Ar[0];
+        }
+        if (lane == 0) colsq[(j + 1) & 1][wid] = sq;
+      } else {
+        float sq = 0.f;
+        for (int a = wid; a < m; a += tdw)
+          if (lane == 0 && a >= 2) sq += A[(j + 1 + a) * r + (j + 1)] * A[(j + 1 + a) * r + (j + 1)];
+        if (lane == 0) colsq[(j + 1) & 1][wid] = sq;
       }
-      if (lane == 0) colsq[(j + 1) & 1][wid] = sq;
-    } else {
-      float sq = 0.f;
-      for (int a = wid; a < m; a += nwarps)
-        if (lane == 0 && a >= 2) sq += A[(j + 1 + a) * r + (j + 1)] * A[(j + 1 + a) * r + (j + 1)];
-      if (lane == 0) colsq[(j + 1) & 1][wid] = sq;
+      tridiag_sync();
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (tid == 0) {
     if (r >= 2) {
       d[r - 2] = A[(r - 2) * r + (r - 2)];
@@ -533,6 +735,7 @@ eig32_kernel(int n, DW w) {
 // once, so the sequential work is one factorisation and kInvIters solves of length r.
 constexpr int kInvThreads = 64;
 constexpr int kInvSmemMembers = 63;
+constexpr int kInvLuFloats = 24 * 1024;   // shared memory for the LU factors (96 KB)
 __global__ void __launch_bounds__(kInvThreads)
 invit_kernel(int n, DW w) {
   extern __shared__ float zsh[];
@@ -549,8 +752,13 @@ invit_kernel(int n, DW w) {
   const int zld = insm ? (m | 1) : r;
   float* Z = insm ? zsh : w.Z32 + c0;            // Z[a * zld + t], member t = jv - c0
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const size_t pl = (size_t)r * r;
-  float* __restrict__ LU = w.LU32;
+  // LU factors: planes [5][row][member], in shared memory after the columns when they
+  // fit (a solve step then waits on no L2 round trip), else in global scratch
+  const bool lusm = 5 * r * m <= kInvLuFloats;
+  float* __restrict__ LU = lusm ? zsh + (size_t)n * kInvSmemMembers : w.LU32;
+  const size_t pl = lusm ? (size_t)r * m : (size_t)r * r;   // plane stride
+  const int rs = lusm ? m : r;                               // row stride
+  const int cbase = lusm ? 0 : c0;                           // column of member 0
   for (int t = tid; t < m; t += kInvThreads) {
     const int jv = c0 + t;
     const float x = shift[jv];
@@ -570,14 +778,14 @@ invit_kernel(int n, DW w) {
         p1 = cnext;
       }
       if (fabsf(a0) < tiny) a0 = (a0 < 0.f) ? -tiny : tiny;
-      const size_t o = (size_t)jj * r + jv;
+      const size_t o = (size_t)jj * rs + (cbase + t);
       LU[o] = __frcp_rn(a0);
       LU[pl + o] = a1;
       LU[2 * pl + o] = a2;
       LU[3 * pl + o] = mm;
       LU[4 * pl + o] = sw;
     }
-    const size_t o = (size_t)(r - 1) * r + jv;
+    const size_t o = (size_t)(r - 1) * rs + (cbase + t);
     LU[o] = __frcp_rn((fabsf(p0) < tiny) ? ((p0 < 0.f) ? -tiny : tiny) : p0);
     LU[pl + o] = 0.f;
     LU[2 * pl + o] = 0.f;
@@ -585,7 +793,6 @@ invit_kernel(int n, DW w) {
   }
   for (int itr = 0; itr < kInvIters; ++itr) {
     for (int t = tid; t < m; t += kInvThreads) {
-      const int jv = c0 + t;
       float* Zc = Z + t;
       // forward elimination with the row swaps; cur carries the updated z[jj]
       float cur = Zc[0];
@@ -595,7 +802,7 @@ invit_kernel(int n, DW w) {
         for (int u = 0; u < 8; ++u) {
           const int jj = j0 + u;
           if (jj + 1 < r) {
-            const size_t o = (size_t)jj * r + jv;
+            const size_t o = (size_t)jj * rs + (cbase + t);
             mv[u] = LU[3 * pl + o];
             sv[u] = LU[4 * pl + o];
             nx[u] = Zc[(jj + 1) * zld];
@@ -624,7 +831,7 @@ invit_kernel(int n, DW w) {
         for (int u = 0; u < 4; ++u) {
           const int a = a1 - u;
           if (a >= 0) {
-            const size_t o = (size_t)a * r + jv;
+            const size_t o = (size_t)a * rs + (cbase + t);
             u0v[u] = LU[o];
             u1v[u] = LU[pl + o];
             u2v[u] = LU[2 * pl + o];
@@ -943,17 +1150,123 @@ coeff_kernel(int n, const double* acc, double floor_rel, DW w) {
   }
 }
 
-// One CTA per cluster: first-order orthonormalisation K = I + R_c / 2, exact FP64
-// Jacobi diagonalisation of K S_c K, E block = K V - I.
+// One CTA per cluster: first-order orthonormalisation K = I + R_c / 2, then the
+// eigenvectors V of K S_c K, E block = K V - I.  K S_c K = mu I + Delta with Delta of
+// the size of the cluster's spread.  The FP64 pipe is what limits this kernel, so the
+// rotations are first found by cyclic Jacobi in FP32 on Delta / max|Delta| (V0); V0 is
+// made orthogonal to FP64 accuracy by one Newton-Schulz step V1 = V0 (3 I - V0^T V0) / 2,
+// and FP64 Jacobi sweeps on the nearly diagonal V1^T K S_c K V1 (one or two, against
+// about seven from the identity) finish the diagonalisation exactly.
 constexpr int kClThreads = 256;
+constexpr size_t kClSmem = sizeof(double) * 5 * kMaxCluster * kMaxCluster + sizeof(float) * 2 * kMaxCluster * kMaxCluster;
+// Cyclic Jacobi sweeps (round-robin pairing, mm/2 rotations per round) on the mm x mm
+// matrix A, accumulating the rotations into V, until off(A) <= tol fro(A) or `sweeps`
+// sweeps; T is the arithmetic (float or double).
+template <typename T>
+__device__ void jacobi_sweeps(T* A, T* V, int mm, int sweeps, T tol, T* ccs_c, T* ccs_s, int* cpr_p,
+                              int* cpr_q, T* red) {
+  const int tid = threadIdx.x;
+  const int m2 = (mm % 2 == 0) ? mm : mm + 1;
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    T off = 0, fro = 0;
+    for (int q = tid; q < mm * mm; q += kClThreads) {
+      const T v = A[q];
+      fro += v * v;
+      if (q / mm != q % mm) off += v * v;
+    }
+    off = block_sum<T>(off, red);
+    fro = block_sum<T>(fro, red);
+    if (off <= tol * fro || fro == T(0)) break;
+    for (int step = 0; step < m2 - 1; ++step) {
+      if (tid < m2 / 2) {
+        const int i = tid;
+        auto player = [&](int t) { return t == 0 ? 0 : ((t - 1 + step) % (m2 - 1)) + 1; };
+        int p = player(i), q = player(m2 - 1 - i);
+        if (p > q) { const int t = p; p = q; q = t; }
+        T cc = 1, ss = 0;
+        if (q < mm) {
+          const T apq = A[p * mm + q], dd = A[q * mm + q] - A[p * mm + p];
+          if (apq != T(0)) {
+            // t = tan of the rotation angle, 2 apq sgn(d) / (|d| + sqrt(d^2 + 4 apq^2)),
+            // in FP32 on values scaled to about 1 by a power of two; an inexact angle
+            // only slows the last sweep down, while c and s below are consistent to the
+            // working accuracy, so the rotation stays orthogonal.
+            float df, pf;
+            if constexpr (sizeof(T) == sizeof(double)) {
+              const double m = fmax(fabs(dd), 2.0 * fabs(apq));
+              const int ex = (int)((__double_as_longlong(m) >> 52) & 0x7FF) - 1023;
+              const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
+              df = (float)(dd * sc);
+              pf = (float)(2.0 * apq * sc);
+            } else {   // FP32 data of size about 1 (the caller scales it)
+              df = dd;
+              pf = 2.f * apq;
+            }
+            const float tf = ((df < 0.f) ? -pf : pf) / (fabsf(df) + sqrtf(df * df + pf * pf));
+            const T t = (df == 0.f) ? ((apq > T(0)) ? T(1) : T(-1)) : (T)tf;
+            if constexpr (sizeof(T) == sizeof(double)) {
+              cc = rsqrt_nr(fma(t, t, 1.0));
+            } else {
+              cc = rsqrtf(fmaf(t, t, 1.f));
+            }
+            ss = t * cc;
+          }
+        }
+        ccs_c[i] = cc; ccs_s[i] = ss; cpr_p[i] = p; cpr_q[i] = (q < mm && ss != T(0)) ? q : -1;
+      }
+      __syncthreads();
+      const int half = m2 / 2;
+      for (int it = tid; it < half * mm; it += kClThreads) {
+        const int i = it / mm, col = it % mm;
+        const int q = cpr_q[i];
+        if (q < 0) continue;
+        const int p = cpr_p[i];
+        const T cc = ccs_c[i], ss = ccs_s[i];
+        const T ap = A[p * mm + col], aq = A[q * mm + col];
+        A[p * mm + col] = cc * ap - ss * aq;
+        A[q * mm + col] = ss * ap + cc * aq;
+      }
+      __syncthreads();
+      for (int it = tid; it < half * mm; it += kClThreads) {
+        const int i = it / mm, row = it % mm;
+        const int q = cpr_q[i];
+        if (q < 0) continue;
+        const int p = cpr_p[i];
+        const T cc = ccs_c[i], ss = ccs_s[i];
+        const T ap = A[row * mm + p], aq = A[row * mm + q];
+        A[row * mm + p] = cc * ap - ss * aq;
+        A[row * mm + q] = ss * ap + cc * aq;
+        const T vp = V[row * mm + p], vq = V[row * mm + q];
+        V[row * mm + p] = cc * vp - ss * vq;
+        V[row * mm + q] = ss * vp + cc * vq;
+      }
+      __syncthreads();
+    }
+  }
+}
+// C = op(X) Y for mm x mm matrices in shared memory (op = transpose if tx), by the CTA
+template <typename TX>
+__device__ void small_mm(const TX* X, const double* Y, double* C, int mm, bool tx) {
+  for (int q = threadIdx.x; q < mm * mm; q += kClThreads) {
+    const int a = q / mm, e = q % mm;
+    double sacc = 0.0;
+    for (int u = 0; u < mm; ++u) sacc = fma((double)(tx ? X[u * mm + a] : X[a * mm + u]), Y[u * mm + e], sacc);
+    C[q] = sacc;
+  }
+  __syncthreads();
+}
 __global__ void __launch_bounds__(kClThreads)
 cluster_kernel(int n, DW w) {
-  __shared__ double cK[kMaxCluster * kMaxCluster], cA[kMaxCluster * kMaxCluster],
-      cV[kMaxCluster * kMaxCluster];
-  __shared__ double ccs_c[kMaxCluster / 2], ccs_s[kMaxCluster / 2];
+  extern __shared__ double csm[];
+  constexpr int MM = kMaxCluster * kMaxCluster;
+  double *cK = csm, *cA = csm + MM, *cV = csm + 2 * MM, *cT1 = csm + 3 * MM, *cT2 = csm + 4 * MM;
+  float* fA = reinterpret_cast<float*>(csm + 5 * MM);
+  float* fV = fA + MM;
+  __shared__ double ccs_c[kMaxCluster / 2], ccs_s[kMaxCluster / 2], red[32];
+  __shared__ float fcs_c[kMaxCluster / 2], fcs_s[kMaxCluster / 2], redf[32];
   __shared__ int cpr_p[kMaxCluster / 2], cpr_q[kMaxCluster / 2];
   __shared__ int idx[kMaxCluster];
-  __shared__ double red[32];
+  __shared__ double s_mu, s_sc;
   const int c = blockIdx.x;
   if (c >= w.cl[0]) return;
   const int b = w.cl[1 + c], mm = w.cl[2 + c] - b;
@@ -965,23 +1278,44 @@ cluster_kernel(int n, DW w) {
     const int a = q / mm, e = q % mm;
     const double gs = 0.5 * (w.G[idx[a] * n + idx[e]] + w.G[idx[e] * n + idx[a]]);
     cK[q] = (a == e ? 1.5 : 0.0) - 0.5 * gs;
+    cT2[q] = 0.5 * (w.SS[idx[a] * n + idx[e]] + w.SS[idx[e] * n + idx[a]]);
   }
   __syncthreads();
-  for (int q = tid; q < mm * mm; q += kClThreads) {    // cV = K S_c
+  small_mm(cK, cT2, cT1, mm, false);   // K S_c
+  small_mm(cT1, cK, cA, mm, false);    // K S_c K
+  // Delta = sym(K S_c K) - mu I, scaled by its largest entry, in FP32
+  if (tid == 0) {
+    double mu = 0.0;
+    for (int a = 0; a < mm; ++a) mu += cA[a * mm + a];
+    mu /= mm;
+    double mx = 0.0;
+    for (int a = 0; a < mm; ++a)
+      for (int e = a; e < mm; ++e)
+        mx = fmax(mx, fabs(0.5 * (cA[a * mm + e] + cA[e * mm + a]) - (a == e ? mu : 0.0)));
+    s_mu = mu;
+    s_sc = (mx > 0.0) ? 1.0 / mx : 0.0;
+  }
+  __syncthreads();
+  for (int q = tid; q < mm * mm; q += kClThreads) {
     const int a = q / mm, e = q % mm;
-    double s = 0.0;
-    for (int u = 0; u < mm; ++u)
-      s += cK[a * mm + u] * 0.5 * (w.SS[idx[u] * n + idx[e]] + w.SS[idx[e] * n + idx[u]]);
-    cV[q] = s;
+    const double v = 0.5 * (cA[a * mm + e] + cA[e * mm + a]);
+    cT2[q] = v;
+    fA[q] = (float)((v - (a == e ? s_mu : 0.0)) * s_sc);
+    fV[q] = (a == e) ? 1.f : 0.f;
   }
   __syncthreads();
-  for (int q = tid; q < mm * mm; q += kClThreads) {    // cA = (K S_c) K
+  jacobi_sweeps<float>(fA, fV, mm, 12, 1e-13f, fcs_c, fcs_s, cpr_p, cpr_q, redf);
+  // V1 = V0 (3 I - V0^T V0) / 2
+  for (int q = tid; q < mm * mm; q += kClThreads) {
     const int a = q / mm, e = q % mm;
-    double s = 0.0;
-    for (int u = 0; u < mm; ++u) s += cV[a * mm + u] * cK[u * mm + e];
-    cA[q] = s;
+    double sacc = 0.0;
+    for (int u = 0; u < mm; ++u) sacc = fma((double)fV[u * mm + a], (double)fV[u * mm + e], sacc);
+    cT1[q] = (a == e ? 1.5 : 0.0) - 0.5 * sacc;
   }
   __syncthreads();
+  small_mm(fV, cT1, cV, mm, false);    // V1
+  small_mm(cT2, cV, cT1, mm, false);   // sym(K S_c K) V1
+  small_mm(cV, cT1, cA, mm, true);     // A' = V1^T K S_c K V1
   for (int q = tid; q < mm * mm; q += kClThreads) {
     const int a = q / mm, e = q % mm;
     if (a < e) {
@@ -991,79 +1325,12 @@ cluster_kernel(int n, DW w) {
     }
   }
   __syncthreads();
-  for (int q = tid; q < mm * mm; q += kClThreads) cV[q] = (q / mm == q % mm) ? 1.0 : 0.0;
-  __syncthreads();
-  const int m2 = (mm % 2 == 0) ? mm : mm + 1;
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0, fro = 0.0;
-    for (int q = tid; q < mm * mm; q += kClThreads) {
-      const double v = cA[q];
-      fro += v * v;
-      if (q / mm != q % mm) off += v * v;
-    }
-    off = block_sum<double>(off, red);
-    fro = block_sum<double>(fro, red);
-    if (off <= 1e-32 * fro || fro == 0.0) break;
-    for (int step = 0; step < m2 - 1; ++step) {
-      if (tid < m2 / 2) {
-        const int i = tid;
-        auto player = [&](int t) { return t == 0 ? 0 : ((t - 1 + step) % (m2 - 1)) + 1; };
-        int p = player(i), q = player(m2 - 1 - i);
-        if (p > q) { const int t = p; p = q; q = t; }
-        double cc = 1.0, ss = 0.0;
-        if (q < mm) {
-          const double apq = cA[p * mm + q], dd = cA[q * mm + q] - cA[p * mm + p];
-          if (apq != 0.0) {
-            // t = tan of the rotation angle, 2 apq sgn(d) / (|d| + sqrt(d^2 + 4 apq^2)),
-            // in FP32 on values scaled to about 1 by a power of two; an inexact angle
-            // only slows the last sweep down, while c and s below are consistent to
-            // FP64 accuracy, so the rotation stays orthogonal.
-            const double m = fmax(fabs(dd), 2.0 * fabs(apq));
-            const int ex = (int)((__double_as_longlong(m) >> 52) & 0x7FF) - 1023;
-            const double sc = __longlong_as_double((long long)(1023 - ex) << 52);
-            const float df = (float)(dd * sc), pf = (float)(2.0 * apq * sc);
-            const float tf = ((df < 0.f) ? -pf : pf) / (fabsf(df) + sqrtf(df * df + pf * pf));
-            const double t = (df == 0.f) ? ((apq > 0.0) ? 1.0 : -1.0) : (double)tf;
-            cc = rsqrt_nr12(fma(t, t, 1.0));
-            ss = t * cc;
-          }
-        }
-        ccs_c[i] = cc; ccs_s[i] = ss; cpr_p[i] = p; cpr_q[i] = (q < mm && ss != 0.0) ? q : -1;
-      }
-      __syncthreads();
-      const int half = m2 / 2;
-      for (int it = tid; it < half * mm; it += kClThreads) {
-        const int i = it / mm, col = it % mm;
-        const int q = cpr_q[i];
-        if (q < 0) continue;
-        const int p = cpr_p[i];
-        const double cc = ccs_c[i], ss = ccs_s[i];
-        const double ap = cA[p * mm + col], aq = cA[q * mm + col];
-        cA[p * mm + col] = cc * ap - ss * aq;
-        cA[q * mm + col] = ss * ap + cc * aq;
-      }
-      __syncthreads();
-      for (int it = tid; it < half * mm; it += kClThreads) {
-        const int i = it / mm, row = it % mm;
-        const int q = cpr_q[i];
-        if (q < 0) continue;
-        const int p = cpr_p[i];
-        const double cc = ccs_c[i], ss = ccs_s[i];
-        const double ap = cA[row * mm + p], aq = cA[row * mm + q];
-        cA[row * mm + p] = cc * ap - ss * aq;
-        cA[row * mm + q] = ss * ap + cc * aq;
-        const double vp = cV[row * mm + p], vq = cV[row * mm + q];
-        cV[row * mm + p] = cc * vp - ss * vq;
-        cV[row * mm + q] = ss * vp + cc * vq;
-      }
-      __syncthreads();
-    }
-  }
+  jacobi_sweeps<double>(cA, cV, mm, 10, 1e-32, ccs_c, ccs_s, cpr_p, cpr_q, red);
   for (int q = tid; q < mm * mm; q += kClThreads) {
     const int a = q / mm, e = q % mm;
-    double s = 0.0;
-    for (int u = 0; u < mm; ++u) s += cK[a * mm + u] * cV[u * mm + e];
-    w.E[idx[a] * n + idx[e]] = s - (a == e ? 1.0 : 0.0);
+    double sacc = 0.0;
+    for (int u = 0; u < mm; ++u) sacc += cK[a * mm + u] * cV[u * mm + e];
+    w.E[idx[a] * n + idx[e]] = sacc - (a == e ? 1.0 : 0.0);
   }
 }
 
@@ -1187,6 +1454,12 @@ DW carve(double* work, int n) {
   w.srt = reinterpret_cast<int*>(p); p += n / 2 + 1;
   w.cl = reinterpret_cast<int*>(p); p += n / 2 + 2;
   w.rank = reinterpret_cast<int*>(p); p += 1;
+  w.qc = p; p += nn;
+  w.qL = p; p += nn;
+  w.qd = p; p += n;
+  w.qrl = p; p += n;
+  w.qperm = reinterpret_cast<int*>(p); p += n / 2 + 1;
+  w.qflag = reinterpret_cast<int*>(p); p += 1;
   return w;
 }
 
@@ -1239,20 +1512,42 @@ void backsub(int n, int k, const DW& w, double* Y, cudaStream_t s) {
 
 size_t dense_work_doubles(int n) {
   const size_t nn = (size_t)n * n;
-  return 11 * nn + 3 * (size_t)n + 48 + (nn + n) / 2 + 1 + (nn / 2 + 1) + (5 * nn + 1) / 2 + 1 + (3 * (size_t)n + 5) / 2 + 1 + ((size_t)n + 3) / 2 + 1 + 4 * ((size_t)n / 2 + 2) + 1 + 16;
+  return 11 * nn + 3 * (size_t)n + 48 + (nn + n) / 2 + 1 + (nn / 2 + 1) + (5 * nn + 1) / 2 + 1 + (3 * (size_t)n + 5) / 2 + 1 + ((size_t)n + 3) / 2 + 1 + 4 * ((size_t)n / 2 + 2) + 1 + 16 +
+         2 * nn + 2 * (size_t)n + (size_t)n / 2 + 2;
 }
 
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k, double* theta,
-               double* Y, int* rank, double* work, double* quality, double drop_tol, cudaStream_t s) {
+               double* Y, int* rank, double* work, double* quality, double drop_tol, int nq, cudaStream_t s) {
   if (n < 1 || n > kMaxDense || k < 1 || k > n) fail(BMG_ERR_INVALID_ARG, "dense_eig: need 1 <= k <= n <= 224");
   prof_begin(KC_DENSE, s);
   DW w = carve(work, n);
-  // 1. basis
-  const size_t smemS = (size_t)n * n * sizeof(double);
-  const bool useS = smemS <= 200 * 1024;
-  if (useS) BMG_CUDA(cudaFuncSetAttribute(basis_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemS));
-  basis_kernel<<<1, kBig, useS ? smemS : 0, s>>>(Mhat, n, w, useS ? 1 : 0, drop_tol);
-  check_launch("basis_kernel");
+  // 1. basis: whole pivoted factorisation, or the block form when the leading nq x nq
+  //    block repeats (its factor cached in the workspace)
+  if (nq > 0 && nq <= kMaxQ && nq < n && (size_t)(n - nq) * (n - nq) * sizeof(double) <= 200 * 1024) {
+    const int kx = n - nq;
+    qfactor_kernel<kFactorWarps><<<1, kFactorWarps * 32, 0, s>>>(Mhat, n, nq, w, drop_tol);
+    check_launch("qfactor_kernel");
+    const size_t xsm = sizeof(double) * ((size_t)nq * (nq - 1) / 2 + (size_t)kTriWarps * nq);
+    if (nq <= 32) {
+      xsolve_kernel<1><<<(kx + kTriWarps - 1) / kTriWarps, kTriWarps * 32, xsm, s>>>(Mhat, n, nq, kx, w);
+    } else {
+      xsolve_kernel<2><<<(kx + kTriWarps - 1) / kTriWarps, kTriWarps * 32, xsm, s>>>(Mhat, n, nq, kx, w);
+    }
+    check_launch("xsolve_kernel");
+    const int nt = (kx + 7) / 8;
+    schur_kernel<<<dim3(nt, nt), 64, 0, s>>>(Mhat, n, nq, kx, w);
+    check_launch("schur_kernel");
+    const size_t xfs = (size_t)kx * kx * sizeof(double);
+    BMG_CUDA(cudaFuncSetAttribute(xfactor_kernel<kFactorWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xfs));
+    xfactor_kernel<kFactorWarps><<<1, kFactorWarps * 32, xfs, s>>>(n, nq, kx, w, 1, drop_tol);
+    check_launch("xfactor_kernel");
+  } else {
+    const size_t smemS = (size_t)n * n * sizeof(double);
+    const bool useS = smemS <= 200 * 1024;
+    if (useS) BMG_CUDA(cudaFuncSetAttribute(basis_kernel<kBasisWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemS));
+    basis_kernel<kBasisWarps><<<1, kBasisWarps * 32, useS ? smemS : 0, s>>>(Mhat, n, w, useS ? 1 : 0, drop_tol);
+    check_launch("basis_kernel");
+  }
   // 2. reduced standard matrix
   trsm(Ahat, Mhat, n, sigma, 0, w, s);
   trsm(Ahat, Mhat, n, sigma, 1, w, s);
@@ -1262,7 +1557,7 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
   BMG_CUDA(cudaFuncSetAttribute(eig32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
   eig32_kernel<<<1, kBig, esm, s>>>(n, w);
   check_launch("eig32_kernel");
-  const size_t ism = sizeof(float) * (size_t)n * (kInvSmemMembers | 1);
+  const size_t ism = sizeof(float) * ((size_t)n * kInvSmemMembers + kInvLuFloats);
   BMG_CUDA(cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
   invit_kernel<<<n, kInvThreads, ism, s>>>(n, w);
   check_launch("invit_kernel");
@@ -1290,7 +1585,8 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
     if (modes[it] == 1) {
       coeff_kernel<<<1, kBig, 0, s>>>(n, acc, floors[it], w);
       check_launch("coeff_kernel");
-      cluster_kernel<<<n, kClThreads, 0, s>>>(n, w);
+      BMG_CUDA(cudaFuncSetAttribute(cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem));
+      cluster_kernel<<<n, kClThreads, kClSmem, s>>>(n, w);
       check_launch("cluster_kernel");
     } else {
       e_kernel<<<(n * n + 255) / 256, 256, 0, s>>>(n, acc, floors[it], w);
