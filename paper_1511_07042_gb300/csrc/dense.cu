@@ -999,24 +999,38 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc) {
   double* As = gsm;                 // kTile x r
   double* Bs = gsm + kTile * r;     // r x kTile
   const int tid = threadIdx.x;
-#pragma unroll 8
-  for (int q = tid; q < kTile * r; q += kTile * kTile) {
-    const int a = q / r, kq = q % r;
-    const int row = row0 + a;
-    As[q] = (row < r) ? (jb.ta ? jb.A[kq * n + row] : jb.A[row * n + kq]) : 0.0;
+  static_assert(kTile == 8, "panel loads map 8 consecutive threads to one tile row/column");
+  if (jb.ta) {                      // As[a][kq] = A[kq][row0 + a]: 8 consecutive per kq
+    for (int q = tid; q < kTile * r; q += kTile * kTile) {
+      const int kq = q >> 3, a = q & 7;
+      As[a * r + kq] = (row0 + a < r) ? jb.A[kq * n + row0 + a] : 0.0;
+    }
+  } else {                          // As[a][kq] = A[row0 + a][kq]: rows contiguous
+    for (int a = 0; a < kTile; ++a)
+      for (int kq = tid; kq < r; kq += kTile * kTile)
+        As[a * r + kq] = (row0 + a < r) ? jb.A[(row0 + a) * n + kq] : 0.0;
   }
   const double* B = jb.bmode == 2 ? w.E : jb.B;
-#pragma unroll 4
   for (int q = tid; q < r * kTile; q += kTile * kTile) {
-    const int kq = q / kTile, b = q % kTile;
-    const int col = col0 + b;
-    Bs[q] = (col < r) ? B[kq * n + col] : 0.0;
+    const int kq = q >> 3, b = q & 7;
+    Bs[q] = (col0 + b < r) ? B[kq * n + col0 + b] : 0.0;
   }
   __syncthreads();
   const int ty = tid / kTile, tx = tid % kTile;
   const int row = row0 + ty, col = col0 + tx;
-  double a_acc = 0.0;
-  for (int kq = 0; kq < r; ++kq) a_acc = fma(As[ty * r + kq], Bs[kq * kTile + tx], a_acc);
+  // four interleaved partial sums: the FP64 FMA latency, not the pipe, bounds a
+  // single dependent chain
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const double* Ar = As + ty * r;
+  int kq = 0;
+  for (; kq + 3 < r; kq += 4) {
+    s0 = fma(Ar[kq], Bs[kq * kTile + tx], s0);
+    s1 = fma(Ar[kq + 1], Bs[(kq + 1) * kTile + tx], s1);
+    s2 = fma(Ar[kq + 2], Bs[(kq + 2) * kTile + tx], s2);
+    s3 = fma(Ar[kq + 3], Bs[(kq + 3) * kTile + tx], s3);
+  }
+  for (; kq < r; ++kq) s0 = fma(Ar[kq], Bs[kq * kTile + tx], s0);
+  const double a_acc = (s0 + s1) + (s2 + s3);
   const bool in = row < r && col < r;
   if (in) jb.C[row * n + col] = jb.addD ? jb.D[row * n + col] + a_acc : a_acc;
   const bool offdiag = blockIdx.y != blockIdx.x;
@@ -1030,8 +1044,17 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc) {
       } else if (row == col) {
         // g_ii from the A panel (W^T rows), in the order of the G product, so that
         // G and S can be formed in one launch
-        double gii = 0.0;
-        for (int kq = 0; kq < r; ++kq) gii = fma(As[ty * r + kq], As[ty * r + kq], gii);
+        const double* Ar2 = As + ty * r;
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
+        int kk = 0;
+        for (; kk + 3 < r; kk += 4) {
+          g0 = fma(Ar2[kk], Ar2[kk], g0);
+          g1 = fma(Ar2[kk + 1], Ar2[kk + 1], g1);
+          g2 = fma(Ar2[kk + 2], Ar2[kk + 2], g2);
+          g3 = fma(Ar2[kk + 3], Ar2[kk + 3], g3);
+        }
+        for (; kk < r; ++kk) g0 = fma(Ar2[kk], Ar2[kk], g0);
+        const double gii = (g0 + g1) + (g2 + g3);
         const double lam = a_acc / (2.0 - gii);
         w.lam[row] = lam;
         c0 = (a_acc - lam) * (a_acc - lam);
