@@ -541,55 +541,54 @@ eig32_kernel(int n, DW w) {
   // so a step needs no separate block reduction.
   // The first kTriDiagWarps warps run the reduction, synchronised by a named barrier
   // (the others, if any, wait at the block barrier after it; 32 warps measured faster
-  // than 8).  Warp 0 forms each reflector (norm, beta, tau, v) while the rest wait at
-  // the step's first barrier.
+  // than 8).  A step has two barriers: every warp forms the reflector's scalars itself
+  // (norm from the per-warp column sums, beta, tau) and reads v from column j as it
+  // goes, so the product p = tau A22 v starts at once; warp 0 also stores v, which the
+  // rank-2 update reads after the first barrier and which is written into column j
+  // (for the back-transformation) before the second.
   __shared__ float colsq[2][32];
-  __shared__ float s_t;
   constexpr int tdw = kTriDiagWarps;
   if (wid < tdw) {
     for (int j = 0; j + 2 < r; ++j) {
       const int m = r - j - 1;
-      if (wid == 0) {
-        const float a0 = A[(j + 1) * r + j];
-        float xn2;
-        if (j == 0) {
-          float part = 0.f;
-          for (int i = j + 2 + lane; i < r; i += 32) part += A[i * r + j] * A[i * r + j];
-          xn2 = warp_sumf(part);
-        } else {
-          xn2 = warp_sumf(lane < tdw ? colsq[j & 1][lane] : 0.f);
-        }
-        float beta = a0, tt = 0.f, scale = 0.f;
-        if (xn2 > 0.f) {
-          beta = -copysignf(sqrtf(a0 * a0 + xn2), a0);
-          tt = (beta - a0) / beta;
-          scale = 1.f / (a0 - beta);
-        }
-        for (int q = lane; q < m; q += 32) {
-          const float v = (q == 0) ? 1.f : A[(j + 1 + q) * r + j] * scale;
-          vb[q] = v;
-          if (q > 0) A[(j + 1 + q) * r + j] = v;
-        }
-        if (lane == 0) { d[j] = A[j * r + j]; e[j] = beta; tau[j] = tt; s_t = tt; }
+      const float a0 = A[(j + 1) * r + j];
+      float xn2;
+      if (j == 0) {
+        float part = 0.f;
+        for (int i = j + 2 + lane; i < r; i += 32) part += A[i * r + j] * A[i * r + j];
+        xn2 = warp_sumf(part);
+      } else {
+        xn2 = warp_sumf(lane < tdw ? colsq[j & 1][lane] : 0.f);
       }
-      tridiag_sync();
-      const float t = s_t;
+      float beta = a0, t = 0.f, scale = 0.f;
+      if (xn2 > 0.f) {
+        beta = -copysignf(sqrtf(a0 * a0 + xn2), a0);
+        t = (beta - a0) / beta;
+        scale = 1.f / (a0 - beta);
+      }
+      const float* colj = A + (j + 1) * r + j;      // colj[q * r] = A[j + 1 + q][j]
+      if (wid == 0) {
+        for (int q = lane; q < m; q += 32) vb[q] = (q == 0) ? 1.f : colj[q * r] * scale;
+        if (lane == 0) { d[j] = A[j * r + j]; e[j] = beta; tau[j] = t; }
+      }
       if (t != 0.f) {
         // p = t A22 v: 8 lanes per row, 4 rows per warp (the row loop is uniform over
         // the warp, so every lane reaches the shuffles)
-        for (int a0 = 4 * wid; a0 < m; a0 += 4 * tdw) {
-          const int a = a0 + (lane >> 3);
+        for (int a0r = 4 * wid; a0r < m; a0r += 4 * tdw) {
+          const int a = a0r + (lane >> 3);
           float sv = 0.f;
           if (a < m) {
             const float* Ar = A + (j + 1 + a) * r + (j + 1);
-            for (int b = lane & 7; b < m; b += 8) sv = fmaf(Ar[b], vb[b], sv);
+            for (int b = lane & 7; b < m; b += 8) sv = fmaf(Ar[b], (b == 0) ? 1.f : colj[b * r] * scale, sv);
           }
           sv += __shfl_xor_sync(0xffffffffu, sv, 1);
           sv += __shfl_xor_sync(0xffffffffu, sv, 2);
           sv += __shfl_xor_sync(0xffffffffu, sv, 4);
           if ((lane & 7) == 0 && a < m) pv[a] = t * sv;
         }
-        tridiag_sync();
+      }
+      tridiag_sync();
+      if (t != 0.f) {
         float kk = 0.f;                                 // K = (t/2) p.v, per warp
         for (int a = lane; a < m; a += 32) kk += pv[a] * vb[a];
         kk = 0.5f * t * warp_sumf(kk);
@@ -607,6 +606,8 @@ eig32_kernel(int n, DW w) {
           if (lane == 0 && a >= 2) sq += A[(j + 1 + a) * r + (j + 1)] * A[(j + 1 + a) * r + (j + 1)];
         if (lane == 0) colsq[(j + 1) & 1][wid] = sq;
       }
+      if (wid == 0)                                     // v_j into column j, below the subdiagonal
+        for (int q = 1 + lane; q < m; q += 32) A[(j + 1 + q) * r + j] = vb[q];
       tridiag_sync();
     }
   }
