@@ -32,6 +32,8 @@
 #ifndef BMG_H
 #define BMG_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -80,11 +82,15 @@ typedef struct {
   int max_cycles;            /* cycle cap on the finest level                      */
   int precision;             /* bmg_precision                                     */
   double switch_tol;         /* FP32 -> FP64 hand-over residual (BMG_PREC_FP32)    */
+  int stop_after_cycles;     /* > 0: stop before cycle stop_after_cycles + 1 and   */
+                             /*      keep the state (checkpoint, see below)        */
+  int resume;                /* 1: continue from the state given to bmg_set_state  */
 } bmg_options;
 
 /* Fills the defaults: Jacobi, nu=2, omega=2/3, shifted form, full depth,
  * 6 intermediate cycles, no intermediate tolerance, 200 finest cycles, float64,
- * switch_tol 1e-7 (near the float32 floor of the relative residual).           */
+ * switch_tol 1e-7 (near the float32 floor of the relative residual), no stop,
+ * no resume.                                                                     */
 void bmg_default_options(bmg_options* opt);
 
 typedef struct bmg_problem bmg_problem;
@@ -185,6 +191,27 @@ bmg_status bmg_solve_batched(int n_jobs, bmg_problem* const* problems, const dou
                              bmg_solve_info* infos, int concurrency);
 
 /* ---------------------------------------------- inspection (host outputs) --- */
+
+/* Checkpoint and resume of bmg_solve at a cycle boundary of the BFMG loop (Alg. 4:
+ * the state between two cycles is the level, the cycle count on it, the iterate block
+ * on that level in the working arithmetic, the arithmetic phase of the precision form,
+ * and the counters and history reported in bmg_solve_info).
+ *   A bmg_solve with options.stop_after_cycles = c > 0 stops before its (c+1)-th
+ *   cycle (counted over all levels), returns BMG_ERR_NOT_CONVERGED with the last
+ *   cycle's Ritz values and residuals (evecs is written only if that cycle ran on
+ *   the finest level) and keeps its state with the problem, for block size k.
+ *   bmg_get_state copies that state into buf (host, len bytes); *used receives the
+ *   size in bytes (buf may be NULL to query it).  BMG_ERR_STATE if no solve of block
+ *   size k was stopped; BMG_ERR_INVALID_ARG if len is too small.
+ *   bmg_set_state loads a state (host buffer) taken from this or another problem
+ *   handle built from the same mesh and hierarchy; the next bmg_solve on (p, k) with
+ *   options.resume = 1 and the same n_wanted, sigma, tol and options (other than
+ *   stop_after_cycles and resume) continues from it, and its outputs are bit-identical
+ *   to those of the uninterrupted solve.  BMG_ERR_INVALID_ARG for a malformed state
+ *   or one of another hierarchy; bmg_solve with resume = 1 returns BMG_ERR_STATE
+ *   without a state and BMG_ERR_INVALID_ARG if the arguments differ from the state's. */
+bmg_status bmg_get_state(const bmg_problem* p, int k, void* buf, size_t len, size_t* used);
+bmg_status bmg_set_state(bmg_problem* p, int k, const void* buf, size_t len);
 
 /* Sizes of refinement r (0..R): vertices, triangles, CSR nonzeros.             */
 bmg_status bmg_get_sizes(const bmg_problem* p, int refinement, int* n, int* n_tris,

@@ -35,7 +35,7 @@ class Options(C.Structure):
     _fields_ = [("smoother", C.c_int), ("nu", C.c_int), ("omega", C.c_double), ("form", C.c_int),
                 ("vcycle_depth", C.c_int), ("cycles_intermediate", C.c_int),
                 ("tol_intermediate", C.c_double), ("max_cycles", C.c_int), ("precision", C.c_int),
-                ("switch_tol", C.c_double)]
+                ("switch_tol", C.c_double), ("stop_after_cycles", C.c_int), ("resume", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -87,6 +87,8 @@ def _load():
         "bmg_kernel_class_name": (C.c_char_p, [i]),
         "bmg_launch_count": (C.c_longlong, []),
         "bmg_autotune_report": (i, [C.c_char_p, i]),
+        "bmg_get_state": (i, [vp, i, vp, C.c_size_t, P(C.c_size_t)]),
+        "bmg_set_state": (i, [vp, i, vp, C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -128,7 +130,7 @@ def _stream():
 
 def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_depth=99,
             cycles_intermediate=6, tol_intermediate=-1.0, max_cycles=200, precision="fp64",
-            switch_tol=1e-7) -> Options:
+            switch_tol=1e-7, stop_after_cycles=0, resume=False) -> Options:
     o = Options()
     LIB.bmg_default_options(C.byref(o))
     o.smoother = SMOOTHERS[smoother]
@@ -141,6 +143,8 @@ def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_dep
     o.max_cycles = max_cycles
     o.precision = PRECISIONS[precision]
     o.switch_tol = switch_tol
+    o.stop_after_cycles = stop_after_cycles
+    o.resume = int(bool(resume))
     return o
 
 
@@ -238,13 +242,14 @@ class Problem:
         return ev, U_host, rs, info
 
     def solve(self, X0, k, n_wanted, sigma, tol, opt=None, evecs=True, evecs_device=None):
-        """BFMG solve.  X0: numpy [N_2, k] (host) or torch CUDA tensor (device).
+        """BFMG solve.  X0: numpy [N_2, k] (host) or torch CUDA tensor (device); None
+        with options(resume=True), which continues from the state given to set_state.
 
         Returns (evals, evecs, resid, info) with evecs a numpy array, or the
         caller's torch tensor `evecs_device` when given.
         """
-        on_dev = not isinstance(X0, np.ndarray)
-        X0c = X0 if on_dev else np.ascontiguousarray(X0, dtype=np.float64)
+        on_dev = X0 is not None and not isinstance(X0, np.ndarray)
+        X0c = X0 if (on_dev or X0 is None) else np.ascontiguousarray(X0, dtype=np.float64)
         nL = self.sizes(self.refinements)[0]
         ev = np.empty(n_wanted)
         rs = np.empty(n_wanted)
@@ -261,6 +266,19 @@ class Problem:
         if code not in (0, 5):
             _check(code)
         return ev, U, rs, info
+
+    def get_state(self, k):
+        """State of the last solve of block size k stopped by stop_after_cycles (bytes)."""
+        n = C.c_size_t(0)
+        _check(LIB.bmg_get_state(self.h, k, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _check(LIB.bmg_get_state(self.h, k, buf, n.value, C.byref(n)))
+        return buf.raw[:n.value]
+
+    def set_state(self, k, state):
+        """Loads a state; the next solve with options(resume=True) continues from it."""
+        buf = C.create_string_buffer(bytes(state), len(state))
+        _check(LIB.bmg_set_state(self.h, k, buf, len(state)))
 
 
 def solve_batched(problems, sigmas, X0s, k, n_wanted, tol, opt=None, evecs=False, concurrency=0):

@@ -112,6 +112,8 @@ extern "C" void bmg_default_options(bmg_options* o) {
   o->max_cycles = 200;
   o->precision = BMG_PREC_FP64;
   o->switch_tol = 1e-7;
+  o->stop_after_cycles = 0;
+  o->resume = 0;
 }
 
 extern "C" const char* bmg_last_error(void) { return g_last_error.c_str(); }
@@ -839,20 +841,65 @@ bmg_options checked_options(const bmg_problem* p, int k, int n_wanted, double si
   const int n1 = p->meshOf(1).n, n2 = p->meshOf(2).n;
   if (k < 1 || k > 160 || n_wanted < 1 || n_wanted > k || k > n2 || n1 + k > 224)
     fail(BMG_ERR_INVALID_ARG, "need 1 <= n_wanted <= k <= min(N_2, 160) and N_1 + k <= 224");
-  if (!X0 || !evals) fail(BMG_ERR_INVALID_ARG, "X0 and evals are required");
+  if ((!X0 && o.resume != 1) || !evals) fail(BMG_ERR_INVALID_ARG, "X0 (unless resuming) and evals are required");
   if (!(tol > 0.0) || !std::isfinite(sigma)) fail(BMG_ERR_INVALID_ARG, "bad tol or sigma");
   if (o.nu < 1 || o.nu > 64 || o.smoother < 0 || o.smoother > 2 || o.form < 0 || o.form > 1 ||
       o.max_cycles < 1 || o.cycles_intermediate < 1 || !(o.omega > 0.0) || o.precision < 0 ||
-      o.precision > 1 || !(o.switch_tol > 0.0))
+      o.precision > 1 || !(o.switch_tol > 0.0) || o.stop_after_cycles < 0 || o.resume < 0 || o.resume > 1)
     fail(BMG_ERR_INVALID_ARG, "bad options");
   return o;
+}
+
+// --- Checkpoint: the solver state between two cycles of the BFMG loop, as bytes:
+// StateHead, then hist[n_hist], hist_level[n_info], hist_fp32[n_info] (int32),
+// hist_resid[n_info], lamv[k], rho[k], X[n_f][k] (the iterate; float32 values of the
+// precision form are exact in float64).
+struct StateHead {
+  uint32_t magic, version;
+  int32_t k, L, n_wanted, level, cycle, fp32, total_cycles, fp32_cycles, n_f, n_hist, n_info, pad;
+  int32_t cyc[33];
+  double sigma, tol, max_dense_err;
+  int32_t smoother, nu, form, vcycle_depth, cycles_intermediate, max_cycles, precision, pad2;
+  double omega, tol_intermediate, switch_tol;
+};
+constexpr uint32_t kStateMagic = 0x53474d42u;   // "BMGS"
+constexpr uint32_t kStateVersion = 1;
+size_t state_bytes(const StateHead& h) {
+  return sizeof(StateHead) + sizeof(double) * ((size_t)h.n_hist + h.n_info + 2 * (size_t)h.k + (size_t)h.n_f * h.k) +
+         sizeof(int32_t) * 2 * (size_t)h.n_info;
+}
+void head_options(StateHead& h, const bmg_options& o) {
+  h.smoother = o.smoother; h.nu = o.nu; h.form = o.form; h.vcycle_depth = o.vcycle_depth;
+  h.cycles_intermediate = o.cycles_intermediate; h.max_cycles = o.max_cycles; h.precision = o.precision;
+  h.omega = o.omega; h.tol_intermediate = o.tol_intermediate; h.switch_tol = o.switch_tol;
+}
+bool same_options(const StateHead& h, const bmg_options& o) {
+  StateHead g = h;
+  head_options(g, o);
+  return g.smoother == h.smoother && g.nu == h.nu && g.form == h.form && g.vcycle_depth == h.vcycle_depth &&
+         g.cycles_intermediate == h.cycles_intermediate && g.max_cycles == h.max_cycles &&
+         g.precision == h.precision && g.omega == h.omega && g.tol_intermediate == h.tol_intermediate &&
+         g.switch_tol == h.switch_tol;
+}
+// Checks a state's structure against the problem; returns its header.
+StateHead parse_state(const bmg_problem* p, int k, const unsigned char* buf, size_t len) {
+  StateHead h;
+  if (!buf || len < sizeof(StateHead)) fail(BMG_ERR_INVALID_ARG, "state buffer too small");
+  std::memcpy(&h, buf, sizeof(h));
+  if (h.magic != kStateMagic || h.version != kStateVersion) fail(BMG_ERR_INVALID_ARG, "not a solver state");
+  if (h.k != k || h.L != p->L || h.level < 2 || h.level > p->L || h.n_f != p->meshOf(h.level).n ||
+      h.n_hist < 0 || h.n_info < 0 || h.n_info > 256 || h.cycle < 0 || h.total_cycles < 0)
+    fail(BMG_ERR_INVALID_ARG, "state of another problem, hierarchy or block size");
+  if (state_bytes(h) != len) fail(BMG_ERR_INVALID_ARG, "state size mismatch");
+  return h;
 }
 
 // The BFMG solve (Alg. 4) of one problem and shift on the workspace w and its stream.
 // Returns whether every wanted pair met tol; throws BmgException on errors.
 bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma, double tol,
                 const bmg_options& o, const double* X0, int x0_on_device, double* evals, double* evecs,
-                int evecs_on_device, double* resid, bmg_solve_info* info) {
+                int evecs_on_device, double* resid, bmg_solve_info* info,
+                const std::vector<unsigned char>* resume = nullptr, bool* stopped = nullptr) {
   const int L = p->L;
   const int n2 = p->meshOf(2).n, nL = p->meshOf(L).n;
   // the solve runs on the workspace's own non-blocking stream (capturable into CUDA
@@ -881,12 +928,6 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
     ensure_ops32(p);
     b32 = blocks32(p, w);
   }
-  // X0 -> X on level 2 (ld-strided; padding columns stay zero)
-  BMG_CUDA(cudaMemsetAsync(w.X.get(), 0, sizeof(double) * (size_t)n2 * ld, s));
-  BMG_CUDA(cudaMemcpy2DAsync(w.X.get(), sizeof(double) * ld, X0, sizeof(double) * k, sizeof(double) * k, n2,
-                             x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-  if (fp32) convert_block(w.X.get(), ld, b32.X, b32.ld, n2, k, s);
-
   CycleState cs;
   cs.rho.assign(k, 0.0);
   cs.lamv.assign(k, 0.0);
@@ -896,18 +937,98 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
   std::vector<double> hist;   // finest-level FP32 max residuals
   std::vector<int> hl, hp;     // per-cycle level and arithmetic (info history)
   std::vector<double> hr;      // per-cycle largest wanted residual
-  for (int f = 2; f <= L; ++f) {
+  int f0 = 2, c0 = 0, last_level = 0;
+  if (resume) {
+    // continue from a state: the iterate on its level, counters and history
+    const StateHead h = parse_state(p, k, resume->data(), resume->size());
+    if (h.n_wanted != n_wanted || h.sigma != sigma || h.tol != tol || !same_options(h, o))
+      fail(BMG_ERR_INVALID_ARG, "resume needs the n_wanted, sigma, tol and options of the stopped solve");
+    const unsigned char* q = resume->data() + sizeof(StateHead);
+    auto take = [&](void* dst, size_t bytes) { std::memcpy(dst, q, bytes); q += bytes; };
+    f0 = h.level;
+    c0 = h.cycle;
+    fp32 = h.fp32 != 0;
+    total_cycles = h.total_cycles;
+    fp32_cycles = h.fp32_cycles;
+    for (int f = 0; f <= L && f < 33; ++f) cyc[f] = h.cyc[f];
+    cs.max_dense_err = h.max_dense_err;
+    hist.resize(h.n_hist);
+    hl.resize(h.n_info);
+    hp.resize(h.n_info);
+    hr.resize(h.n_info);
+    take(hist.data(), sizeof(double) * h.n_hist);
+    take(hl.data(), sizeof(int32_t) * h.n_info);
+    take(hp.data(), sizeof(int32_t) * h.n_info);
+    take(hr.data(), sizeof(double) * h.n_info);
+    take(cs.lamv.data(), sizeof(double) * k);
+    take(cs.rho.data(), sizeof(double) * k);
+    BMG_CUDA(cudaMemsetAsync(w.X.get(), 0, sizeof(double) * (size_t)h.n_f * ld, s));
+    BMG_CUDA(cudaMemcpy2DAsync(w.X.get(), sizeof(double) * ld, q, sizeof(double) * k, sizeof(double) * k, h.n_f,
+                               cudaMemcpyHostToDevice, s));
+    if (fp32) convert_block(w.X.get(), ld, b32.X, b32.ld, h.n_f, k, s);
+  } else {
+    // X0 -> X on level 2 (ld-strided; padding columns stay zero)
+    BMG_CUDA(cudaMemsetAsync(w.X.get(), 0, sizeof(double) * (size_t)n2 * ld, s));
+    BMG_CUDA(cudaMemcpy2DAsync(w.X.get(), sizeof(double) * ld, X0, sizeof(double) * k, sizeof(double) * k, n2,
+                               x0_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    if (fp32) convert_block(w.X.get(), ld, b32.X, b32.ld, n2, k, s);
+  }
+  // keeps the state before cycle c on level f (the iterate is in the X block)
+  auto save_state = [&](int f, int c) {
+    StateHead h;
+    std::memset(&h, 0, sizeof(h));
+    h.magic = kStateMagic;
+    h.version = kStateVersion;
+    h.k = k; h.L = L; h.n_wanted = n_wanted; h.level = f; h.cycle = c; h.fp32 = fp32 ? 1 : 0;
+    h.total_cycles = total_cycles; h.fp32_cycles = fp32_cycles; h.n_f = p->meshOf(f).n;
+    h.n_hist = (int)hist.size(); h.n_info = (int)hr.size();
+    for (int j = 0; j <= L && j < 33; ++j) h.cyc[j] = cyc[j];
+    h.sigma = sigma; h.tol = tol; h.max_dense_err = cs.max_dense_err;
+    head_options(h, o);
+    std::vector<unsigned char> buf(state_bytes(h));
+    unsigned char* q = buf.data();
+    auto put = [&](const void* src, size_t bytes) { std::memcpy(q, src, bytes); q += bytes; };
+    put(&h, sizeof(h));
+    put(hist.data(), sizeof(double) * hist.size());
+    std::vector<int32_t> hl32(hl.begin(), hl.end()), hp32(hp.begin(), hp.end());
+    put(hl32.data(), sizeof(int32_t) * hl32.size());
+    put(hp32.data(), sizeof(int32_t) * hp32.size());
+    put(hr.data(), sizeof(double) * hr.size());
+    put(cs.lamv.data(), sizeof(double) * k);
+    put(cs.rho.data(), sizeof(double) * k);
+    if (fp32) {
+      std::vector<float> xf((size_t)h.n_f * k);
+      BMG_CUDA(cudaMemcpy2DAsync(xf.data(), sizeof(float) * k, b32.X, sizeof(float) * b32.ld, sizeof(float) * k,
+                                 h.n_f, cudaMemcpyDeviceToHost, s));
+      BMG_CUDA(cudaStreamSynchronize(s));
+      std::vector<double> xd(xf.begin(), xf.end());
+      put(xd.data(), sizeof(double) * xd.size());
+    } else {
+      BMG_CUDA(cudaMemcpy2DAsync(q, sizeof(double) * k, w.X.get(), sizeof(double) * ld, sizeof(double) * k, h.n_f,
+                                 cudaMemcpyDeviceToHost, s));
+      BMG_CUDA(cudaStreamSynchronize(s));
+    }
+    p->ckpt[k] = std::move(buf);
+  };
+  bool halted = false;
+  for (int f = f0; f <= L && !halted; ++f) {
     const Mesh& mf = p->meshOf(f);
-    if (f > 2) {
+    if (f > f0) {
       if (fp32) prolong<float>(mf, b32.U, b32.X, b32.ld, false, s);
       else prolong<double>(mf, b64.U, b64.X, ld, false, s);
     }
     const int budget = (f == L) ? o.max_cycles : o.cycles_intermediate;
     const double ftol = (f == L) ? tol : o.tol_intermediate;
-    for (int c = 0; c < budget; ++c) {
+    for (int c = (f == f0) ? c0 : 0; c < budget; ++c) {
+      if (o.stop_after_cycles > 0 && total_cycles >= o.stop_after_cycles) {
+        save_state(f, c);
+        halted = true;
+        break;
+      }
       const bool last = c + 1 == budget;
       const bool conv = fp32 ? run_cycle<float>(p, w, b32, f, o, sigma, k, n_wanted, ftol, last, cs)
                              : run_cycle<double>(p, w, b64, f, o, sigma, k, n_wanted, ftol, last, cs);
+      last_level = f;
       if (total_cycles < 256) {
         double mr = 0.0;
         for (int i = 0; i < n_wanted; ++i) mr = std::max(mr, cs.rho[i]);
@@ -933,12 +1054,15 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
         }
       }
     }
+    if (converged) break;
   }
-  // outputs: the last Ritz pairs on level L
-  if (fp32) convert_block(b32.U, b32.ld, w.U.get(), ld, nL, ld, s);
+  if (stopped) *stopped = halted;
+  // outputs: the last Ritz pairs (on level L unless the solve stopped before it)
+  const bool on_finest = last_level == L;
+  if (fp32 && on_finest) convert_block(b32.U, b32.ld, w.U.get(), ld, nL, ld, s);
   for (int i = 0; i < n_wanted; ++i) evals[i] = cs.lamv[i];
   if (resid) for (int i = 0; i < n_wanted; ++i) resid[i] = cs.rho[i];
-  if (evecs) {
+  if (evecs && on_finest) {
     BMG_CUDA(cudaMemcpy2DAsync(evecs, sizeof(double) * n_wanted, w.U.get(), sizeof(double) * ld,
                                sizeof(double) * n_wanted, nL,
                                evecs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -972,14 +1096,24 @@ extern "C" bmg_status bmg_solve(bmg_problem* p, int k, int n_wanted, double sigm
                                 const bmg_options* opt_in, const double* X0, int x0_on_device,
                                 double* evals, double* evecs, int evecs_on_device, double* resid,
                                 bmg_solve_info* info) {
-  bool converged = false;
+  bool converged = false, stopped = false;
   bmg_status st = guarded([&] {
     const bmg_options o = checked_options(p, k, n_wanted, sigma, tol, opt_in, X0, evals);
+    const std::vector<unsigned char>* state = nullptr;
+    if (o.resume) {
+      auto it = p->resume_state.find(k);
+      if (it == p->resume_state.end()) fail(BMG_ERR_STATE, "resume without a state (bmg_set_state)");
+      state = &it->second;
+    }
     SolveWork& w = workspace(p, k, 0, p->stream);
     converged = solve_impl(p, w, k, n_wanted, sigma, tol, o, X0, x0_on_device, evals, evecs, evecs_on_device,
-                           resid, info);
+                           resid, info, state, &stopped);
   });
   if (st != BMG_OK) return st;
+  if (stopped) {
+    set_error("stopped after stop_after_cycles cycles; state kept (bmg_get_state)");
+    return BMG_ERR_NOT_CONVERGED;
+  }
   if (!converged) {
     set_error("cycle cap reached before every wanted pair met tol");
     return BMG_ERR_NOT_CONVERGED;
@@ -997,6 +1131,8 @@ extern "C" bmg_status bmg_solve_batched(int n_jobs, bmg_problem* const* problems
     if (n_jobs < 1 || !problems || !sigmas || !X0 || !evals) fail(BMG_ERR_INVALID_ARG, "bad batch arrays");
     std::vector<bmg_options> opts(n_jobs);
     std::vector<int> slot(n_jobs, 0);
+    if (opt_in && (opt_in->stop_after_cycles != 0 || opt_in->resume != 0))
+      fail(BMG_ERR_INVALID_ARG, "stop_after_cycles and resume are for bmg_solve");
     for (int j = 0; j < n_jobs; ++j) {
       opts[j] = checked_options(problems[j], k, n_wanted, sigmas[j], tol, opt_in, X0[j], evals[j]);
       for (int q = 0; q < j; ++q) slot[j] += problems[q] == problems[j];
@@ -1105,5 +1241,28 @@ extern "C" bmg_status bmg_gram_f32(const float* X, const float* Y, int n, int k,
     DBuf<double> partial((size_t)parts * k * k);
     gram(X, Y, n, k, ld, G, partial.get(), parts, (cudaStream_t)stream);
     BMG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  });
+}
+
+extern "C" bmg_status bmg_get_state(const bmg_problem* p, int k, void* buf, size_t len, size_t* used) {
+  return guarded([&] {
+    if (!p) fail(BMG_ERR_INVALID_ARG, "null problem");
+    auto it = p->ckpt.find(k);
+    if (it == p->ckpt.end()) fail(BMG_ERR_STATE, "no stopped solve of this block size");
+    if (used) *used = it->second.size();
+    if (buf) {
+      if (len < it->second.size()) fail(BMG_ERR_INVALID_ARG, "state buffer too small");
+      std::memcpy(buf, it->second.data(), it->second.size());
+    }
+  });
+}
+
+extern "C" bmg_status bmg_set_state(bmg_problem* p, int k, const void* buf, size_t len) {
+  return guarded([&] {
+    if (!p) fail(BMG_ERR_INVALID_ARG, "null problem");
+    if (!p->L) fail(BMG_ERR_STATE, "bmg_hierarchy not called");
+    const unsigned char* b = static_cast<const unsigned char*>(buf);
+    parse_state(p, k, b, len);
+    p->resume_state[k].assign(b, b + len);
   });
 }

@@ -180,6 +180,8 @@ struct bmg_problem {
   // assembled matrices); built on the first precision-form call.
   std::vector<std::vector<bmg::OpSet32>> ops32;
   std::unique_ptr<bmg::SolveWork> ws;  // cached solve workspace (bmg_solve; batch slot 0)
+  // per block size k: state of the last stopped solve, and the state to resume from
+  std::map<int, std::vector<unsigned char>> ckpt, resume_state;
   std::vector<std::unique_ptr<bmg::SolveWork>> ws_more;  // batch slots 1, 2, ...
   bmg::Mesh& meshOf(int level) { return mesh[r0 + level - 1]; }
   const bmg::Mesh& meshOf(int level) const { return mesh[r0 + level - 1]; }

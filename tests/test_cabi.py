@@ -26,6 +26,7 @@ def test_default_options(bmg):
     o = bmg.options()
     assert (o.smoother, o.nu, o.form, o.cycles_intermediate, o.max_cycles) == (0, 2, 0, 6, 200)
     assert abs(o.omega - 2.0 / 3.0) < 1e-16
+    assert (o.stop_after_cycles, o.resume) == (0, 0)
 
 
 def test_argument_errors_are_reported_without_gpu(bmg):
@@ -43,4 +44,7 @@ def test_argument_errors_are_reported_without_gpu(bmg):
     assert bmg.LIB.bmg_solve(None, 4, 2, 0.0, 1e-8, None, None, 0, None, None, 0, None, None) == 1
     assert bmg.LIB.bmg_dense_eig(None, None, 4, 0.0, 2, None, None, None, None) == 1
     assert bmg.LIB.bmg_gram(None, None, 4, 2, 2, None, None) == 1
+    used = C.c_size_t(0)
+    assert bmg.LIB.bmg_get_state(None, 4, None, 0, C.byref(used)) == 1
+    assert bmg.LIB.bmg_set_state(None, 4, None, 0) == 1
     bmg.LIB.bmg_destroy(None)
