@@ -53,6 +53,7 @@ struct DW {
   // kept across calls: factor of the repeating leading block of M-hat (block form)
   double *qc, *qL, *qd, *qrl;      // block copy, L_Q (nq x nq), scaling, reciprocal pivots
   int *qperm, *qflag;              // pivot order; qflag[0] = 1 valid / 2 deficient, qflag[1] = nq
+  double* part;                    // per output tile of the G and S products: [tile][2] partial norms
 };
 
 // 1/x to about 1e-14 relative: an FP32 seed refined by one Newton-Raphson step
@@ -974,10 +975,11 @@ backtr_kernel(int n, DW w) {
 // Products of r x r matrices (stride n) with kTile x kTile output tiles; the A row
 // panel and the B column panel are staged whole in shared memory.
 //   bmode 0: B read from memory;  2: B = E read from memory.  With addD: C = D + op(A) B.
-//   acc_mode 1 (the G product): accumulate ||I - G||_F^2 into acc[1];
-//   acc_mode 2 (the S product): store lam_i = s_ii / (2 - g_ii), accumulate
-//   ||S - diag(lam)||_F^2 into acc[0] and max |lam| into acc[2] (as the bits of a
-//   non-negative double).
+//   acc_mode 1 (the G product): the tile's part of ||I - G||_F^2 into part[tile][0];
+//   acc_mode 2 (the S product): store lam_i = s_ii / (2 - g_ii), the tile's part of
+//   ||S - diag(lam)||_F^2 into part[tile][1], and max |lam| into acc[2] (as the bits
+//   of a non-negative double; a max is order-independent).  The norms are summed by
+//   their readers in a fixed order (part_sums), so results repeat bit for bit.
 //   Both accumulating products are symmetric (W^T W and W^T T W): only the tiles on
 //   and above the diagonal are formed, each written to both halves.
 // Asynchronous global-to-shared copy of one double (zero-filled when !valid; src is
@@ -993,19 +995,41 @@ struct GemmJob {
   const double* A; const double* B; double* C; const double* D;
   int ta, bmode, addD, acc_mode;
 };
-__device__ __forceinline__ double thr_from(const double* acc, double floor_rel) {
-  const double amax = __longlong_as_double((long long)((const unsigned long long*)acc)[2]);
-  return fmax(2.0 * (sqrt(acc[0]) + amax * sqrt(acc[1])), floor_rel * amax);
+__device__ __forceinline__ double acc_max(const double* acc) {
+  return __longlong_as_double((long long)((const unsigned long long*)acc)[2]);
+}
+// ||S - diag||_F^2 (x) and ||I - G||_F^2 (y) from the tiles' parts of the last G and S
+// products, in a fixed order by the whole block (every thread gets them).
+__device__ double2 part_sums(const double* part, int n, double* red) {
+  const int nt = (n + kTile - 1) / kTile, ns = nt * nt;
+  double g = 0.0, sv = 0.0;
+  for (int t = threadIdx.x; t < ns; t += blockDim.x) {
+    g += part[2 * t];
+    sv += part[2 * t + 1];
+  }
+  g = block_sum<double>(g, red);
+  sv = block_sum<double>(sv, red);
+  return make_double2(sv, g);
+}
+__device__ __forceinline__ double thr_from(double2 nrm, double amax, double floor_rel) {
+  return fmax(2.0 * (sqrt(nrm.x) + amax * sqrt(nrm.y)), floor_rel * amax);
 }
 __global__ void __launch_bounds__(kTile * kTile)
 gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc) {
   extern __shared__ double gsm[];
   __shared__ double red[2][2];
   const GemmJob jb = blockIdx.z == 0 ? j0 : j1;
-  if (jb.acc_mode && blockIdx.y > blockIdx.x) return;
+  double* mypart = w.part + 2 * (blockIdx.y * gridDim.x + blockIdx.x) + (jb.acc_mode == 1 ? 0 : 1);
+  if (jb.acc_mode && blockIdx.y > blockIdx.x) {
+    if (threadIdx.x == 0) *mypart = 0.0;
+    return;
+  }
   const int r = *w.rank;
   const int row0 = blockIdx.y * kTile, col0 = blockIdx.x * kTile;
-  if (row0 >= r || col0 >= r) return;
+  if (row0 >= r || col0 >= r) {
+    if (jb.acc_mode && threadIdx.x == 0) *mypart = 0.0;
+    return;
+  }
   double* As = gsm;                 // kTile x r
   double* Bs = gsm + kTile * r;     // r x kTile
   const int tid = threadIdx.x;
@@ -1091,12 +1115,9 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc) {
       double s0 = red[0][0] + red[1][0];
       const double s1 = fmax(red[0][1], red[1][1]);
       if (offdiag) s0 *= 2.0;   // the mirrored tile
-      if (jb.acc_mode == 1) {
-        atomicAdd(acc + 1, s0);
-      } else {
-        atomicAdd(acc + 0, s0);
+      *mypart = s0;
+      if (jb.acc_mode == 2)
         atomicMax((unsigned long long*)(acc + 2), (unsigned long long)__double_as_longlong(s1));
-      }
     }
   }
 }
@@ -1107,9 +1128,10 @@ gemm_kernel(GemmJob j0, GemmJob j1, int n, DW w, double* acc) {
 // threshold (if below the guard), r_ij / 2 otherwise.  One thread per entry.
 __global__ void __launch_bounds__(256)
 e_kernel(int n, const double* acc, double floor_rel, DW w) {
-  __shared__ double s_thr;
+  __shared__ double s_thr, red[32];
   const int r = *w.rank;
-  if (threadIdx.x == 0) s_thr = thr_from(acc, floor_rel);
+  const double2 nrm = part_sums(w.part, n, red);
+  if (threadIdx.x == 0) s_thr = thr_from(nrm, acc_max(acc), floor_rel);
   __syncthreads();
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= r * r) return;
@@ -1143,11 +1165,12 @@ __global__ void __launch_bounds__(kBig)
 coeff_kernel(int n, const double* acc, double floor_rel, DW w) {
   __shared__ double sl[kMaxN], ss[kMaxN];
   __shared__ int srt[kMaxN];
-  __shared__ double s_thr;
+  __shared__ double s_thr, red[32];
   const int r = *w.rank;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = kBig / 32;
-  if (tid == 0) s_thr = thr_from(acc, floor_rel);
+  const double2 nrm = part_sums(w.part, n, red);
+  if (tid == 0) s_thr = thr_from(nrm, acc_max(acc), floor_rel);
   for (int i = tid; i < r; i += kBig) sl[i] = w.lam[i];
   for (int i = wid; i < r; i += nwarps)
     for (int j = lane; j < r; j += 32) w.E[i * n + j] = (i == j) ? 0.5 * (1.0 - w.G[i * n + i]) : 0.0;
@@ -1378,9 +1401,11 @@ cluster_kernel(int n, DW w) {
 __global__ void select_kernel(int k, int n, const double* acc, DW w, double* __restrict__ theta) {
   const int r = *w.rank;
   for (int c = threadIdx.x; c < k; c += blockDim.x) w.order[c] = 0;   // rank < k: stays in bounds
+  __shared__ double red[32];
+  const double2 nrm = part_sums(w.part, n, red);
   if (threadIdx.x == 0) {
-    const double amax = __longlong_as_double((long long)((const unsigned long long*)acc)[2]);
-    w.misc[1] = (amax > 0.0) ? sqrt(acc[0]) / amax + sqrt(acc[1]) : sqrt(acc[1]);
+    const double amax = acc_max(acc);
+    w.misc[1] = (amax > 0.0) ? sqrt(nrm.x) / amax + sqrt(nrm.y) : sqrt(nrm.y);
   }
   __syncthreads();
   // order by (|lam|, lam, index) through integer keys: the magnitude's bits, then a
@@ -1500,6 +1525,7 @@ DW carve(double* work, int n) {
   w.qrl = p; p += n;
   w.qperm = reinterpret_cast<int*>(p); p += n / 2 + 1;
   w.qflag = reinterpret_cast<int*>(p); p += 1;
+  w.part = p; p += 2 * (size_t)((n + kTile - 1) / kTile) * ((n + kTile - 1) / kTile);
   return w;
 }
 
@@ -1553,7 +1579,7 @@ void backsub(int n, int k, const DW& w, double* Y, cudaStream_t s) {
 size_t dense_work_doubles(int n) {
   const size_t nn = (size_t)n * n;
   return 11 * nn + 3 * (size_t)n + 48 + (nn + n) / 2 + 1 + (nn / 2 + 1) + (5 * nn + 1) / 2 + 1 + (3 * (size_t)n + 5) / 2 + 1 + ((size_t)n + 3) / 2 + 1 + 4 * ((size_t)n / 2 + 2) + 1 + 16 +
-         2 * nn + 2 * (size_t)n + (size_t)n / 2 + 2;
+         2 * nn + 2 * (size_t)n + (size_t)n / 2 + 2 + 2 * (size_t)((n + kTile - 1) / kTile) * ((n + kTile - 1) / kTile);
 }
 
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k, double* theta,
