@@ -53,6 +53,20 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def whole_job(ms_total, e2e_s, conv, e2e_conv, dist=None, device="cpu"):
+    """Whole-job figures over the replicas: the slowest rank's device time and end-to-end
+    wall time (max over ranks) and the converged pairs of all ranks (sum).  Returns
+    (ms_max, e2e_max_s, pairs/s, end-to-end pairs/s)."""
+    import torch
+    tmax = torch.tensor([ms_total, e2e_s], dtype=torch.float64, device=device)
+    csum = torch.tensor([conv, e2e_conv], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(csum, op=dist.ReduceOp.SUM)
+    ms_max, e2e_max = float(tmax[0]), float(tmax[1])
+    return ms_max, e2e_max, float(csum[0]) / (ms_max * 1e-3), float(csum[1]) / e2e_max
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -372,14 +386,7 @@ def run_ours(args):
         e2e_total += time.perf_counter() - ta
         e2e_conv += int((rs <= CONV_TOL).sum())
 
-    tmax = torch.tensor([ms_total, e2e_total], dtype=torch.float64, device=dev)
-    csum = torch.tensor([conv_total, e2e_conv], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(csum, op=dist.ReduceOp.SUM)
-    ms_max, e2e_max = float(tmax[0]), float(tmax[1])
-    value = float(csum[0]) / (ms_max * 1e-3)
-    e2e_value = float(csum[1]) / e2e_max
+    ms_max, e2e_max, value, e2e_value = whole_job(ms_total, e2e_total, conv_total, e2e_conv, dist, dev)
     hbm_peak, peak_kind = load_peaks()
     roof, dom = dominant_roofline(prof, hbm_peak, peak_kind)
     smoother_spmm = class_gbs(prof, ["spmm_am", "smooth_sweep"])
