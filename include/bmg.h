@@ -282,7 +282,9 @@ bmg_status bmg_gram_f32(const float* X, const float* Y, int n, int k, int ld, do
  * (Ahat - sigma Mhat) y = theta Mhat y, n x n row-major device matrices (n <= 224):
  * Mhat is scaled to unit diagonal, reduced by a Cholesky factorisation with
  * diagonal pivoting that drops pivots below 1e-12 (rank-deficient enriched
- * spaces), and the reduced standard problem is solved (Alg. 2 step 4).
+ * spaces), and the reduced standard problem is solved (Alg. 2 step 4): an FP32
+ * tridiagonal start refined to FP64 accuracy.  (bmg_solve factors the enriched
+ * Mhat in block form, reusing the factor of its coarse-space block.)
  * theta [k], Y [n][k] device; Y^T Mhat Y = I.  rank_out (device int or NULL)
  * receives the kept rank.  Errors: BMG_ERR_INVALID_ARG; a rank below k is
  * reported through bmg_solve as BMG_ERR_SINGULAR.                               */

@@ -2,28 +2,32 @@
 // the k pairs of (Ahat - sigma Mhat) y = theta Mhat y with smallest |theta|, for the
 // block matrices of Sec. 4.1 (size n = N_1 + k <= 224).
 //
-// GB300 executes FP64 at about 1/70 of its FP32 rate and a single CTA is bound by the
-// latency of its dependent steps, so the solve is organised around few steps:
-//   1. basis_kernel    [1 CTA, FP64]  the b_h-orthogonalisation of Alg. 2 step 3: Mhat
-//      scaled to unit diagonal, Cholesky with diagonal pivoting in shared memory;
-//      pivots below kDropTol mark basis vectors already in the span of the others,
-//      which are dropped (rank r).
+// GB300 executes FP64 at about 1/70 of its FP32 rate, and a single CTA is bound by the
+// latency of its dependent steps, so the solve keeps FP64 off its sequential chains
+// and spreads FP64 products over the SMs:
+//   1. basis          the b_h-orthogonalisation of Alg. 2 step 3: Mhat scaled to unit
+//      diagonal and factored by Cholesky with diagonal pivoting; pivots below the drop
+//      tolerance mark basis vectors already in the span of the others, which are
+//      dropped (rank r).  basis_kernel [1 CTA] factors the whole of Mhat; the block
+//      form (qfactor_kernel, xsolve_kernel, schur_kernel, xfactor_kernel) keeps the
+//      factor of a repeating leading block and factors the Schur complement of the
+//      new columns.
 //   2. trsm_kernel     [multi-CTA, FP64]  reduced standard matrix
 //      T = L^{-1} D P^T (Ahat - sigma Mhat) P D L^{-T}: two forward substitutions, one
 //      warp per column, L staged in shared memory.
-//   3. eig32_kernel    [1 CTA, FP32]  Householder tridiagonalisation of T, bisection
-//      on Sturm counts for all eigenvalues, inverse iteration (with modified
-//      Gram-Schmidt inside clusters of close eigenvalues) for the eigenvectors, and
-//      the back-transformation, each column owned by one warp.
+//   3. FP32 start: eig32_kernel [1 CTA] Householder tridiagonalisation of sym(T) and
+//      multisection on Sturm counts for all eigenvalues; invit_kernel [one CTA per
+//      cluster] inverse iteration with Gram-Schmidt inside clusters of close
+//      eigenvalues; backtr_kernel [multi-CTA] the back-transformation.
 //   4. refinement      [multi-CTA, FP64]  the eigenvectors W are refined to FP64
 //      accuracy by the iterative scheme of Ogita & Aishima (2018):
 //          G = W^T W, R = I - G, S = W^T T W, lt_i = s_ii / (1 - r_ii),
 //          E_ij = (s_ij + lt_j r_ij) / (lt_j - lt_i) for well separated pairs,
 //          r_ij / 2 otherwise,   W <- W (I + E);
 //      P = T W is carried along as P <- P (I + E), so a step is three launches (E,
-//      the two updates, G and S);
-//      clusters of nearly equal values are diagonalised exactly (FP64 Jacobi on the
-//      cluster block, one CTA per cluster) once the separated pairs converged.
+//      the two updates, G and S); in the cluster step the groups of nearly equal
+//      values are diagonalised (FP32 Jacobi, Newton-Schulz, FP64 Jacobi polish; one
+//      CTA per cluster).
 //   5. select / backsub  the k smallest |theta|; Y = D P L^{-T} W_sel.
 #include <algorithm>
 #include <cmath>
