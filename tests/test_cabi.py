@@ -1,6 +1,7 @@
 """Host-side checks of the C-ABI library: it loads, exports every declared symbol,
 and validates arguments before touching the GPU."""
 import ctypes as C
+import os
 
 import numpy as np
 import pytest
@@ -48,3 +49,32 @@ def test_argument_errors_are_reported_without_gpu(bmg):
     assert bmg.LIB.bmg_get_state(None, 4, None, 0, C.byref(used)) == 1
     assert bmg.LIB.bmg_set_state(None, 4, None, 0) == 1
     bmg.LIB.bmg_destroy(None)
+
+
+def test_struct_layouts_match_the_header(bmg, tmp_path):
+    """The ctypes mirrors of bmg_options and bmg_solve_info have the C layout: every
+    field's offset and the struct sizes, compiled from include/bmg.h by the host C
+    compiler."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = {"bmg_options": bmg.Options, "bmg_solve_info": bmg.SolveInfo}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "bmg.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    out = dict(l.split() for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                  check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(out[cname]) == C.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(out["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
