@@ -943,6 +943,8 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
     const StateHead h = parse_state(p, k, resume->data(), resume->size());
     if (h.n_wanted != n_wanted || h.sigma != sigma || h.tol != tol || !same_options(h, o))
       fail(BMG_ERR_INVALID_ARG, "resume needs the n_wanted, sigma, tol and options of the stopped solve");
+    if (h.cycle >= ((h.level == L) ? o.max_cycles : o.cycles_intermediate))
+      fail(BMG_ERR_INVALID_ARG, "state past the cycle budget of its level");
     const unsigned char* q = resume->data() + sizeof(StateHead);
     auto take = [&](void* dst, size_t bytes) { std::memcpy(dst, q, bytes); q += bytes; };
     f0 = h.level;
