@@ -127,6 +127,7 @@ extern "C" bmg_status bmg_assemble(const double* verts, int n_verts, const int* 
                                    int refinements, double amplitude, const double* sh_coefs,
                                    void* stream, bmg_problem** out) {
   return guarded([&] {
+    TraceRange trace("bmg_assemble");
     if (!out) fail(BMG_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!verts || !tris || n_verts < 4 || n_tris < 4) fail(BMG_ERR_INVALID_ARG, "empty or null mesh");
@@ -175,6 +176,7 @@ extern "C" bmg_status bmg_assemble(const double* verts, int n_verts, const int* 
 
 extern "C" bmg_status bmg_hierarchy(bmg_problem* p, int levels) {
   return guarded([&] {
+    TraceRange trace("bmg_hierarchy");
     if (!p) fail(BMG_ERR_INVALID_ARG, "null problem");
     if (levels < 2 || levels > p->R) fail(BMG_ERR_INVALID_ARG, "levels must be in 2..refinements");
     if (p->L) fail(BMG_ERR_STATE, "hierarchy already built");
@@ -774,7 +776,10 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
     BMG_CUDA(cudaMemcpyAsync(hint, w.rank.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
     BMG_CUDA(cudaMemcpyAsync(hqual, w.dquality.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
   };
-  run_graph(p, w, std::make_tuple(0, f, (int)sizeof(T), 0), part_a);
+  {
+    TraceRange trace("cycle: products, Rayleigh-Ritz, Ritz vectors, residuals");
+    run_graph(p, w, std::make_tuple(0, f, (int)sizeof(T), 0), part_a);
+  }
   BMG_CUDA(cudaStreamSynchronize(s));
   if (hint[0] < k) fail(BMG_ERR_SINGULAR, "enriched space rank " + std::to_string(hint[0]) + " < k");
   if (!(*hqual <= 1e-6))
@@ -827,7 +832,10 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
       prolong<T>(mf, b.cB[f - 1], b.X, ld, true, s);
     }
   };
-  run_graph(p, w, std::make_tuple(1, f, (int)sizeof(T), (int)legs.size()), part_b);
+  {
+    TraceRange trace("cycle: smoothing and down-leg");
+    run_graph(p, w, std::make_tuple(1, f, (int)sizeof(T), (int)legs.size()), part_b);
+  }
   return false;
 }
 // Argument checks shared by bmg_solve and bmg_solve_batched.
@@ -900,6 +908,7 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
                 const bmg_options& o, const double* X0, int x0_on_device, double* evals, double* evecs,
                 int evecs_on_device, double* resid, bmg_solve_info* info,
                 const std::vector<unsigned char>* resume = nullptr, bool* stopped = nullptr) {
+  TraceRange trace("bmg_solve");
   const int L = p->L;
   const int n2 = p->meshOf(2).n, nL = p->meshOf(L).n;
   // the solve runs on the workspace's own non-blocking stream (capturable into CUDA
@@ -1014,6 +1023,9 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
   };
   bool halted = false;
   for (int f = f0; f <= L && !halted; ++f) {
+    static const char* const kLevelNames[] = {"level 0", "level 1", "level 2", "level 3", "level 4", "level 5",
+                                              "level 6", "level 7", "level 8", "level 9", "level 10"};
+    TraceRange trace_level(kLevelNames[f <= 10 ? f : 10]);
     const Mesh& mf = p->meshOf(f);
     if (f > f0) {
       if (fp32) prolong<float>(mf, b32.U, b32.X, b32.ld, false, s);

@@ -11,12 +11,23 @@
 #include <vector>
 
 #include "../../include/bmg.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace bmg {
 
 // ---------------------------------------------------------------- errors ----
 void set_error(const std::string& msg);
 // Thrown by fail(); every extern "C" entry catches it and returns its code.
+// Host-side trace range (NVTX, header-only): the phases of set-up and solve (assembly,
+// hierarchy, levels, the two halves of a cycle, the enriched eigensolve) appear on a
+// profiler's timeline; without an attached tool a push or pop is one pointer check.
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+
 struct BmgException {
   bmg_status code;
   std::string msg;

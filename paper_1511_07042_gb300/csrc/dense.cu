@@ -1589,6 +1589,7 @@ size_t dense_work_doubles(int n) {
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k, double* theta,
                double* Y, int* rank, double* work, double* quality, double drop_tol, int nq, cudaStream_t s) {
   if (n < 1 || n > kMaxDense || k < 1 || k > n) fail(BMG_ERR_INVALID_ARG, "dense_eig: need 1 <= k <= n <= 224");
+  TraceRange trace("enriched eigensolve");
   prof_begin(KC_DENSE, s);
   DW w = carve(work, n);
   // 1. basis: whole pivoted factorisation, or the block form when the leading nq x nq
