@@ -47,7 +47,8 @@ typedef enum {
   BMG_ERR_NOT_CONVERGED = 5, /* cycle cap reached; best pairs are returned       */
   BMG_ERR_NONFINITE = 6,     /* NaN/Inf met in the iteration                     */
   BMG_ERR_MESH = 7,          /* input mesh not a closed manifold triangulation   */
-  BMG_ERR_STATE = 8          /* call order violated (e.g. solve before hierarchy)*/
+  BMG_ERR_STATE = 8,         /* call order violated (e.g. solve before hierarchy)*/
+  BMG_ERR_TIMEOUT = 9        /* a bounded wait inside a kernel expired           */
 } bmg_status;
 
 typedef enum { BMG_SMOOTH_JACOBI = 0, BMG_SMOOTH_MCGS = 1, BMG_SMOOTH_MCSGS = 2 } bmg_smoother;
@@ -85,12 +86,20 @@ typedef struct {
   int stop_after_cycles;     /* > 0: stop before cycle stop_after_cycles + 1 and   */
                              /*      keep the state (checkpoint, see below)        */
   int resume;                /* 1: continue from the state given to bmg_set_state  */
+  int tensor_cores;          /* 1: the Gram products and the Ritz-vector expansion */
+                             /*    run on the tcgen05 tensor cores from exact digit */
+                             /*    slices (k <= 128; see bmg_gram_tc), 0: float64  */
+                             /*    (float32) fused multiply-adds on the CUDA cores  */
+  int autotune;              /* 1: row-kernel shapes timed on first use, 0: default */
+  int graphs;                /* 1: cycles replayed as CUDA graphs, 0: eager launches*/
 } bmg_options;
 
 /* Fills the defaults: Jacobi, nu=2, omega=2/3, shifted form, full depth,
  * 6 intermediate cycles, no intermediate tolerance, 200 finest cycles, float64,
  * switch_tol 1e-7 (near the float32 floor of the relative residual), no stop,
- * no resume.                                                                     */
+ * no resume, tensor cores, autotuned shapes and CUDA graphs on.  autotune and
+ * graphs change no result (the tests check bit-identical outputs); tensor_cores
+ * changes the rounding of the products.                                          */
 void bmg_default_options(bmg_options* opt);
 
 typedef struct bmg_problem bmg_problem;
@@ -278,6 +287,32 @@ bmg_status bmg_gram(const double* X, const double* Y, int n, int k, int ld, doub
 bmg_status bmg_gram_f32(const float* X, const float* Y, int n, int k, int ld, double* G,
                         void* stream);
 
+/* The Rayleigh-Ritz block products of Sec. 4.1 (G = X^T Y, same arguments and
+ * result as bmg_gram / bmg_gram_f32) on the tcgen05 tensor cores, 1 <= k <= 128.
+ * Each value is turned into an integer relative to the largest exponent of its
+ * column over a window of 128 rows and cut into balanced 7-bit digits (BF16 values
+ * exactly); the digit products are summed exactly in float32 tensor memory and
+ * combined in int64, so only the digit pairs left out and the rounding of the
+ * integers contribute error: below 2^-53 (float64 blocks, 8 digits, 36 pairs) or
+ * 2^-33 (float32 blocks, 5 digits, 15 pairs) of 128 max|x| max|y| per window.
+ * Synchronous.  BMG_ERR_TIMEOUT if a bounded wait inside the kernel expired.     */
+bmg_status bmg_gram_tc(const double* X, const double* Y, int n, int k, int ld, double* G,
+                       void* stream);
+bmg_status bmg_gram_tc_f32(const float* X, const float* Y, int n, int k, int ld, double* G,
+                           void* stream);
+
+/* Ritz vectors in the enriched space V_{h1} + span X (Alg. 2 step 4; Alg. 3
+ * step 5): U = Z + X Yx for X, Z, U [n][ld] device blocks (Z may be NULL: U = X Yx)
+ * and Yx [k][ldy] device float64 coefficients; columns k..ld-1 of U are set to
+ * those of Z (zero without Z).  tensor_cores = 0: float64 (or float32) fused
+ * multiply-adds on the CUDA cores; 1: digit products on the tcgen05 tensor cores
+ * with the digits and error of bmg_gram_tc, scaled per row of X and per column of
+ * Yx (k <= 128).  Synchronous.  The f32 form takes float32 blocks (ld % 4 == 0).  */
+bmg_status bmg_expand(const double* Z, const double* X, const double* Yx, int n, int k, int ld,
+                      int ldy, double* U, int tensor_cores, void* stream);
+bmg_status bmg_expand_f32(const float* Z, const float* X, const double* Yx, int n, int k,
+                          int ld, int ldy, float* U, int tensor_cores, void* stream);
+
 /* Smallest-|theta| k eigenpairs of the symmetric-semidefinite pencil
  * (Ahat - sigma Mhat) y = theta Mhat y, n x n row-major device matrices (n <= 224):
  * Mhat is scaled to unit diagonal, reduced by a Cholesky factorisation with
@@ -321,7 +356,7 @@ const char* bmg_kernel_class_name(int cls);
 /* Row-kernel shapes chosen by the autotuner so far (SpMM, Jacobi and residual
  * kernels: lanes per row, 16-byte chunks per lane and warps per block, picked per
  * arithmetic, block width and row count by timing the candidates on first use;
- * environment BMG_AUTOTUNE=0 keeps the default shape).  Writes at most len-1 bytes
+ * bmg_options.autotune = 0 keeps the default shape).  Writes at most len-1 bytes
  * of text and a terminating zero into buf; returns the full length.               */
 int bmg_autotune_report(char* buf, int len);
 /* Number of kernels libbmg has launched in this process.                         */

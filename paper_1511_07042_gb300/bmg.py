@@ -22,7 +22,7 @@ FORMS = {"shifted": 0, "homogeneous": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 STATUS = {0: "BMG_OK", 1: "BMG_ERR_INVALID_ARG", 2: "BMG_ERR_CUDA", 3: "BMG_ERR_OOM",
           4: "BMG_ERR_SINGULAR", 5: "BMG_ERR_NOT_CONVERGED", 6: "BMG_ERR_NONFINITE",
-          7: "BMG_ERR_MESH", 8: "BMG_ERR_STATE"}
+          7: "BMG_ERR_MESH", 8: "BMG_ERR_STATE", 9: "BMG_ERR_TIMEOUT"}
 
 
 class BmgError(RuntimeError):
@@ -35,7 +35,8 @@ class Options(C.Structure):
     _fields_ = [("smoother", C.c_int), ("nu", C.c_int), ("omega", C.c_double), ("form", C.c_int),
                 ("vcycle_depth", C.c_int), ("cycles_intermediate", C.c_int),
                 ("tol_intermediate", C.c_double), ("max_cycles", C.c_int), ("precision", C.c_int),
-                ("switch_tol", C.c_double), ("stop_after_cycles", C.c_int), ("resume", C.c_int)]
+                ("switch_tol", C.c_double), ("stop_after_cycles", C.c_int), ("resume", C.c_int),
+                ("tensor_cores", C.c_int), ("autotune", C.c_int), ("graphs", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -80,6 +81,10 @@ def _load():
         "bmg_restrict": (i, [vp, i, vp, vp, i, i, vp]),
         "bmg_gram": (i, [vp, vp, i, i, i, vp, vp]),
         "bmg_gram_noalloc": (i, [vp, vp, i, i, i, vp, vp]),
+        "bmg_gram_tc": (i, [vp, vp, i, i, i, vp, vp]),
+        "bmg_gram_tc_f32": (i, [vp, vp, i, i, i, vp, vp]),
+        "bmg_expand": (i, [vp, vp, vp, i, i, i, i, vp, i, vp]),
+        "bmg_expand_f32": (i, [vp, vp, vp, i, i, i, i, vp, i, vp]),
         "bmg_dense_eig": (i, [vp, vp, i, d, i, vp, vp, vp, vp]),
         "bmg_profile_enable": (i, [i]),
         "bmg_profile_reset": (i, []),
@@ -130,7 +135,8 @@ def _stream():
 
 def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_depth=99,
             cycles_intermediate=6, tol_intermediate=-1.0, max_cycles=200, precision="fp64",
-            switch_tol=1e-7, stop_after_cycles=0, resume=False) -> Options:
+            switch_tol=1e-7, stop_after_cycles=0, resume=False, tensor_cores=True, autotune=True,
+            graphs=True) -> Options:
     o = Options()
     LIB.bmg_default_options(C.byref(o))
     o.smoother = SMOOTHERS[smoother]
@@ -145,6 +151,9 @@ def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_dep
     o.switch_tol = switch_tol
     o.stop_after_cycles = stop_after_cycles
     o.resume = int(bool(resume))
+    o.tensor_cores = int(bool(tensor_cores))
+    o.autotune = int(bool(autotune))
+    o.graphs = int(bool(graphs))
     return o
 
 
@@ -361,6 +370,23 @@ def gram(X, Y, k, G):
 def gram_f32(X, Y, k, G):
     """G (float64) = X^T Y for float32 blocks, compensated accumulation."""
     _check(LIB.bmg_gram_f32(_ptr(X), _ptr(Y), X.shape[0], k, X.shape[1], _ptr(G), _stream()))
+
+
+def gram_tc(X, Y, k, G):
+    """G = X^T Y on the tensor cores (exact BF16 digit products; k <= 128)."""
+    _check(LIB.bmg_gram_tc(_ptr(X), _ptr(Y), X.shape[0], k, X.shape[1], _ptr(G), _stream()))
+
+
+def gram_tc_f32(X, Y, k, G):
+    """G (float64) = X^T Y for float32 blocks on the tensor cores (k <= 128)."""
+    _check(LIB.bmg_gram_tc_f32(_ptr(X), _ptr(Y), X.shape[0], k, X.shape[1], _ptr(G), _stream()))
+
+
+def expand(Z, X, Yx, k, U, tensor_cores=True):
+    """U = Z + X Yx (Z may be None) for [n][ld] blocks; Yx float64 [k][ldy]."""
+    fn = LIB.bmg_expand if X.dtype.itemsize == 8 else LIB.bmg_expand_f32
+    _check(fn(_ptr(Z), _ptr(X), _ptr(Yx), X.shape[0], k, X.shape[1], Yx.shape[1], _ptr(U),
+              int(bool(tensor_cores)), _stream()))
 
 
 def gram_noalloc(X, Y, k, G):

@@ -114,6 +114,9 @@ extern "C" void bmg_default_options(bmg_options* o) {
   o->switch_tol = 1e-7;
   o->stop_after_cycles = 0;
   o->resume = 0;
+  o->tensor_cores = 1;
+  o->autotune = 1;
+  o->graphs = 1;
 }
 
 extern "C" const char* bmg_last_error(void) { return g_last_error.c_str(); }
@@ -360,6 +363,70 @@ extern "C" bmg_status bmg_gram(const double* X, const double* Y, int n, int k, i
   });
 }
 
+// Reads a device error flag raised by a tensor-core kernel after the stream is idle.
+static void check_tc_flag(const int* flag, cudaStream_t s) {
+  int h = 0;
+  BMG_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaStreamSynchronize(s));
+  if (h) fail(BMG_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel expired");
+}
+
+template <typename T>
+static void gram_tc_entry(const T* X, const T* Y, int n, int k, int ld, double* G, void* stream) {
+  if (!X || !Y || !G || n < 1 || k < 1 || k > kTcMaxK || ld < k)
+    fail(BMG_ERR_INVALID_ARG, "bad gram arguments (1 <= k <= 128, ld >= k)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int parts = gram_tc_parts(n, k);
+  DBuf<double> partial((size_t)parts * k * k);
+  DBuf<int> flag(1);
+  BMG_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int), s));
+  gram_tc(X, Y, n, k, ld, G, partial.get(), parts, flag.get(), s, false);
+  check_tc_flag(flag.get(), s);
+}
+
+extern "C" bmg_status bmg_gram_tc(const double* X, const double* Y, int n, int k, int ld, double* G, void* stream) {
+  return guarded([&] { gram_tc_entry(X, Y, n, k, ld, G, stream); });
+}
+
+extern "C" bmg_status bmg_gram_tc_f32(const float* X, const float* Y, int n, int k, int ld, double* G,
+                                      void* stream) {
+  return guarded([&] {
+    if (ld & 3) fail(BMG_ERR_INVALID_ARG, "bad gram arguments (ld % 4 == 0)");
+    gram_tc_entry(X, Y, n, k, ld, G, stream);
+  });
+}
+
+template <typename T>
+static void expand_entry(const T* Z, const T* X, const double* Yx, int n, int k, int ld, int ldy, T* U,
+                         int tensor_cores, void* stream) {
+  const int align = sizeof(T) == 8 ? 2 : 4;
+  if (!X || !Yx || !U || n < 1 || k < 1 || ld < k || ld % align || ldy < k)
+    fail(BMG_ERR_INVALID_ARG, "bad expand arguments");
+  if (k > 160) fail(BMG_ERR_INVALID_ARG, "expand: k <= 160");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (tensor_cores) {
+    if (k > kTcMaxK) fail(BMG_ERR_INVALID_ARG, "tensor-core expand: k <= 128");
+    DBuf<unsigned char> scratch(expand_tc_scratch_bytes(k));
+    DBuf<int> flag(1);
+    BMG_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int), s));
+    expand_tc(Z, X, Yx, n, k, ld, ldy, U, scratch.get(), flag.get(), s);
+    check_tc_flag(flag.get(), s);
+  } else {
+    expand<T>(Z, X, Yx, n, k, ld, ldy, U, s);
+    BMG_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
+extern "C" bmg_status bmg_expand(const double* Z, const double* X, const double* Yx, int n, int k, int ld, int ldy,
+                                 double* U, int tensor_cores, void* stream) {
+  return guarded([&] { expand_entry(Z, X, Yx, n, k, ld, ldy, U, tensor_cores, stream); });
+}
+
+extern "C" bmg_status bmg_expand_f32(const float* Z, const float* X, const double* Yx, int n, int k, int ld,
+                                     int ldy, float* U, int tensor_cores, void* stream) {
+  return guarded([&] { expand_entry(Z, X, Yx, n, k, ld, ldy, U, tensor_cores, stream); });
+}
+
 extern "C" bmg_status bmg_dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k,
                                     double* theta, double* Y, int* rank_out, void* stream) {
   return guarded([&] {
@@ -604,8 +671,13 @@ std::unique_ptr<SolveWork> make_work(bmg_problem* p, int k, cudaStream_t s) {
   w.GM.alloc((size_t)k * k);
   w.dense.alloc(dense_work_doubles(w.nh));
   BMG_CUDA(cudaMemsetAsync(w.dense.get(), 0, sizeof(double) * dense_work_doubles(w.nh), s));
-  w.parts = gram_parts(nL);
+  w.parts = std::max(gram_parts(nL), gram_tc_parts(nL, std::min(k, kTcMaxK)));
   w.partial.alloc((size_t)w.parts * std::max(k * k, 2 * k));
+  if (k <= kTcMaxK) {
+    w.tcscratch.alloc(expand_tc_scratch_bytes(k));
+    w.tcerr.alloc(1);
+    BMG_CUDA(cudaMemsetAsync(w.tcerr.get(), 0, sizeof(int), s));
+  }
   w.res.alloc(2 * k);
   w.rank.alloc(1);
   w.dquality.alloc(1);
@@ -662,19 +734,11 @@ struct CycleState {
 // CUDA graph: the first time a key is met the body runs eagerly (the row-kernel
 // autotuner times its candidates then); the second time it is captured, instantiated
 // and replayed from then on.  Graphs are off while the kernel profiler runs (its
-// events must be recorded per launch) and when BMG_GRAPHS=0.
-bool graphs_enabled() {
-  static const bool on = [] {
-    const char* e = std::getenv("BMG_GRAPHS");
-    return !(e && e[0] == '0');
-  }();
-  return on;
-}
-
+// events must be recorded per launch) and with bmg_options.graphs = 0.
 template <typename F>
 void run_graph(bmg_problem* p, SolveWork& w, const std::tuple<int, int, int, int>& key, F&& body) {
   (void)p;
-  if (!graphs_enabled() || prof_enabled() || w.s != w.own) {
+  if (!w.use_graphs || prof_enabled() || w.s != w.own) {
     body();
     return;
   }
@@ -732,12 +796,19 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
   double* hlam = w.hbuf + 2 * k;    // k Ritz values
   double* hqual = w.hbuf + 3 * k;   // error estimate of the enriched eigensolve
   int* hint = reinterpret_cast<int*>(w.hbuf + 3 * k + 1);  // rank
+  int* htc = reinterpret_cast<int*>(w.hbuf + 3 * k + 2);   // tensor-core wait expired
+  const bool tc = o.tensor_cores && k <= kTcMaxK;
   // 1-4: products, Grams and couplings, enriched eigensolve, Ritz vectors, residuals
   auto part_a = [&]() {
     // 1-2: products, Grams, couplings Q^T AX, Q^T MX by the restriction chain
     spmm_am<T>(mf, Af, Mf, b.X, ld, b.AX, b.MX, s);
-    gram(b.X, b.AX, nf, k, ld, w.GA.get(), w.partial.get(), gram_parts(nf), s, true);
-    gram(b.X, b.MX, nf, k, ld, w.GM.get(), w.partial.get(), gram_parts(nf), s, true);
+    if (tc) {
+      gram_tc(b.X, b.AX, nf, k, ld, w.GA.get(), w.partial.get(), gram_tc_parts(nf, k), w.tcerr.get(), s, true);
+      gram_tc(b.X, b.MX, nf, k, ld, w.GM.get(), w.partial.get(), gram_tc_parts(nf, k), w.tcerr.get(), s, true);
+    } else {
+      gram(b.X, b.AX, nf, k, ld, w.GA.get(), w.partial.get(), gram_parts(nf), s, true);
+      gram(b.X, b.MX, nf, k, ld, w.GM.get(), w.partial.get(), gram_parts(nf), s, true);
+    }
     const T* ca = b.AX;
     const T* cm = b.MX;
     for (int j = f; j >= 2; --j) {
@@ -768,19 +839,24 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
       z = b.cC[j];
     }
     prolong<T>(mf, z, b.Zf, ld, false, s);
-    expand<T>(b.Zf, b.X, w.Y.get() + (size_t)n1 * k, nf, k, ld, k, b.U, s);
+    if (tc)
+      expand_tc<T>(b.Zf, b.X, w.Y.get() + (size_t)n1 * k, nf, k, ld, k, b.U, w.tcscratch.get(), w.tcerr.get(), s);
+    else
+      expand<T>(b.Zf, b.X, w.Y.get() + (size_t)n1 * k, nf, k, ld, k, b.U, s);
     spmm_am<T>(mf, Af, Mf, b.U, ld, b.AU, b.MU, s);
     eig_residuals<T>(b.AU, b.MU, b.U, w.lam.get(), nf, k, ld, w.partial.get(), gram_parts(nf), w.res.get(), s);
     BMG_CUDA(cudaMemcpyAsync(hres, w.res.get(), sizeof(double) * 2 * k, cudaMemcpyDeviceToHost, s));
     BMG_CUDA(cudaMemcpyAsync(hlam, w.lam.get(), sizeof(double) * k, cudaMemcpyDeviceToHost, s));
     BMG_CUDA(cudaMemcpyAsync(hint, w.rank.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
     BMG_CUDA(cudaMemcpyAsync(hqual, w.dquality.get(), sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (tc) BMG_CUDA(cudaMemcpyAsync(htc, w.tcerr.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
   };
   {
     TraceRange trace("cycle: products, Rayleigh-Ritz, Ritz vectors, residuals");
     run_graph(p, w, std::make_tuple(0, f, (int)sizeof(T), 0), part_a);
   }
   BMG_CUDA(cudaStreamSynchronize(s));
+  if (tc && *htc) fail(BMG_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel expired");
   if (hint[0] < k) fail(BMG_ERR_SINGULAR, "enriched space rank " + std::to_string(hint[0]) + " < k");
   if (!(*hqual <= 1e-6))
     fail(BMG_ERR_NONFINITE, "enriched eigensolve refinement failed (error estimate " + std::to_string(*hqual) + ")");
@@ -853,7 +929,8 @@ bmg_options checked_options(const bmg_problem* p, int k, int n_wanted, double si
   if (!(tol > 0.0) || !std::isfinite(sigma)) fail(BMG_ERR_INVALID_ARG, "bad tol or sigma");
   if (o.nu < 1 || o.nu > 64 || o.smoother < 0 || o.smoother > 2 || o.form < 0 || o.form > 1 ||
       o.max_cycles < 1 || o.cycles_intermediate < 1 || !(o.omega > 0.0) || o.precision < 0 ||
-      o.precision > 1 || !(o.switch_tol > 0.0) || o.stop_after_cycles < 0 || o.resume < 0 || o.resume > 1)
+      o.precision > 1 || !(o.switch_tol > 0.0) || o.stop_after_cycles < 0 || o.resume < 0 || o.resume > 1 ||
+      o.tensor_cores < 0 || o.tensor_cores > 1 || o.autotune < 0 || o.autotune > 1 || o.graphs < 0 || o.graphs > 1)
     fail(BMG_ERR_INVALID_ARG, "bad options");
   return o;
 }
@@ -867,11 +944,11 @@ struct StateHead {
   int32_t k, L, n_wanted, level, cycle, fp32, total_cycles, fp32_cycles, n_f, n_hist, n_info, pad;
   int32_t cyc[33];
   double sigma, tol, max_dense_err;
-  int32_t smoother, nu, form, vcycle_depth, cycles_intermediate, max_cycles, precision, pad2;
+  int32_t smoother, nu, form, vcycle_depth, cycles_intermediate, max_cycles, precision, tensor_cores;
   double omega, tol_intermediate, switch_tol;
 };
 constexpr uint32_t kStateMagic = 0x53474d42u;   // "BMGS"
-constexpr uint32_t kStateVersion = 1;
+constexpr uint32_t kStateVersion = 2;
 size_t state_bytes(const StateHead& h) {
   return sizeof(StateHead) + sizeof(double) * ((size_t)h.n_hist + h.n_info + 2 * (size_t)h.k + (size_t)h.n_f * h.k) +
          sizeof(int32_t) * 2 * (size_t)h.n_info;
@@ -879,6 +956,7 @@ size_t state_bytes(const StateHead& h) {
 void head_options(StateHead& h, const bmg_options& o) {
   h.smoother = o.smoother; h.nu = o.nu; h.form = o.form; h.vcycle_depth = o.vcycle_depth;
   h.cycles_intermediate = o.cycles_intermediate; h.max_cycles = o.max_cycles; h.precision = o.precision;
+  h.tensor_cores = o.tensor_cores;
   h.omega = o.omega; h.tol_intermediate = o.tol_intermediate; h.switch_tol = o.switch_tol;
 }
 bool same_options(const StateHead& h, const bmg_options& o) {
@@ -886,7 +964,7 @@ bool same_options(const StateHead& h, const bmg_options& o) {
   head_options(g, o);
   return g.smoother == h.smoother && g.nu == h.nu && g.form == h.form && g.vcycle_depth == h.vcycle_depth &&
          g.cycles_intermediate == h.cycles_intermediate && g.max_cycles == h.max_cycles &&
-         g.precision == h.precision && g.omega == h.omega && g.tol_intermediate == h.tol_intermediate &&
+         g.precision == h.precision && g.tensor_cores == h.tensor_cores && g.omega == h.omega && g.tol_intermediate == h.tol_intermediate &&
          g.switch_tol == h.switch_tol;
 }
 // Checks a state's structure against the problem; returns its header.
@@ -909,6 +987,8 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
                 int evecs_on_device, double* resid, bmg_solve_info* info,
                 const std::vector<unsigned char>* resume = nullptr, bool* stopped = nullptr) {
   TraceRange trace("bmg_solve");
+  AutotuneScope tune_scope(o.autotune != 0);
+  w.use_graphs = o.graphs != 0;
   const int L = p->L;
   const int n2 = p->meshOf(2).n, nL = p->meshOf(L).n;
   // the solve runs on the workspace's own non-blocking stream (capturable into CUDA
@@ -924,7 +1004,7 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
   const int ld = w.ld;
   // the cycle graphs hold these values as launch arguments: recapture when they change
   const std::vector<double> sig = {sigma, (double)o.form, (double)o.smoother, (double)o.nu, o.omega,
-                                   (double)o.vcycle_depth, (double)o.precision};
+                                   (double)o.vcycle_depth, (double)o.precision, (double)o.tensor_cores};
   if (sig != w.gsig) {
     BMG_CUDA(cudaStreamSynchronize(s));
     w.drop_graphs();

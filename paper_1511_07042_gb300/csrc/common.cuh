@@ -151,7 +151,10 @@ struct SolveWork {
   std::vector<DBuf<float>> cA32, cB32, cC32, cD32;
   std::vector<DBuf<double>> AQ, MQ;         // per f: dense n1 x n1 coarse blocks
   std::vector<std::vector<double>> ratio;   // [f][j] max_i dM_i / dA_i
-  double* hbuf = nullptr;                   // pinned host staging (res, lam, quality, rank)
+  double* hbuf = nullptr;                   // pinned host staging (res, lam, quality, rank, tc flag)
+  DBuf<unsigned char> tcscratch;            // digits of the expansion coefficients (tensor cores)
+  DBuf<int> tcerr;                          // raised by a tensor-core kernel whose wait expired
+  bool use_graphs = true;                   // bmg_options.graphs of the running solve
   // CUDA graphs of the cycle: part A (steps 1-4) per (level, arithmetic), part B
   // (step 5) per (level, arithmetic, down-leg depth); instantiated on the second cycle
   // of a level on this workspace (the first runs eagerly, so the autotuner can time).
@@ -250,7 +253,32 @@ void gram(const double* X, const double* Y, int n, int k, int ld, double* G, dou
 void gram(const float* X, const float* Y, int n, int k, int ld, double* G, double* partial,
           int nparts, cudaStream_t s, bool sym = false);
 int gram_parts(int n);
+// Row-kernel autotuning on the calling thread while the scope lives (a solve's
+// bmg_options.autotune); off: the default shapes.
+struct AutotuneScope {
+  explicit AutotuneScope(bool on);
+  ~AutotuneScope();
+  AutotuneScope(const AutotuneScope&) = delete;
+  AutotuneScope& operator=(const AutotuneScope&) = delete;
+ private:
+  bool prev_;
+};
+// G[q] = sum of the nparts partials partial[b][q] in block order (q < k*k); with sym an
+// entry below the diagonal 4x4 tiles takes its mirror.
+void gram_reduce(const double* partial, int nparts, int k, double* G, bool sym, cudaStream_t s);
 std::string tuned_report();
+
+// tensor-core products (tc.cu): float64-class results from exact BF16 digit slices on
+// tcgen05, for k <= kTcMaxK.  err: device int raised when a bounded wait expired.
+constexpr int kTcMaxK = 128;
+int gram_tc_parts(int n, int k);
+size_t expand_tc_scratch_bytes(int k);
+template <typename TI>
+void gram_tc(const TI* X, const TI* Y, int n, int k, int ld, double* G, double* partial, int nparts, int* err,
+             cudaStream_t s, bool sym);
+template <typename TI>
+void expand_tc(const TI* Zf, const TI* X, const double* Yx, int n, int k, int ld, int ldy, TI* U,
+               unsigned char* scratch, int* err, cudaStream_t s);
 template <typename T>
 void eig_residuals(const T* AU, const T* MU, const T* U, const double* lam, int n, int k, int ld,
                    double* partial, int nparts, double* out, cudaStream_t s);

@@ -587,18 +587,14 @@ void row_launch(RowCfg c, const Mesh& m, const T* a, const T* mm, const T* da, c
 
 // Tuned shapes, process-wide.  The candidates are timed on the call's own data and
 // stream (spmm, Jacobi and residual kernels are idempotent: they write a block they
-// do not read), three launches each after one warm-up, with CUDA events.  Set
-// BMG_AUTOTUNE=0 to use the default shape (32 lanes per row, 8 warps per block).
+// do not read), three launches each after one warm-up, with CUDA events.  A solve
+// with bmg_options.autotune = 0 uses the default shape (32 lanes per row, 8 warps
+// per block) on its thread.
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, RowCfg> g_tuned;
+thread_local bool t_autotune = true;
 
-bool autotune_enabled() {
-  static const bool on = [] {
-    const char* e = std::getenv("BMG_AUTOTUNE");
-    return !(e && e[0] == '0');
-  }();
-  return on;
-}
+bool autotune_enabled() { return t_autotune; }
 
 template <typename F>
 RowCfg tune_rows(int kind, int tsize, int nch, int n, cudaStream_t s, F&& launch) {
@@ -609,6 +605,7 @@ RowCfg tune_rows(int kind, int tsize, int nch, int n, cudaStream_t s, F&& launch
     if (it != g_tuned.end()) return it->second;
   }
   RowCfg best = default_cfg(nch);
+  if (!autotune_enabled()) return best;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   check_cuda(cudaStreamIsCapturing(s, &cap), "cudaStreamIsCapturing");
   if (!autotune_enabled() || cap != cudaStreamCaptureStatusNone) return best;
@@ -637,6 +634,9 @@ RowCfg tune_rows(int kind, int tsize, int nch, int n, cudaStream_t s, F&& launch
   return best;
 }
 }  // namespace
+
+AutotuneScope::AutotuneScope(bool on) : prev_(t_autotune) { t_autotune = on; }
+AutotuneScope::~AutotuneScope() { t_autotune = prev_; }
 
 template <typename T>
 void spmm_am(const Mesh& m, const T* a, const T* mm, const T* X, int ld, T* AX, T* MX, cudaStream_t s) {
@@ -667,7 +667,7 @@ static void row_update(const Mesh& m, const T* a, const T* mm, const T* da, cons
     c = tune_rows(3, (int)sizeof(T), nch, nrows, s, [&](RowCfg q) {
       row_launch<T, 2>(q, m, a, mm, da, dm, rows, nrows, X, scratch, B, shift, nch, omega, s);
     });
-  } else if (MODE == 1) {
+  } else if (MODE == 1 && autotune_enabled()) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     for (int kd : {2, 1}) {
       auto it = g_tuned.find(std::make_tuple(kd, (int)sizeof(T), nch, m.n));
@@ -766,6 +766,11 @@ void gram(const float* X, const float* Y, int n, int k, int ld, double* G, doubl
   gram_reduce_kernel<<<blocks_for(k * k, 256), 256, 0, s>>>(partial, nparts, k * k, G, k, sym ? 1 : 0);
   check_launch("gram_reduce_kernel");
   prof_end(KC_GRAM, s, 8.0 * n * ld + 16.0 * nparts * k * k + 8.0 * k * k, 2.0 * n * k * k);
+}
+
+void gram_reduce(const double* partial, int nparts, int k, double* G, bool sym, cudaStream_t s) {
+  gram_reduce_kernel<<<blocks_for(k * k, 256), 256, 0, s>>>(partial, nparts, k * k, G, k, sym ? 1 : 0);
+  check_launch("gram_reduce_kernel");
 }
 
 template <typename T>

@@ -23,7 +23,9 @@ def solve(bmg, R, k, nw, sigma, tol, amp=0.0, seed=None, x0seed=1001, colour=Fal
 @pytest.mark.parametrize("kw", [dict(smoother="jacobi", nu=2, omega=2 / 3),
                                 dict(smoother="jacobi", nu=2, omega=2 / 3, form="homogeneous"),
                                 dict(smoother="mcsgs", nu=1, omega=1.0),
-                                dict(smoother="mcgs", nu=2, omega=1.0, form="homogeneous")])
+                                dict(smoother="mcgs", nu=2, omega=1.0, form="homogeneous"),
+                                dict(smoother="jacobi", nu=2, omega=2 / 3, tensor_cores=False),
+                                dict(smoother="mcsgs", nu=1, omega=1.0, tensor_cores=False)])
 def test_sphere642_k20_matches_dense(gpu_bmg, kw):
     ev, U, rs, info, H = solve(gpu_bmg, 3, 20, 16, 0.0, 1e-10, **kw)
     assert info.converged == 1
