@@ -276,7 +276,7 @@ bmg_status bmg_restrict(const bmg_problem* p, int level, const double* R, double
                         int k, int ld, void* stream);
 
 /* G[i][j] = sum_r X[r][i] Y[r][j] (k x k, row-major, float64) for X, Y [n][ld],
- * 1 <= k <= 160.  Synchronous.                                                   */
+ * 1 <= k <= 160, k <= ld <= 800.  Synchronous.                                   */
 bmg_status bmg_gram(const double* X, const double* Y, int n, int k, int ld, double* G,
                     void* stream);
 
@@ -334,7 +334,10 @@ bmg_status bmg_dense_eig(const double* Ahat, const double* Mhat, int n, double s
  * the library (4 MiB, held by every GPU that loads it until the process exits).
  * The first call on each device looks up that array's device address; make that
  * first call before any stream capture.  Asynchronous on `stream`; no device
- * memory is allocated or freed.  k <= 160 (larger k: BMG_ERR_INVALID_ARG).  All
+ * memory is allocated or freed.  k <= 160 and ld <= 800 (else BMG_ERR_INVALID_ARG;
+ * k <= 160 is the Gram kernel's limit).  The array caps the row blocks that run at
+ * once at 524288 / k^2 (20 blocks at k = 160, 128 at k = 64, against up to 304 in
+ * bmg_gram), so large n at large k runs several times slower than bmg_gram.  All
  * calls share the array: calls whose work overlaps on the GPU (e.g. on two
  * streams) race and give wrong results; order them on one stream.               */
 bmg_status bmg_gram_noalloc(const double* X, const double* Y, int n, int k, int ld, double* G,

@@ -355,7 +355,8 @@ extern "C" bmg_status bmg_restrict(const bmg_problem* p, int level, const double
 
 extern "C" bmg_status bmg_gram(const double* X, const double* Y, int n, int k, int ld, double* G, void* stream) {
   return guarded([&] {
-    if (!X || !Y || !G || n < 1 || k < 1 || k > 160 || ld < k) fail(BMG_ERR_INVALID_ARG, "bad gram arguments (1 <= k <= 160)");
+    if (!X || !Y || !G || n < 1 || k < 1 || k > 160 || ld < k || ld > kGramMaxLd)
+      fail(BMG_ERR_INVALID_ARG, "bad gram arguments (1 <= k <= 160, k <= ld <= 800)");
     const int parts = gram_parts(n);
     DBuf<double> partial((size_t)parts * k * k);
     gram(X, Y, n, k, ld, G, partial.get(), parts, (cudaStream_t)stream);
@@ -1329,8 +1330,8 @@ extern "C" bmg_status bmg_smooth_f32(bmg_problem* p, int f, int level, float* X,
 
 extern "C" bmg_status bmg_gram_f32(const float* X, const float* Y, int n, int k, int ld, double* G, void* stream) {
   return guarded([&] {
-    if (!X || !Y || !G || n < 1 || k < 1 || k > 160 || ld < k || (ld & 3))
-      fail(BMG_ERR_INVALID_ARG, "bad gram arguments (1 <= k <= 160, ld % 4 == 0)");
+    if (!X || !Y || !G || n < 1 || k < 1 || k > 160 || ld < k || (ld & 3) || ld > kGramMaxLd)
+      fail(BMG_ERR_INVALID_ARG, "bad gram arguments (1 <= k <= 160, k <= ld <= 800, ld % 4 == 0)");
     const int parts = gram_parts(n);
     DBuf<double> partial((size_t)parts * k * k);
     gram(X, Y, n, k, ld, G, partial.get(), parts, (cudaStream_t)stream);

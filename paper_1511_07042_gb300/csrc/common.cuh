@@ -253,6 +253,8 @@ void gram(const double* X, const double* Y, int n, int k, int ld, double* G, dou
 void gram(const float* X, const float* Y, int n, int k, int ld, double* G, double* partial,
           int nparts, cudaStream_t s, bool sym = false);
 int gram_parts(int n);
+// Widest block the CUDA-core Gram kernels stage (2 x 16 rows of ld values in shared memory).
+constexpr int kGramMaxLd = 800;
 // Row-kernel autotuning on the calling thread while the scope lives (a solve's
 // bmg_options.autotune); off: the default shapes.
 struct AutotuneScope {

@@ -22,6 +22,7 @@ namespace bmg {
 namespace {
 
 constexpr size_t kScratchDoubles = size_t(1) << 19;   // 4 MiB of partial sums
+static_assert(160 * 160 <= kScratchDoubles, "one k x k partial of the largest block fits the array");
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_gram_scratch[kScratchDoubles];
@@ -53,14 +54,16 @@ extern "C" bmg_status bmg_gram_noalloc(const double* X, const double* Y, int n, 
                                        void* stream) {
   try {
     if (!X || !Y || !G) fail(BMG_ERR_INVALID_ARG, "bmg_gram_noalloc: null pointer");
-    if (n < 1 || k < 1 || ld < k) fail(BMG_ERR_INVALID_ARG, "bmg_gram_noalloc: need n >= 1 and 1 <= k <= ld");
+    if (n < 1 || k < 1 || ld < k || ld > kGramMaxLd)
+      fail(BMG_ERR_INVALID_ARG, "bmg_gram_noalloc: need n >= 1 and 1 <= k <= ld <= 800");
     if (k > 160)
       fail(BMG_ERR_INVALID_ARG, "bmg_gram_noalloc: k = " + std::to_string(k) +
                                     " exceeds the maximum of 160 supported by the Gram kernel");
     const size_t kk = (size_t)k * k;
-    if (kk > kScratchDoubles)
-      fail(BMG_ERR_INVALID_ARG, "bmg_gram_noalloc: k * k exceeds the fixed scratch of 524288 doubles");
     double* scratch = scratch_for_current_device();
+    // The array bounds the number of row blocks that run in parallel, not k: each
+    // block keeps a k x k partial, so k = 160 allows 20 blocks (where bmg_gram runs up
+    // to 304) and each block then sums n / 20 rows.
     int parts = gram_parts(n);
     const int cap = (int)(kScratchDoubles / kk);
     if (parts > cap) parts = cap;

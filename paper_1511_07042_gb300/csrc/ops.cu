@@ -739,6 +739,13 @@ void gram(const double* X, const double* Y, int n, int k, int ld, double* G, dou
   const int tk = (k + 3) / 4;
   const int ntiles = sym ? tk * (tk + 1) / 2 : tk * tk;
   const size_t smem = 2 * kGramRows * ld * sizeof(double);
+  if (smem > 48 * 1024) {   // blocks wider than 192 columns (e.g. column slices of a wider block)
+    const int sm = (int)smem;
+    check_cuda(cudaFuncSetAttribute(gram_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm), "gram attr");
+    check_cuda(cudaFuncSetAttribute(gram_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm), "gram attr");
+    check_cuda(cudaFuncSetAttribute(gram_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm), "gram attr");
+    check_cuda(cudaFuncSetAttribute(gram_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm), "gram attr");
+  }
   prof_begin(KC_GRAM, s);
   if (ntiles <= kGramThreads) gram_kernel<1><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial, sym ? 1 : 0);
   else if (ntiles <= 2 * kGramThreads) gram_kernel<2><<<nparts, kGramThreads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial, sym ? 1 : 0);
@@ -759,6 +766,9 @@ void gram(const float* X, const float* Y, int n, int k, int ld, double* G, doubl
   const int tk = (k + 3) / 4;
   const int ntiles = sym ? tk * (tk + 1) / 2 : tk * tk;
   const size_t smem = 2 * kGramRows * ld * sizeof(float);
+  if (smem > 48 * 1024)
+    check_cuda(cudaFuncSetAttribute(gram_f32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem),
+               "gram_f32 attr");
   prof_begin(KC_GRAM, s);
   const dim3 grid(nparts, (ntiles + kGram32Threads - 1) / kGram32Threads);
   gram_f32_kernel<<<grid, kGram32Threads, smem, s>>>(X, Y, n, k, ld, rows_per_part, partial, sym ? 1 : 0);

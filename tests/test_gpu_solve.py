@@ -79,6 +79,11 @@ def test_sphere40962_k64_full_size(gpu_bmg):
     X0 = inputs.gaussian_block(inputs.n_vertices(2), 64, 1001)
     ref = obmg.bfmg(H, X0, 64, 49, 0.0, 1e-10, obmg.Options(smoother="mcsgs", nu=1, omega=1.0))
     assert np.max(np.abs(lam - np.sort(ref.lam[:49])) / np.maximum(np.abs(lam), 1)) <= 1e-10
+    # and spans the same invariant subspaces: M-principal angles per cluster
+    o = np.argsort(ref.lam[:49])
+    err, ang = certify.compare_to_reference(M, ev, U, ref.lam[:49][o], ref.U[:, :49][:, o])
+    print("40962-vertex solve: max eigenvalue error %.2e, max cluster angle %.2e" % (err.max(), ang.max()))
+    assert err.max() <= 1e-10 and ang.max() <= 1e-8
 
 
 def test_invalid_arguments_and_nonfinite(gpu_bmg):

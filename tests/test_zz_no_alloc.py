@@ -39,6 +39,47 @@ def test_gram_noalloc_matches_gram_on_two_consecutive_calls(gpu_bmg, n, k):
         assert np.max(np.abs(a - X.T @ Y)) <= 1e-14 * n * 4, call
 
 
+def test_gram_noalloc_allocates_nothing_on_a_side_stream(gpu_bmg):
+    """The entry point's contract: after a first call (which looks up the array's
+    address), repeated calls on a non-default stream leave the device's free memory
+    unchanged; only the end is synchronised."""
+    n, k = 40962, 64
+    rng = np.random.default_rng(5)
+    Xd, Yd = _dev(rng.standard_normal((n, k))), _dev(rng.standard_normal((n, k)))
+    G = torch.empty((k, k), dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        gpu_bmg.gram_noalloc(Xd, Yd, k, G)          # first call on this device
+    side.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with torch.cuda.stream(side):
+        for _ in range(5):
+            gpu_bmg.gram_noalloc(Xd, Yd, k, G)
+        free1 = torch.cuda.mem_get_info()[0]
+    side.synchronize()
+    assert free1 == free0 and torch.cuda.mem_get_info()[0] == free0
+    ref = torch.empty_like(G)
+    gpu_bmg.gram(Xd, Yd, k, ref)
+    assert torch.max(torch.abs(G - ref)).item() <= 1e-14 * n * 4      # tolerance of the Gram tests
+
+
+def test_gram_noalloc_wide_leading_dimension(gpu_bmg):
+    """A k = 20 column slice of a 200-wide block (shared-memory rows wider than the
+    default 48 KB allowance) against bmg_gram and the host product."""
+    n, k, ld = 4099, 20, 200
+    rng = np.random.default_rng(9)
+    Xw = torch.from_numpy(rng.standard_normal((n, ld))).cuda()
+    Yw = torch.from_numpy(rng.standard_normal((n, ld))).cuda()
+    G1 = torch.empty((k, k), dtype=torch.float64, device="cuda")
+    G2 = torch.full((k, k), np.nan, dtype=torch.float64, device="cuda")
+    gpu_bmg.gram(Xw, Yw, k, G1)
+    gpu_bmg.gram_noalloc(Xw, Yw, k, G2)
+    torch.cuda.synchronize()
+    ref = Xw[:, :k].cpu().numpy().T @ Yw[:, :k].cpu().numpy()
+    assert np.max(np.abs(G1.cpu().numpy() - ref)) <= 1e-14 * n * 4
+    assert torch.equal(G1, G2)
+
+
 def test_gram_noalloc_rejects_oversize_block(gpu_bmg):
     X = torch.zeros((8, 162), dtype=torch.float64, device="cuda")
     G = torch.zeros((161, 161), dtype=torch.float64, device="cuda")
