@@ -64,25 +64,83 @@ __device__ __forceinline__ void stv(float* p, size_t i, const float (&v)[4]) {
   reinterpret_cast<float4*>(p)[i] = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// aa += A_row X, mm += M_row X for one CSR row owned by a warp (pattern and values
-// streamed, neighbour rows of X gathered through the read-only path).
+// aa += A_row X, mm += M_row X for one CSR row owned by LPR lanes (pattern and values
+// streamed, neighbour rows of X gathered through the read-only path).  The row's
+// nonzeros are taken G at a time: lane q of the row's lanes loads nonzero q's column
+// and values (one coalesced load each), the columns are broadcast by shuffles and all
+// G neighbour gathers are issued before the first multiply, so a warp keeps G gathers
+// in flight instead of one dependent load chain per nonzero.  The products are added
+// in the order of the nonzeros, as one nonzero at a time would.  Every lane of the
+// warp must call this (len = 0 for lanes without a row): the loop bound is the
+// warp's longest row.  (float32 blocks; float64 blocks take one nonzero at a time.)
+template <typename T, int LPR, int CPL>
+struct GatherWidth {
+  static constexpr int regs = CPL * Chunk<T>::W * (int)(sizeof(T) / 4);   // 32-bit registers per nonzero
+  static constexpr int G0 = 32 / regs < 2 ? 2 : 32 / regs;
+  static constexpr int G = G0 < LPR ? G0 : LPR;
+};
 template <typename T, int LPR, int CPL>
 __device__ __forceinline__ void gather_row(const int* __restrict__ col, const T* __restrict__ va,
-                                           const T* __restrict__ vm, const T* __restrict__ X, int b, int e,
+                                           const T* __restrict__ vm, const T* __restrict__ X, int b, int len,
                                            int nch, int sl, T (&aa)[CPL][Chunk<T>::W],
                                            T (&mm)[CPL][Chunk<T>::W]) {
   constexpr int W = Chunk<T>::W;
-  for (int p = b; p < e; ++p) {
-    const int j = __ldcs(col + p);
-    const T a = __ldcs(va + p), m = __ldcs(vm + p);
+  if (sizeof(T) == 8) {
+    // float64 blocks: the sweeps are bound by the FP64 pipe, not by memory latency,
+    // so one nonzero at a time (no shuffles competing for issue slots)
+    for (int p = b; p < b + len; ++p) {
+      const int j = __ldcs(col + p);
+      const T a = __ldcs(va + p), m = __ldcs(vm + p);
 #pragma unroll
-    for (int u = 0; u < CPL; ++u) {
-      const int c = sl + LPR * u;
-      if (c < nch) {
-        T x[W];
-        ldv_ro(X, (size_t)j * nch + c, x);
+      for (int u = 0; u < CPL; ++u) {
+        const int c = sl + LPR * u;
+        if (c < nch) {
+          T x[W];
+          ldv_ro(X, (size_t)j * nch + c, x);
 #pragma unroll
-        for (int z = 0; z < W; ++z) { aa[u][z] = fma(a, x[z], aa[u][z]); mm[u][z] = fma(m, x[z], mm[u][z]); }
+          for (int z = 0; z < W; ++z) { aa[u][z] = fma(a, x[z], aa[u][z]); mm[u][z] = fma(m, x[z], mm[u][z]); }
+        }
+      }
+    }
+    return;
+  }
+  constexpr int G = GatherWidth<T, LPR, CPL>::G;
+  const int maxlen = __reduce_max_sync(0xffffffffu, len);
+  for (int p0 = 0; p0 < maxlen; p0 += G) {
+    const int cnt = len - p0;
+    int jl = 0;
+    T al = T(0), ml = T(0);
+    if (sl < G && sl < cnt) {
+      jl = __ldcs(col + b + p0 + sl);
+      al = __ldcs(va + b + p0 + sl);
+      ml = __ldcs(vm + b + p0 + sl);
+    }
+    T x[G][CPL][W];
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      const int j = __shfl_sync(0xffffffffu, jl, q, LPR);
+#pragma unroll
+      for (int u = 0; u < CPL; ++u) {
+        const int c = sl + LPR * u;
+        if (q < cnt && c < nch) {
+          ldv_ro(X, (size_t)j * nch + c, x[q][u]);
+        } else {
+#pragma unroll
+          for (int z = 0; z < W; ++z) x[q][u][z] = T(0);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      const T a = __shfl_sync(0xffffffffu, al, q, LPR);
+      const T m = __shfl_sync(0xffffffffu, ml, q, LPR);
+      if (q < cnt) {
+#pragma unroll
+        for (int u = 0; u < CPL; ++u)
+          if (sl + LPR * u < nch) {
+#pragma unroll
+            for (int z = 0; z < W; ++z) { aa[u][z] = fma(a, x[q][u][z], aa[u][z]); mm[u][z] = fma(m, x[q][u][z], mm[u][z]); }
+          }
       }
     }
   }
@@ -105,30 +163,43 @@ __device__ __forceinline__ float recip(float d) { return __frcp_rn(d); }
 // Row tiling: LPR lanes per row (32 / LPR rows per warp), CPL 16-byte chunks per lane
 // (chunks sl, sl + LPR, ...), blockDim.x / 32 warps per block; picked per level size
 // and block width by the autotuner (tune_rows).
+// Row groups (a group: the rows of one pass of a CTA's warps) are dealt to the CTAs in
+// chunks of `groups` consecutive groups, round robin: an SM walks short contiguous
+// stretches of the Morton row order (neighbour rows of X found in its L1), while all
+// SMs together stay within a window of the order that L2 holds (neighbours shared
+// across chunks found in L2).
 template <typename T, int LPR, int CPL>
 __global__ void __launch_bounds__(512)
 spmm_am_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
                const T* __restrict__ va, const T* __restrict__ vm,
                const T* __restrict__ X, int n, int nch, T* __restrict__ AX,
-               T* __restrict__ MX, const int* __restrict__ order) {
+               T* __restrict__ MX, const int* __restrict__ order, int groups) {
   constexpr int W = Chunk<T>::W;
   constexpr int RPW = 32 / LPR;
   const int lane = threadIdx.x & 31, sl = lane % LPR;
-  const int w = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RPW + lane / LPR;
-  if (w >= n) return;
-  const int row = order ? order[w] : w;
-  T aa[CPL][W], mm[CPL][W];
+  const int per_group = (blockDim.x >> 5) * RPW;
+  const int ngroups = (n + per_group - 1) / per_group;
+  for (int g = blockIdx.x * groups, gc = 0; g < ngroups; ++g) {
+    if (gc == groups) { g += (gridDim.x - 1) * groups; gc = 0; if (g >= ngroups) break; }
+    ++gc;
+    const int w = g * per_group + (threadIdx.x >> 5) * RPW + lane / LPR;
+    const bool live = w < n;               // every lane takes part in the row's shuffles
+    const int row = live ? (order ? order[w] : w) : 0;
+    T aa[CPL][W], mm[CPL][W];
 #pragma unroll
-  for (int u = 0; u < CPL; ++u)
+    for (int u = 0; u < CPL; ++u)
 #pragma unroll
-    for (int q = 0; q < W; ++q) { aa[u][q] = T(0); mm[u][q] = T(0); }
-  gather_row<T, LPR, CPL>(col, va, vm, X, row_ptr[row], row_ptr[row + 1], nch, sl, aa, mm);
+      for (int q = 0; q < W; ++q) { aa[u][q] = T(0); mm[u][q] = T(0); }
+    const int b = live ? row_ptr[row] : 0;
+    gather_row<T, LPR, CPL>(col, va, vm, X, b, live ? row_ptr[row + 1] - b : 0, nch, sl, aa, mm);
+    if (!live) continue;
 #pragma unroll
-  for (int u = 0; u < CPL; ++u) {
-    const int c = sl + LPR * u;
-    if (c < nch) {
-      stv_cs(AX, (size_t)row * nch + c, aa[u]);
-      stv_cs(MX, (size_t)row * nch + c, mm[u]);
+    for (int u = 0; u < CPL; ++u) {
+      const int c = sl + LPR * u;
+      if (c < nch) {
+        stv_cs(AX, (size_t)row * nch + c, aa[u]);
+        stv_cs(MX, (size_t)row * nch + c, mm[u]);
+      }
     }
   }
 }
@@ -145,48 +216,56 @@ row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
                   const T* __restrict__ da, const T* __restrict__ dm,
                   const int* __restrict__ rows, int nrows, const T* X,
                   T* Out, const T* __restrict__ B, const T* __restrict__ shift,
-                  int nch, T omega) {
+                  int nch, T omega, int groups) {
   constexpr int W = Chunk<T>::W;
   constexpr int RPW = 32 / LPR;
   const int lane = threadIdx.x & 31, sl = lane % LPR;
-  const int w = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RPW + lane / LPR;
-  if (w >= nrows) return;
-  const int row = rows ? rows[w] : w;
-  T aa[CPL][W], mm[CPL][W];
+  const int per_group = (blockDim.x >> 5) * RPW;
+  const int ngroups = (nrows + per_group - 1) / per_group;
+  for (int g = blockIdx.x * groups, gc = 0; g < ngroups; ++g) {
+    if (gc == groups) { g += (gridDim.x - 1) * groups; gc = 0; if (g >= ngroups) break; }
+    ++gc;
+    const int w = g * per_group + (threadIdx.x >> 5) * RPW + lane / LPR;
+    const bool live = w < nrows;           // every lane takes part in the row's shuffles
+    const int row = live ? (rows ? rows[w] : w) : 0;
+    T aa[CPL][W], mm[CPL][W];
 #pragma unroll
-  for (int u = 0; u < CPL; ++u)
+    for (int u = 0; u < CPL; ++u)
 #pragma unroll
-    for (int q = 0; q < W; ++q) { aa[u][q] = T(0); mm[u][q] = T(0); }
-  gather_row<T, LPR, CPL>(col, va, vm, X, row_ptr[row], row_ptr[row + 1], nch, sl, aa, mm);
-  const T dai = da[row], dmi = dm[row];
+      for (int q = 0; q < W; ++q) { aa[u][q] = T(0); mm[u][q] = T(0); }
+    const int b = live ? row_ptr[row] : 0;
+    gather_row<T, LPR, CPL>(col, va, vm, X, b, live ? row_ptr[row + 1] - b : 0, nch, sl, aa, mm);
+    if (!live) continue;
+    const T dai = da[row], dmi = dm[row];
 #pragma unroll
-  for (int u = 0; u < CPL; ++u) {
-    const int c = sl + LPR * u;
-    if (c >= nch) continue;
-    T s[W], r[W];
-    ldv(shift, c, s);
+    for (int u = 0; u < CPL; ++u) {
+      const int c = sl + LPR * u;
+      if (c >= nch) continue;
+      T s[W], r[W];
+      ldv(shift, c, s);
 #pragma unroll
-    for (int q = 0; q < W; ++q) r[q] = -(aa[u][q] - s[q] * mm[u][q]);
-    const size_t idx = (size_t)row * nch + c;
-    if (B) {
-      T bb[W];
-      ldv(B, idx, bb);
+      for (int q = 0; q < W; ++q) r[q] = -(aa[u][q] - s[q] * mm[u][q]);
+      const size_t idx = (size_t)row * nch + c;
+      if (B) {
+        T bb[W];
+        ldv(B, idx, bb);
 #pragma unroll
-      for (int q = 0; q < W; ++q) r[q] += bb[q];
-    }
-    if (MODE == 2) {
-      stv_cs(Out, idx, r);
-    } else {
-      T x[W], o[W];
-      ldv(X, idx, x);
-#pragma unroll
-      for (int q = 0; q < W; ++q) {
-        const T d = dai - s[q] * dmi;
-        const T rd = recip(d);
-        o[q] = (MODE == 0) ? x[q] + omega * (r[q] * rd) : x[q] + r[q] * rd;
+        for (int q = 0; q < W; ++q) r[q] += bb[q];
       }
-      // padding columns carry zero shift, zero data and stay zero
-      if (MODE == 0) stv_cs(Out, idx, o); else stv(Out, idx, o);
+      if (MODE == 2) {
+        stv_cs(Out, idx, r);
+      } else {
+        T x[W], o[W];
+        ldv_ro(X, idx, x);   // a row of the running colour is read only by its own lanes
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+          const T d = dai - s[q] * dmi;
+          const T rd = recip(d);
+          o[q] = (MODE == 0) ? x[q] + omega * (r[q] * rd) : x[q] + r[q] * rd;
+        }
+        // padding columns carry zero shift, zero data and stay zero
+        if (MODE == 0) stv_cs(Out, idx, o); else stv(Out, idx, o);
+      }
     }
   }
 }
@@ -522,7 +601,9 @@ constexpr int kWPB[3] = {4, 8, 16};
 
 struct RowCfg {
   int shape, wpb;
+  int chunk = 64;   // rows per chunk dealt to a CTA (row_grid)
 };
+constexpr int kChunks[4] = {32, 64, 128, 256};
 
 int pow2_at_least(int x) {
   int p = 1;
@@ -539,49 +620,81 @@ RowCfg default_cfg(int nch) {
   return {cpl == 1 ? 0 : (cpl == 2 ? 1 : 2), 8};
 }
 
+// Resident CTAs of a row kernel per SM (occupancy calculator), cached per kernel and
+// block size.
+std::mutex g_occ_mu;
+std::map<std::pair<const void*, int>, int> g_occ;
+int resident_blocks(const void* kernel, int threads) {
+  std::lock_guard<std::mutex> lock(g_occ_mu);
+  const auto key = std::make_pair(kernel, threads);
+  auto it = g_occ.find(key);
+  if (it != g_occ.end()) return it->second;
+  int nb = 0, dev = 0, sms = 0;
+  check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, 0), "occupancy");
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "sm count");
+  const int v = std::max(1, nb) * std::max(1, sms);
+  g_occ.emplace(key, v);
+  return v;
+}
+// Grid of a row kernel over `items` row groups of `rows_per_group` rows: at most one
+// wave of resident CTAs, dealt chunks of about `chunk` consecutive rows.
+void row_grid(const void* kernel, int threads, int items, int rows_per_group, int chunk, int& grid, int& groups) {
+  const int wave = resident_blocks(kernel, threads);
+  groups = std::max(1, chunk / rows_per_group);
+  const int chunks = (items + groups - 1) / groups;
+  grid = std::max(1, std::min(chunks, wave));
+}
+
 template <typename T, int LPR, int CPL>
-void spmm_shape(int wpb, const Mesh& m, const T* a, const T* mm, const T* X, int nch, T* AX, T* MX,
+void spmm_shape(int wpb, int chunk, const Mesh& m, const T* a, const T* mm, const T* X, int nch, T* AX, T* MX,
                 cudaStream_t s) {
   const int per_block = wpb * (32 / LPR);
-  spmm_am_kernel<T, LPR, CPL><<<blocks_for(m.n, per_block), wpb * 32, 0, s>>>(
-      m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX, m.row_order.get());
+  int grid, groups;
+  row_grid((const void*)spmm_am_kernel<T, LPR, CPL>, wpb * 32, blocks_for(m.n, per_block), per_block, chunk, grid,
+           groups);
+  spmm_am_kernel<T, LPR, CPL><<<grid, wpb * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, X, m.n, nch, AX, MX,
+                                                        m.row_order.get(), groups);
   check_launch("spmm_am_kernel");
 }
 template <typename T>
 void spmm_launch(RowCfg c, const Mesh& m, const T* a, const T* mm, const T* X, int nch, T* AX, T* MX,
                  cudaStream_t s) {
   switch (c.shape) {
-    case 0: spmm_shape<T, 32, 1>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
-    case 1: spmm_shape<T, 32, 2>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
-    case 2: spmm_shape<T, 32, 4>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
-    case 3: spmm_shape<T, 16, 1>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
-    case 4: spmm_shape<T, 16, 2>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
-    case 5: spmm_shape<T, 8, 1>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
-    case 6: spmm_shape<T, 8, 2>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
-    default: spmm_shape<T, 4, 1>(c.wpb, m, a, mm, X, nch, AX, MX, s); break;
+    case 0: spmm_shape<T, 32, 1>(c.wpb, c.chunk, m, a, mm, X, nch, AX, MX, s); break;
+    case 1: spmm_shape<T, 32, 2>(c.wpb, c.chunk, m, a, mm, X, nch, AX, MX, s); break;
+    case 2: spmm_shape<T, 32, 4>(c.wpb, c.chunk, m, a, mm, X, nch, AX, MX, s); break;
+    case 3: spmm_shape<T, 16, 1>(c.wpb, c.chunk, m, a, mm, X, nch, AX, MX, s); break;
+    case 4: spmm_shape<T, 16, 2>(c.wpb, c.chunk, m, a, mm, X, nch, AX, MX, s); break;
+    case 5: spmm_shape<T, 8, 1>(c.wpb, c.chunk, m, a, mm, X, nch, AX, MX, s); break;
+    case 6: spmm_shape<T, 8, 2>(c.wpb, c.chunk, m, a, mm, X, nch, AX, MX, s); break;
+    default: spmm_shape<T, 4, 1>(c.wpb, c.chunk, m, a, mm, X, nch, AX, MX, s); break;
   }
 }
 
 template <typename T, int LPR, int CPL, int MODE>
-void row_shape(int wpb, const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const int* rows,
+void row_shape(int wpb, int chunk, const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const int* rows,
                int nrows, const T* X, T* Out, const T* B, const T* shift, int nch, double omega, cudaStream_t s) {
   const int per_block = wpb * (32 / LPR);
-  row_update_kernel<T, LPR, CPL, MODE><<<blocks_for(nrows, per_block), wpb * 32, 0, s>>>(
-      m.row_ptr.get(), m.col.get(), a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, (T)omega);
+  int grid, groups;
+  row_grid((const void*)row_update_kernel<T, LPR, CPL, MODE>, wpb * 32, blocks_for(nrows, per_block), per_block,
+           chunk, grid, groups);
+  row_update_kernel<T, LPR, CPL, MODE><<<grid, wpb * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, da, dm, rows,
+                                                                 nrows, X, Out, B, shift, nch, (T)omega, groups);
   check_launch("row_update_kernel");
 }
 template <typename T, int MODE>
 void row_launch(RowCfg c, const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const int* rows,
                 int nrows, const T* X, T* Out, const T* B, const T* shift, int nch, double omega, cudaStream_t s) {
   switch (c.shape) {
-    case 0: row_shape<T, 32, 1, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 1: row_shape<T, 32, 2, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 2: row_shape<T, 32, 4, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 3: row_shape<T, 16, 1, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 4: row_shape<T, 16, 2, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 5: row_shape<T, 8, 1, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 6: row_shape<T, 8, 2, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    default: row_shape<T, 4, 1, MODE>(c.wpb, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 0: row_shape<T, 32, 1, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 1: row_shape<T, 32, 2, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 2: row_shape<T, 32, 4, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 3: row_shape<T, 16, 1, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 4: row_shape<T, 16, 2, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 5: row_shape<T, 8, 1, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 6: row_shape<T, 8, 2, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    default: row_shape<T, 4, 1, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
   }
 }
 
@@ -616,7 +729,9 @@ RowCfg tune_rows(int kind, int tsize, int nch, int n, cudaStream_t s, F&& launch
   for (int sh = 0; sh < kNumShapes; ++sh) {
     if (!shape_ok(sh, nch)) continue;
     for (int wpb : kWPB) {
-      const RowCfg c{sh, wpb};
+      RowCfg c;
+      c.shape = sh;
+      c.wpb = wpb;
       launch(c);
       check_cuda(cudaEventRecord(e0, s), "cudaEventRecord");
       for (int q = 0; q < 3; ++q) launch(c);
@@ -626,6 +741,20 @@ RowCfg tune_rows(int kind, int tsize, int nch, int n, cudaStream_t s, F&& launch
       check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
       if (ms < best_ms) { best_ms = ms; best = c; }
     }
+  }
+  // then the chunk length for the chosen shape
+  for (int ch : kChunks) {
+    if (ch == best.chunk) continue;
+    RowCfg c = best;
+    c.chunk = ch;
+    launch(c);
+    check_cuda(cudaEventRecord(e0, s), "cudaEventRecord");
+    for (int q = 0; q < 3; ++q) launch(c);
+    check_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
+    check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float ms = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+    if (ms < best_ms) { best_ms = ms; best = c; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -828,7 +957,7 @@ void scale_rhs(const T* MU, const double* theta, int n, int k, int ld, T* B, cud
 }
 
 // Text of the tuned row-kernel shapes, one line per entry:
-// "kind bytes nch rows -> lanes_per_row chunks_per_lane warps_per_block".
+// "kind bytes nch rows -> lanes_per_row chunks_per_lane warps_per_block rows_per_cta_chunk".
 std::string tuned_report() {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   std::string out;
@@ -839,7 +968,7 @@ std::string tuned_report() {
     out += std::string(kinds[std::get<0>(k)]) + " " + std::to_string(std::get<1>(k)) + " " +
            std::to_string(std::get<2>(k)) + " " + std::to_string(std::get<3>(k)) + " -> " +
            std::to_string(kShapeLPR[c.shape]) + " " + std::to_string(kShapeCPL[c.shape]) + " " +
-           std::to_string(c.wpb) + "\n";
+           std::to_string(c.wpb) + " " + std::to_string(c.chunk) + "\n";
   }
   return out;
 }
