@@ -51,7 +51,18 @@ typedef enum {
   BMG_ERR_TIMEOUT = 9        /* a bounded wait inside a kernel expired           */
 } bmg_status;
 
-typedef enum { BMG_SMOOTH_JACOBI = 0, BMG_SMOOTH_MCGS = 1, BMG_SMOOTH_MCSGS = 2 } bmg_smoother;
+/* Smoothers of the source problems (Remark on smoothers after Alg. 1; Sec. 5.3):
+ *   BMG_SMOOTH_JACOBI    damped Jacobi, omega (default 2/3)
+ *   BMG_SMOOTH_MCGS      multicolour Gauss-Seidel, colours ascending
+ *   BMG_SMOOTH_MCSGS     symmetric: ascending then descending colours
+ *   BMG_SMOOTH_KACZMARZ  multicolour Kaczmarz, the paper's smoother for the shifted
+ *      indefinite problems (Sec. 5.3, Table 2): row r projects x onto its equation,
+ *      x += omega (b_r - k_r^T x) / ||k_r||^2 k_r, k_r = a_r - s m_r; the rows of one
+ *      colour of a distance-2 colouring (greedy in the same priority) share no column
+ *      and are projected at once, which equals the sequential sweep in (colour,
+ *      index) order.  Use omega = 1 for plain Kaczmarz.                           */
+typedef enum { BMG_SMOOTH_JACOBI = 0, BMG_SMOOTH_MCGS = 1, BMG_SMOOTH_MCSGS = 2,
+               BMG_SMOOTH_KACZMARZ = 3 } bmg_smoother;
 
 /* Source problem smoothed for each Ritz pair (theta_i, u_i), lambda_i = theta_i + sigma:
  *   BMG_FORM_SHIFTED:     (A - sigma M) x_i = theta_i M u_i   (Eq. pb-m-s, Alg. 3 step 3)
@@ -92,12 +103,18 @@ typedef struct {
                              /*    (float32) fused multiply-adds on the CUDA cores  */
   int autotune;              /* 1: row-kernel shapes timed on first use, 0: default */
   int graphs;                /* 1: cycles replayed as CUDA graphs, 0: eager launches*/
+  int adaptive_shift;        /* 1: before the eigensolve of every cycle but the     */
+                             /*    solve's first, the shift becomes the mean        */
+                             /*    Rayleigh quotient x^T A x / x^T M x of the k     */
+                             /*    columns of X (the previous shift plus the mean   */
+                             /*    shifted quotient; Alg. 3 step 4, Sec. 5.3); the  */
+                             /*    first cycle uses sigma.  0: sigma throughout.    */
 } bmg_options;
 
 /* Fills the defaults: Jacobi, nu=2, omega=2/3, shifted form, full depth,
  * 6 intermediate cycles, no intermediate tolerance, 200 finest cycles, float64,
  * switch_tol 1e-7 (near the float32 floor of the relative residual), no stop,
- * no resume, tensor cores, autotuned shapes and CUDA graphs on.  autotune and
+ * no resume, tensor cores, autotuned shapes and CUDA graphs on, fixed shift.  autotune and
  * graphs change no result (the tests check bit-identical outputs); tensor_cores
  * changes the rounding of the products.                                          */
 void bmg_default_options(bmg_options* opt);
@@ -116,6 +133,7 @@ typedef struct {
   int history_level[256];    /* level of each cycle                               */
   int history_fp32[256];     /* 1 if the cycle ran with float32 blocks            */
   double history_resid[256]; /* largest wanted relative residual after the cycle  */
+  double final_shift;        /* shift of the last cycle (sigma unless adaptive)   */
 } bmg_solve_info;
 
 /* ---------------------------------------------------------------- set-up ----- */
@@ -239,6 +257,10 @@ bmg_status bmg_get_galerkin(const bmg_problem* p, int f, int j, double* a, doubl
 /* Colouring of level l (1..L): colour [n] host; returns the colour count.        */
 bmg_status bmg_get_colouring(const bmg_problem* p, int level, int* colour,
                              int* n_colours);
+
+/* Distance-2 colouring of level l (1..L), built on first use (the Kaczmarz
+ * smoother's): colour [n] host; returns the colour count.                        */
+bmg_status bmg_get_colouring2(bmg_problem* p, int level, int* colour, int* n_colours);
 
 /* ------------------------------------- individual cycle steps (device data) -- */
 /* All pointers below are device memory; all calls are asynchronous on `stream`.

@@ -29,9 +29,13 @@ Readings of the paper used here (each listed in the design notes):
     correction from zero on its Galerkin operator, passes its residual down, and
     the corrections are prolonged back and added.  Levels whose shifted diagonal is
     not safely positive are skipped (with all coarser ones).
-  * fixed shift (Remark on the choice of shifts allows it); intermediate levels run
-    a fixed number of cycles; the finest level cycles until every wanted pair has
-    relative residual ||A u - lambda M u||_2 / (||A||_1 ||u||_2) <= tol.
+  * shift: fixed by default (the Remark on the choice of shifts allows it), or, with
+    adaptive_shift, updated before the eigensolve of every cycle after the first
+    (Alg. 3 step 4; Sec. 5.3): the previous shift plus the mean of the shifted
+    Rayleigh quotients of the source solutions in X, i.e. mu = mean_i x_i^T A x_i /
+    x_i^T M x_i over the k columns of X; the first cycle uses the given shift.  Intermediate levels run a fixed number of cycles; the finest level
+    cycles until every wanted pair has relative residual
+    ||A u - lambda M u||_2 / (||A||_1 ||u||_2) <= tol.
 """
 from __future__ import annotations
 
@@ -49,7 +53,7 @@ DIAG_MARGIN = 0.25
 
 @dataclass
 class Options:
-    smoother: str = "jacobi"        # "jacobi" | "mcgs" | "mcsgs"
+    smoother: str = "jacobi"        # "jacobi" | "mcgs" | "mcsgs" | "kaczmarz"
     nu: int = 2
     omega: float = 2.0 / 3.0
     form: str = "shifted"           # "shifted" (Eq. pb-m-s) | "homogeneous"
@@ -57,6 +61,7 @@ class Options:
     cycles_intermediate: int = 6     # cycle cap on levels 2..L-1
     tol_intermediate: float = -1.0   # early stop on levels 2..L-1 (negative: none)
     max_cycles: int = 200
+    adaptive_shift: bool = False     # Alg. 3 step 4: shift from the Rayleigh quotients of X
 
 
 @dataclass
@@ -68,6 +73,7 @@ class Hierarchy:
     M: list = field(default_factory=list)
     P: list = field(default_factory=list)       # P[l]: level l-1 -> l
     colour: list = field(default_factory=list)
+    colour2: list = field(default_factory=list)   # distance-2 colourings (Kaczmarz)
     GA: dict = field(default_factory=dict)      # GA[f][j]: Galerkin of A_f on level j
     GM: dict = field(default_factory=dict)
 
@@ -77,18 +83,20 @@ class Hierarchy:
 
 
 def build_hierarchy(coarse_verts, coarse_tris, levels: int, amplitude=0.0,
-                    coefs=None, colour=True) -> Hierarchy:
+                    coefs=None, colour=True, colour2=False) -> Hierarchy:
     """Refine, assemble, and build prolongations and Galerkin sets (setup, a0)."""
     meshes = mesh.surface_hierarchy(coarse_verts, coarse_tris, levels, amplitude, coefs)
     H = Hierarchy()
     H.verts.append(None); H.tris.append(None); H.A.append(None); H.M.append(None)
-    H.P.append(None); H.colour.append(None)
+    H.P.append(None); H.colour.append(None); H.colour2.append(None)
     for l in range(1, levels + 1):
         v, t, par = meshes[l]
         A, M = fem.assemble(v, t)
         H.verts.append(v); H.tris.append(t); H.A.append(A); H.M.append(M)
         H.P.append(None if l == 1 else multilevel.prolongation(par, meshes[l - 1][0].shape[0]))
         H.colour.append(multilevel.greedy_colouring(A.indptr, A.indices) if colour else None)
+        H.colour2.append(multilevel.greedy_colouring(*multilevel.distance2_pattern(A.indptr, A.indices))
+                         if colour2 else None)
     for f in range(2, levels + 1):
         ga = {f: H.A[f]}
         gm = {f: H.M[f]}
@@ -162,7 +170,9 @@ def residuals(A, M, U, lam, anorm=None):
     return np.linalg.norm(R, axis=0) / (anorm * np.linalg.norm(U, axis=0))
 
 
-def smooth(A, M, X, B, s, colour, opt: Options):
+def smooth(A, M, X, B, s, colour, opt: Options, colour2=None):
+    if opt.smoother == "kaczmarz":
+        return multilevel.kaczmarz(A, M, X, B, s, colour2, opt.nu, opt.omega)
     if opt.smoother == "jacobi":
         return multilevel.jacobi(A, M, X, B, s, opt.omega, opt.nu)
     if opt.smoother in ("mcgs", "mcsgs"):
@@ -195,7 +205,7 @@ def source_smoothing(H: Hierarchy, f: int, U, MU, theta, lam, sigma, opt: Option
         s = lam.copy()
         B = np.zeros_like(U)
     A, M = H.A[f], H.M[f]
-    X = smooth(A, M, U, B, s, H.colour[f], opt)
+    X = smooth(A, M, U, B, s, H.colour[f], opt, H.colour2[f])
     levels = vleg_levels(H, f, s, opt)
     if not levels:
         return X
@@ -204,7 +214,7 @@ def source_smoothing(H: Hierarchy, f: int, U, MU, theta, lam, sigma, opt: Option
     for idx, j in enumerate(levels):
         Ga, Gm = H.GA[f][j], H.GM[f][j]
         rj = H.P[j + 1].T @ r[j + 1]
-        ej = smooth(Ga, Gm, np.zeros_like(rj), rj, s, H.colour[j], opt)
+        ej = smooth(Ga, Gm, np.zeros_like(rj), rj, s, H.colour[j], opt, H.colour2[j])
         e[j] = ej
         if idx + 1 < len(levels):
             r[j] = rj - multilevel.shifted_apply(Ga, Gm, ej, s)
@@ -219,13 +229,24 @@ class CycleResult:
     U: np.ndarray
     resid: np.ndarray
     X_next: np.ndarray | None
+    sigma: float = 0.0
+
+
+def mean_rayleigh_quotient(X, AX, MX) -> float:
+    """Mean over the columns of X of x^T A x / x^T M x (Sec. 5.3, the shift update)."""
+    return float(np.mean(np.sum(X * AX, axis=0) / np.sum(X * MX, axis=0)))
 
 
 def cycle(H: Hierarchy, f: int, X, sigma: float, k: int, n_wanted: int, tol: float,
-          opt: Options, anorm=None, smooth_if_converged=False):
-    """One BMG cycle on level f: enriched RR, residual check, source smoothing."""
+          opt: Options, anorm=None, smooth_if_converged=False, first=True):
+    """One BMG cycle on level f: enriched RR, residual check, source smoothing.
+    With opt.adaptive_shift every cycle but the solve's first takes as its shift the
+    mean Rayleigh quotient of X, the source solutions of the previous cycle
+    (returned as CycleResult.sigma); otherwise the shift is `sigma`."""
     A, M = H.A[f], H.M[f]
     AX, MX = A @ X, M @ X
+    if opt.adaptive_shift and not first:
+        sigma = mean_rayleigh_quotient(X, AX, MX)
     Ahat, Mhat = enriched_matrices(H, f, X, AX, MX)
     theta, Y = svqb_eig(Ahat, Mhat, sigma, k)
     lam = theta + sigma
@@ -239,7 +260,7 @@ def cycle(H: Hierarchy, f: int, X, sigma: float, k: int, n_wanted: int, tol: flo
     Xn = None
     if not conv or smooth_if_converged:
         Xn = source_smoothing(H, f, U, MU, theta, lam, sigma, opt)
-    return CycleResult(lam, U, resid, Xn), conv
+    return CycleResult(lam, U, resid, Xn, sigma), conv
 
 
 @dataclass
@@ -251,6 +272,7 @@ class SolveResult:
     converged: bool
     history: list
     level_lams: list        # Ritz values at the end of each level 2..L
+    shifts: list = field(default_factory=list)   # shift of every cycle
 
 
 def bfmg(H: Hierarchy, X0, k: int, n_wanted: int, sigma: float, tol: float,
@@ -258,7 +280,7 @@ def bfmg(H: Hierarchy, X0, k: int, n_wanted: int, sigma: float, tol: float,
     """Alg. 4: cycles on levels 2..L, prolongating the Ritz vectors between levels."""
     L = H.levels
     X = np.array(X0, dtype=np.float64, copy=True)
-    cycles, history, level_lams = [], [], []
+    cycles, history, level_lams, shifts = [], [], [], []
     res = None
     for f in range(2, L + 1):
         if f > 2:
@@ -268,7 +290,8 @@ def bfmg(H: Hierarchy, X0, k: int, n_wanted: int, sigma: float, tol: float,
         ftol = tol if f == L else opt.tol_intermediate
         c = 0
         while True:
-            res, conv = cycle(H, f, X, sigma, k, n_wanted, ftol, opt, anorm)
+            res, conv = cycle(H, f, X, sigma, k, n_wanted, ftol, opt, anorm, first=not shifts)
+            shifts.append(res.sigma)
             c += 1
             history.append((f, c, float(res.resid[:n_wanted].max())))
             if verbose:
@@ -279,4 +302,4 @@ def bfmg(H: Hierarchy, X0, k: int, n_wanted: int, sigma: float, tol: float,
         cycles.append(c)
         level_lams.append(res.lam.copy())
     conv = bool(np.all(res.resid[:n_wanted] <= tol))
-    return SolveResult(res.lam, res.U, res.resid, cycles, conv, history, level_lams)
+    return SolveResult(res.lam, res.U, res.resid, cycles, conv, history, level_lams, shifts)

@@ -18,6 +18,14 @@ Rows of one colour are not adjacent, so updating a colour at once equals the
 sequential Gauss-Seidel sweep over that colour's rows.
 Colouring: sequential greedy in descending priority; priority(v) = (splitmix64(v), v);
 each vertex takes the smallest colour unused by its already coloured neighbours.
+
+Kaczmarz relaxation (Sec. 5.3, Table 2: the paper's smoother for the shifted indefinite
+source problems): row r of K = A - s M projects x onto the hyperplane of its equation,
+x <- x + omega (b_r - k_r^T x) / ||k_r||^2 k_r, which changes every x_j with k_rj != 0.
+Two rows can be projected at once when no column carries a nonzero of both, i.e.
+when their vertices are more than two edges apart; a greedy colouring of the
+distance-2 graph (same priorities) groups such rows, and projecting the rows of one
+colour at once equals the sequential sweep in (colour, index) order.
 """
 from __future__ import annotations
 
@@ -130,4 +138,60 @@ def gauss_seidel_sequential(A, M, x, b, s: float, colour, symmetric: bool = True
             acc += (A.data[p] - s * M.data[p]) * x[j]
         d = A[i, i] - s * M[i, i]
         x[i] = x[i] + (b[i] - acc) / d
+    return x
+
+
+def distance2_pattern(row_ptr: np.ndarray, col: np.ndarray):
+    """CSR (row_ptr, col) of the vertices within two edges of each vertex (itself
+    included), ascending columns."""
+    n = row_ptr.shape[0] - 1
+    G = sp.csr_matrix((np.ones(col.shape[0]), col, row_ptr), shape=(n, n))
+    G2 = (G @ G).tocsr()
+    G2.sort_indices()
+    return G2.indptr.astype(np.int64), G2.indices.astype(np.int64)
+
+
+def row_norms(A, M):
+    """Per row: sum_j a_rj^2, sum_j a_rj m_rj, sum_j m_rj^2 (shared pattern), so that
+    ||a_r - s m_r||^2 = na - 2 s nam + s^2 nm."""
+    A = A.tocsr(); M = M.tocsr()
+    na = np.asarray(A.multiply(A).sum(axis=1)).ravel()
+    nam = np.asarray(A.multiply(M).sum(axis=1)).ravel()
+    nm = np.asarray(M.multiply(M).sum(axis=1)).ravel()
+    return na, nam, nm
+
+
+def kaczmarz(A, M, X, B, s, colour2, nu: int, omega: float = 1.0):
+    """nu multicolour Kaczmarz sweeps on (A - s_i M) x_i = b_i, colours ascending,
+    colour2 a distance-2 colouring."""
+    A = A.tocsr(); M = M.tocsr()
+    X = X.copy()
+    s = np.asarray(s)[None, :]
+    na, nam, nm = row_norms(A, M)
+    ncol = int(colour2.max()) + 1
+    rows_of = [np.nonzero(colour2 == c)[0] for c in range(ncol)]
+    for _ in range(nu):
+        for c in range(ncol):
+            r = rows_of[c]
+            Ar, Mr = A[r], M[r]
+            R = B[r] - (Ar @ X - (Mr @ X) * s)
+            nrm = na[r][:, None] - 2.0 * s * nam[r][:, None] + s * s * nm[r][:, None]
+            Cf = omega * R / nrm
+            X = X + (Ar.T @ Cf) - (Mr.T @ Cf) * s
+    return X
+
+
+def kaczmarz_sequential(A, M, x, b, s: float, colour2, omega: float = 1.0):
+    """One sequential Kaczmarz sweep over the rows in (colour, index) order.
+
+    Pure-Python definition used to pin the multicolour form on small meshes.
+    """
+    A = A.tocsr(); M = M.tocsr()
+    x = x.copy()
+    n = x.shape[0]
+    for i in sorted(range(n), key=lambda v: (int(colour2[v]), v)):
+        cols = A.indices[A.indptr[i]:A.indptr[i + 1]]
+        k = A.data[A.indptr[i]:A.indptr[i + 1]] - s * M.data[M.indptr[i]:M.indptr[i + 1]]
+        res = b[i] - float(np.dot(k, x[cols]))
+        x[cols] = x[cols] + omega * res / float(np.dot(k, k)) * k
     return x

@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbmg.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "bmg.h")
 
-SMOOTHERS = {"jacobi": 0, "mcgs": 1, "mcsgs": 2}
+SMOOTHERS = {"jacobi": 0, "mcgs": 1, "mcsgs": 2, "kaczmarz": 3}
 FORMS = {"shifted": 0, "homogeneous": 1}
 PRECISIONS = {"fp64": 0, "fp32": 1}
 STATUS = {0: "BMG_OK", 1: "BMG_ERR_INVALID_ARG", 2: "BMG_ERR_CUDA", 3: "BMG_ERR_OOM",
@@ -36,14 +36,16 @@ class Options(C.Structure):
                 ("vcycle_depth", C.c_int), ("cycles_intermediate", C.c_int),
                 ("tol_intermediate", C.c_double), ("max_cycles", C.c_int), ("precision", C.c_int),
                 ("switch_tol", C.c_double), ("stop_after_cycles", C.c_int), ("resume", C.c_int),
-                ("tensor_cores", C.c_int), ("autotune", C.c_int), ("graphs", C.c_int)]
+                ("tensor_cores", C.c_int), ("autotune", C.c_int), ("graphs", C.c_int),
+                ("adaptive_shift", C.c_int)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("levels", C.c_int), ("cycles", C.c_int * 32), ("total_cycles", C.c_int),
                 ("converged", C.c_int), ("max_resid", C.c_double), ("max_dense_err", C.c_double),
                 ("fp32_cycles", C.c_int), ("n_history", C.c_int), ("history_level", C.c_int * 256),
-                ("history_fp32", C.c_int * 256), ("history_resid", C.c_double * 256)]
+                ("history_fp32", C.c_int * 256), ("history_resid", C.c_double * 256),
+                ("final_shift", C.c_double)]
 
     def history(self):
         """[(level, fp32, max wanted residual)] per cycle (first 256 cycles)."""
@@ -72,6 +74,7 @@ def _load():
         "bmg_get_csr": (i, [vp, i, vp, vp, vp, vp]),
         "bmg_get_galerkin": (i, [vp, i, i, vp, vp]),
         "bmg_get_colouring": (i, [vp, i, vp, P(C.c_int)]),
+        "bmg_get_colouring2": (i, [vp, i, vp, P(C.c_int)]),
         "bmg_spmm": (i, [vp, i, i, vp, i, i, vp, vp, vp]),
         "bmg_smooth": (i, [vp, i, i, vp, vp, vp, i, i, i, i, d, vp, vp]),
         "bmg_spmm_f32": (i, [vp, i, i, vp, i, i, vp, vp, vp]),
@@ -136,7 +139,7 @@ def _stream():
 def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_depth=99,
             cycles_intermediate=6, tol_intermediate=-1.0, max_cycles=200, precision="fp64",
             switch_tol=1e-7, stop_after_cycles=0, resume=False, tensor_cores=True, autotune=True,
-            graphs=True) -> Options:
+            graphs=True, adaptive_shift=False) -> Options:
     o = Options()
     LIB.bmg_default_options(C.byref(o))
     o.smoother = SMOOTHERS[smoother]
@@ -154,6 +157,7 @@ def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_dep
     o.tensor_cores = int(bool(tensor_cores))
     o.autotune = int(bool(autotune))
     o.graphs = int(bool(graphs))
+    o.adaptive_shift = int(bool(adaptive_shift))
     return o
 
 
@@ -220,6 +224,14 @@ class Problem:
         c = np.empty(n, np.int32)
         nc = C.c_int()
         _check(LIB.bmg_get_colouring(self.h, level, _ptr(c), C.byref(nc)))
+        return c, nc.value
+
+    def colouring2(self, level):
+        """Distance-2 colouring of a level (the Kaczmarz smoother's)."""
+        n, _, _ = self.sizes(self.level_refinement(level))
+        c = np.empty(n, np.int32)
+        nc = C.c_int()
+        _check(LIB.bmg_get_colouring2(self.h, level, _ptr(c), C.byref(nc)))
         return c, nc.value
 
     # ---- individual cycle steps on torch CUDA tensors ([N][ld] float64) -------

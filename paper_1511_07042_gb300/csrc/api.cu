@@ -117,6 +117,7 @@ extern "C" void bmg_default_options(bmg_options* o) {
   o->tensor_cores = 1;
   o->autotune = 1;
   o->graphs = 1;
+  o->adaptive_shift = 0;
 }
 
 extern "C" const char* bmg_last_error(void) { return g_last_error.c_str(); }
@@ -282,10 +283,46 @@ extern "C" bmg_status bmg_get_galerkin(const bmg_problem* p, int f, int j, doubl
 extern "C" bmg_status bmg_get_colouring(const bmg_problem* p, int level, int* colour, int* n_colours) {
   return guarded([&] {
     check_levels(p, level, level);
-    if (colour) BMG_CUDA(cudaMemcpy(colour, p->lev[level].colour.get(), sizeof(int) * p->meshOf(level).n, cudaMemcpyDeviceToHost));
-    if (n_colours) *n_colours = p->lev[level].n_colours;
+    if (colour) BMG_CUDA(cudaMemcpy(colour, p->lev[level].col1.colour.get(), sizeof(int) * p->meshOf(level).n, cudaMemcpyDeviceToHost));
+    if (n_colours) *n_colours = p->lev[level].col1.n_colours;
   });
 }
+
+extern "C" bmg_status bmg_get_colouring2(bmg_problem* p, int level, int* colour, int* n_colours) {
+  return guarded([&] {
+    check_levels(p, level, level);
+    colour_level2(p->meshOf(level), p->lev[level], p->stream);
+    const Colouring& c = p->lev[level].col2;
+    if (colour) BMG_CUDA(cudaMemcpy(colour, c.colour.get(), sizeof(int) * p->meshOf(level).n, cudaMemcpyDeviceToHost));
+    if (n_colours) *n_colours = c.n_colours;
+  });
+}
+
+namespace bmg {
+// Distance-2 colourings of every level and the row norms of every operator set (and
+// of their float32 copies), for the Kaczmarz smoother; built once.
+void ensure_kaczmarz(bmg_problem* p, bool fp32) {
+  cudaStream_t s = p->stream;
+  for (int l = 1; l <= p->L; ++l) colour_level2(p->meshOf(l), p->lev[l], s);
+  for (int f = 2; f <= p->L; ++f)
+    for (int j = 1; j <= f; ++j) {
+      OpSet& o = p->ops[f][j];
+      const Mesh& mj = p->meshOf(j);
+      if (!o.na.get()) {
+        o.na.alloc(mj.n); o.nam.alloc(mj.n); o.nm.alloc(mj.n);
+        row_norms<double>(mj, p->opA(f, j), p->opM(f, j), o.na.get(), o.nam.get(), o.nm.get(), s);
+      }
+      if (fp32 && !p->ops32.empty()) {
+        OpSet32& q = p->ops32[f][j];
+        if (!q.na.get()) {
+          q.na.alloc(mj.n); q.nam.alloc(mj.n); q.nm.alloc(mj.n);
+          row_norms<float>(mj, q.a.get(), q.m.get(), q.na.get(), q.nam.get(), q.nm.get(), s);
+        }
+      }
+    }
+  BMG_CUDA(cudaStreamSynchronize(s));
+}
+}  // namespace bmg
 
 // ------------------------------------------------------------- step entries ---
 static const double* opDA_or_compute(const bmg_problem* p, int f, int j) {
@@ -323,10 +360,18 @@ extern "C" bmg_status bmg_smooth(const bmg_problem* p, int f, int level, double*
     } else if (smoother == BMG_SMOOTH_MCGS || smoother == BMG_SMOOTH_MCSGS) {
       const Level& lv = p->lev[level];
       for (int it = 0; it < nu; ++it) {
-        for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
+        for (int c = 0; c < lv.col1.n_colours; ++c) gs_colour_sweep(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
         if (smoother == BMG_SMOOTH_MCSGS)
-          for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
+          for (int c = lv.col1.n_colours - 1; c >= 0; --c) gs_colour_sweep(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
       }
+    } else if (smoother == BMG_SMOOTH_KACZMARZ) {
+      bmg_problem* pm = const_cast<bmg_problem*>(p);
+      ensure_kaczmarz(pm, false);
+      const Level& lv = p->lev[level];
+      const OpSet& o = p->ops[f][level];
+      for (int it = 0; it < nu; ++it)
+        for (int c = 0; c < lv.col2.n_colours; ++c)
+          kaczmarz_colour_sweep<double>(m, lv, c, a, mm, o.na.get(), o.nam.get(), o.nm.get(), X, B, sft, ld, omega, s);
     } else {
       fail(BMG_ERR_INVALID_ARG, "unknown smoother");
     }
@@ -448,12 +493,18 @@ namespace {
 // Operators of finest level f on level j in the block arithmetic T.
 template <typename T> struct Ops;
 template <> struct Ops<double> {
+  static const double* NA(const bmg_problem* p, int f, int j) { return p->ops[f][j].na.get(); }
+  static const double* NAM(const bmg_problem* p, int f, int j) { return p->ops[f][j].nam.get(); }
+  static const double* NM(const bmg_problem* p, int f, int j) { return p->ops[f][j].nm.get(); }
   static const double* A(const bmg_problem* p, int f, int j) { return p->opA(f, j); }
   static const double* M(const bmg_problem* p, int f, int j) { return p->opM(f, j); }
   static const double* DA(const bmg_problem* p, int f, int j) { return p->opDA(f, j); }
   static const double* DM(const bmg_problem* p, int f, int j) { return p->opDM(f, j); }
 };
 template <> struct Ops<float> {
+  static const float* NA(const bmg_problem* p, int f, int j) { return p->ops32[f][j].na.get(); }
+  static const float* NAM(const bmg_problem* p, int f, int j) { return p->ops32[f][j].nam.get(); }
+  static const float* NM(const bmg_problem* p, int f, int j) { return p->ops32[f][j].nm.get(); }
   static const float* A(const bmg_problem* p, int f, int j) { return p->ops32[f][j].a.get(); }
   static const float* M(const bmg_problem* p, int f, int j) { return p->ops32[f][j].m.get(); }
   static const float* DA(const bmg_problem* p, int f, int j) { return p->ops32[f][j].da.get(); }
@@ -629,10 +680,17 @@ void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, cons
   }
   if (Xin != Xout) BMG_CUDA(cudaMemcpyAsync(Xout, Xin, bytes, cudaMemcpyDeviceToDevice, s));
   const Level& lv = p->lev[j];
+  if (o.smoother == BMG_SMOOTH_KACZMARZ) {
+    for (int it = 0; it < o.nu; ++it)
+      for (int c = 0; c < lv.col2.n_colours; ++c)
+        kaczmarz_colour_sweep<T>(m, lv, c, a, mm, Ops<T>::NA(p, f, j), Ops<T>::NAM(p, f, j), Ops<T>::NM(p, f, j), Xout,
+                                 B, shift, ld, o.omega, s);
+    return;
+  }
   for (int it = 0; it < o.nu; ++it) {
-    for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s, work);
+    for (int c = 0; c < lv.col1.n_colours; ++c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s, work);
     if (o.smoother == BMG_SMOOTH_MCSGS)
-      for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s, work);
+      for (int c = lv.col1.n_colours - 1; c >= 0; --c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s, work);
   }
 }
 
@@ -682,7 +740,7 @@ std::unique_ptr<SolveWork> make_work(bmg_problem* p, int k, cudaStream_t s) {
   w.res.alloc(2 * k);
   w.rank.alloc(1);
   w.dquality.alloc(1);
-  BMG_CUDA(cudaMallocHost(&w.hbuf, sizeof(double) * (3 * (size_t)k + 8)));  // res, lam, quality, rank
+  BMG_CUDA(cudaMallocHost(&w.hbuf, sizeof(double) * (5 * (size_t)k + 8)));  // res, lam, quality, rank, Gram diagonals
   w.AQ.resize(L + 1);
   w.MQ.resize(L + 1);
   const Mesh& m1 = p->meshOf(1);
@@ -785,9 +843,12 @@ void run_graph(bmg_problem* p, SolveWork& w, const std::tuple<int, int, int, int
 // One BMG cycle on level f with blocks of arithmetic T (steps 1-5 of the file
 // header).  Smoothing (step 5) runs unless the wanted pairs met ftol or `last` is
 // set.  Returns whether every wanted pair met ftol.
+// With bmg_options.adaptive_shift, every cycle of a solve but its first replaces
+// sigma (in/out) by the mean Rayleigh quotient of the columns of X, read from the
+// diagonals of this cycle's Grams before its eigensolve (Alg. 3 step 4; Sec. 5.3).
 template <typename T>
-bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_options& o, double sigma, int k,
-               int n_wanted, double ftol, bool last, CycleState& cs) {
+bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_options& o, double& sigma, int k,
+               int n_wanted, double ftol, bool last, bool first, CycleState& cs) {
   cudaStream_t s = w.s;
   const int ld = b.ld, n1 = w.n1, nh = w.nh;
   const Mesh& mf = p->meshOf(f);
@@ -800,7 +861,7 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
   int* htc = reinterpret_cast<int*>(w.hbuf + 3 * k + 2);   // tensor-core wait expired
   const bool tc = o.tensor_cores && k <= kTcMaxK;
   // 1-4: products, Grams and couplings, enriched eigensolve, Ritz vectors, residuals
-  auto part_a = [&]() {
+  auto part_a1 = [&]() {
     // 1-2: products, Grams, couplings Q^T AX, Q^T MX by the restriction chain
     spmm_am<T>(mf, Af, Mf, b.X, ld, b.AX, b.MX, s);
     if (tc) {
@@ -818,6 +879,10 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
       ca = b.cA[j - 1];
       cm = b.cB[j - 1];
     }
+  };
+  auto part_a2 = [&]() {
+    const T* ca = b.cA[1];
+    const T* cm = b.cB[1];
     prof_begin(KC_SMALL, s);
     assemble_hat_kernel<T><<<grid_of((size_t)nh * nh, 256), 256, 0, s>>>(w.AQ[f].get(), ca, w.GA.get(), n1, k, ld, w.Ahat.get());
     check_launch("assemble_hat_kernel");
@@ -854,7 +919,27 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
   };
   {
     TraceRange trace("cycle: products, Rayleigh-Ritz, Ritz vectors, residuals");
-    run_graph(p, w, std::make_tuple(0, f, (int)sizeof(T), 0), part_a);
+    if (o.adaptive_shift && !first) {
+      // the shift from the Rayleigh quotients of X: diagonals of the Grams
+      part_a1();
+      double* hg = w.hbuf + 3 * k + 8;   // 2k values: diag(X^T A X), diag(X^T M X)
+      BMG_CUDA(cudaMemcpy2DAsync(hg, sizeof(double), w.GA.get(), sizeof(double) * (k + 1), sizeof(double), k,
+                                 cudaMemcpyDeviceToHost, s));
+      BMG_CUDA(cudaMemcpy2DAsync(hg + k, sizeof(double), w.GM.get(), sizeof(double) * (k + 1), sizeof(double), k,
+                                 cudaMemcpyDeviceToHost, s));
+      BMG_CUDA(cudaStreamSynchronize(s));
+      double mu = 0.0;
+      for (int i = 0; i < k; ++i) mu += hg[i] / hg[k + i];
+      mu /= k;
+      if (!std::isfinite(mu)) fail(BMG_ERR_NONFINITE, "adaptive shift not finite");
+      sigma = mu;
+      part_a2();
+    } else {
+      run_graph(p, w, std::make_tuple(0, f, (int)sizeof(T), 0), [&]() {
+        part_a1();
+        part_a2();
+      });
+    }
   }
   BMG_CUDA(cudaStreamSynchronize(s));
   if (tc && *htc) fail(BMG_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel expired");
@@ -928,10 +1013,11 @@ bmg_options checked_options(const bmg_problem* p, int k, int n_wanted, double si
     fail(BMG_ERR_INVALID_ARG, "need 1 <= n_wanted <= k <= min(N_2, 160) and N_1 + k <= 224");
   if ((!X0 && o.resume != 1) || !evals) fail(BMG_ERR_INVALID_ARG, "X0 (unless resuming) and evals are required");
   if (!(tol > 0.0) || !std::isfinite(sigma)) fail(BMG_ERR_INVALID_ARG, "bad tol or sigma");
-  if (o.nu < 1 || o.nu > 64 || o.smoother < 0 || o.smoother > 2 || o.form < 0 || o.form > 1 ||
+  if (o.nu < 1 || o.nu > 64 || o.smoother < 0 || o.smoother > 3 || o.form < 0 || o.form > 1 ||
       o.max_cycles < 1 || o.cycles_intermediate < 1 || !(o.omega > 0.0) || o.precision < 0 ||
       o.precision > 1 || !(o.switch_tol > 0.0) || o.stop_after_cycles < 0 || o.resume < 0 || o.resume > 1 ||
-      o.tensor_cores < 0 || o.tensor_cores > 1 || o.autotune < 0 || o.autotune > 1 || o.graphs < 0 || o.graphs > 1)
+      o.tensor_cores < 0 || o.tensor_cores > 1 || o.autotune < 0 || o.autotune > 1 || o.graphs < 0 || o.graphs > 1 ||
+      o.adaptive_shift < 0 || o.adaptive_shift > 1)
     fail(BMG_ERR_INVALID_ARG, "bad options");
   return o;
 }
@@ -947,6 +1033,8 @@ struct StateHead {
   double sigma, tol, max_dense_err;
   int32_t smoother, nu, form, vcycle_depth, cycles_intermediate, max_cycles, precision, tensor_cores;
   double omega, tol_intermediate, switch_tol;
+  int32_t adaptive_shift, pad3;
+  double mu;                       // shift of the next cycle (adaptive_shift)
 };
 constexpr uint32_t kStateMagic = 0x53474d42u;   // "BMGS"
 constexpr uint32_t kStateVersion = 2;
@@ -958,6 +1046,7 @@ void head_options(StateHead& h, const bmg_options& o) {
   h.smoother = o.smoother; h.nu = o.nu; h.form = o.form; h.vcycle_depth = o.vcycle_depth;
   h.cycles_intermediate = o.cycles_intermediate; h.max_cycles = o.max_cycles; h.precision = o.precision;
   h.tensor_cores = o.tensor_cores;
+  h.adaptive_shift = o.adaptive_shift;
   h.omega = o.omega; h.tol_intermediate = o.tol_intermediate; h.switch_tol = o.switch_tol;
 }
 bool same_options(const StateHead& h, const bmg_options& o) {
@@ -965,7 +1054,8 @@ bool same_options(const StateHead& h, const bmg_options& o) {
   head_options(g, o);
   return g.smoother == h.smoother && g.nu == h.nu && g.form == h.form && g.vcycle_depth == h.vcycle_depth &&
          g.cycles_intermediate == h.cycles_intermediate && g.max_cycles == h.max_cycles &&
-         g.precision == h.precision && g.tensor_cores == h.tensor_cores && g.omega == h.omega && g.tol_intermediate == h.tol_intermediate &&
+         g.precision == h.precision && g.tensor_cores == h.tensor_cores && g.adaptive_shift == h.adaptive_shift &&
+         g.omega == h.omega && g.tol_intermediate == h.tol_intermediate &&
          g.switch_tol == h.switch_tol;
 }
 // Checks a state's structure against the problem; returns its header.
@@ -989,7 +1079,7 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
                 const std::vector<unsigned char>* resume = nullptr, bool* stopped = nullptr) {
   TraceRange trace("bmg_solve");
   AutotuneScope tune_scope(o.autotune != 0);
-  w.use_graphs = o.graphs != 0;
+  w.use_graphs = o.graphs != 0 && !o.adaptive_shift;   // the adaptive shift reads each cycle's Grams
   const int L = p->L;
   const int n2 = p->meshOf(2).n, nL = p->meshOf(L).n;
   // the solve runs on the workspace's own non-blocking stream (capturable into CUDA
@@ -1018,7 +1108,9 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
     ensure_ops32(p);
     b32 = blocks32(p, w);
   }
+  if (o.smoother == BMG_SMOOTH_KACZMARZ) ensure_kaczmarz(p, fp32);
   CycleState cs;
+  double mu = sigma;   // the shift of the current cycle (adaptive_shift updates it)
   cs.rho.assign(k, 0.0);
   cs.lamv.assign(k, 0.0);
   int total_cycles = 0, fp32_cycles = 0;
@@ -1044,6 +1136,7 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
     fp32_cycles = h.fp32_cycles;
     for (int f = 0; f <= L && f < 33; ++f) cyc[f] = h.cyc[f];
     cs.max_dense_err = h.max_dense_err;
+    mu = h.mu;
     hist.resize(h.n_hist);
     hl.resize(h.n_info);
     hp.resize(h.n_info);
@@ -1075,7 +1168,7 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
     h.total_cycles = total_cycles; h.fp32_cycles = fp32_cycles; h.n_f = p->meshOf(f).n;
     h.n_hist = (int)hist.size(); h.n_info = (int)hr.size();
     for (int j = 0; j <= L && j < 33; ++j) h.cyc[j] = cyc[j];
-    h.sigma = sigma; h.tol = tol; h.max_dense_err = cs.max_dense_err;
+    h.sigma = sigma; h.tol = tol; h.max_dense_err = cs.max_dense_err; h.mu = mu;
     head_options(h, o);
     std::vector<unsigned char> buf(state_bytes(h));
     unsigned char* q = buf.data();
@@ -1121,8 +1214,9 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
         break;
       }
       const bool last = c + 1 == budget;
-      const bool conv = fp32 ? run_cycle<float>(p, w, b32, f, o, sigma, k, n_wanted, ftol, last, cs)
-                             : run_cycle<double>(p, w, b64, f, o, sigma, k, n_wanted, ftol, last, cs);
+      const bool first = total_cycles == 0;
+      const bool conv = fp32 ? run_cycle<float>(p, w, b32, f, o, mu, k, n_wanted, ftol, last, first, cs)
+                             : run_cycle<double>(p, w, b64, f, o, mu, k, n_wanted, ftol, last, first, cs);
       last_level = f;
       if (total_cycles < 256) {
         double mr = 0.0;
@@ -1180,6 +1274,7 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
     for (int i = 0; i < n_wanted; ++i) mx = std::max(mx, cs.rho[i]);
     info->max_resid = mx;
     info->max_dense_err = cs.max_dense_err;
+    info->final_shift = mu;
   }
   return converged;
 }
@@ -1318,10 +1413,17 @@ extern "C" bmg_status bmg_smooth_f32(bmg_problem* p, int f, int level, float* X,
     } else if (smoother == BMG_SMOOTH_MCGS || smoother == BMG_SMOOTH_MCSGS) {
       const Level& lv = p->lev[level];
       for (int it = 0; it < nu; ++it) {
-        for (int c = 0; c < lv.n_colours; ++c) gs_colour_sweep<float>(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
+        for (int c = 0; c < lv.col1.n_colours; ++c) gs_colour_sweep<float>(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
         if (smoother == BMG_SMOOTH_MCSGS)
-          for (int c = lv.n_colours - 1; c >= 0; --c) gs_colour_sweep<float>(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
+          for (int c = lv.col1.n_colours - 1; c >= 0; --c) gs_colour_sweep<float>(m, lv, c, a, mm, da, dm, X, B, sft, ld, s);
       }
+    } else if (smoother == BMG_SMOOTH_KACZMARZ) {
+      ensure_kaczmarz(p, true);
+      const Level& lv = p->lev[level];
+      for (int it = 0; it < nu; ++it)
+        for (int c = 0; c < lv.col2.n_colours; ++c)
+          kaczmarz_colour_sweep<float>(m, lv, c, a, mm, Ops<float>::NA(p, f, level), Ops<float>::NAM(p, f, level),
+                                       Ops<float>::NM(p, f, level), X, B, sft, ld, omega, s);
     } else {
       fail(BMG_ERR_INVALID_ARG, "unknown smoother");
     }

@@ -101,21 +101,29 @@ struct Mesh {
 struct OpSet {
   DBuf<double> a, m;     // [nnz_l] values on mesh l's pattern
   DBuf<double> da, dm;   // [n_l] diagonals
+  DBuf<double> na, nam, nm;  // [n_l] sum a^2, sum a m, sum m^2 per row (Kaczmarz; on first use)
 };
 
 // float32 copies of one OpSet (precision form).
 struct OpSet32 {
   DBuf<float> a, m, da, dm;
+  DBuf<float> na, nam, nm;
+};
+
+// A colouring of a level's vertices and its rows grouped by colour.
+struct Colouring {
+  int n_colours = 0;
+  DBuf<int> colour;        // [n]
+  DBuf<int> ptr;           // [n_colours+1]
+  DBuf<int> rows;          // [n] rows grouped by colour, Morton order within a colour
+  std::vector<int> ptr_host;
+  std::vector<long long> nnz_host;  // CSR nonzeros of the rows of each colour
 };
 
 struct Level {
   int refinement = 0;
-  int n_colours = 0;
-  DBuf<int> colour;        // [n]
-  DBuf<int> colour_ptr;    // [n_colours+1]
-  DBuf<int> colour_rows;   // [n] rows grouped by colour, ascending within a colour
-  std::vector<int> colour_ptr_host;
-  std::vector<long long> colour_nnz_host;  // CSR nonzeros of the rows of each colour
+  Colouring col1;          // distance 1: Gauss-Seidel
+  Colouring col2;          // distance 2 (built on first use): Kaczmarz
 };
 
 }  // namespace bmg
@@ -217,6 +225,9 @@ void refine_mesh(const Mesh& c, Mesh& f, double amplitude, const double* sh_cons
                  const double* coefs_dev, cudaStream_t s);
 void assemble_p1(Mesh& m, cudaStream_t s);
 void colour_level(const Mesh& m, Level& lv, cudaStream_t s);
+void colour_mesh(const Mesh& m, Colouring& cl, bool distance2, cudaStream_t s);
+// distance-2 colouring of the level (Kaczmarz), rows in Morton order; once
+void colour_level2(const Mesh& m, Level& lv, cudaStream_t s);
 void locality_order(Mesh& m, Level& lv, cudaStream_t s);
 void galerkin(const Mesh& fine, const Mesh& coarse, const double* fa, const double* fm,
               double* ca, double* cm, cudaStream_t s);
@@ -239,6 +250,16 @@ template <typename T>
 void gs_colour_sweep(const Mesh& m, const Level& lv, int colour, const T* a, const T* mm,
                      const T* da, const T* dm, T* X, const T* B, const T* shift, int ld,
                      cudaStream_t s, T* scratch = nullptr);
+// One multicolour Kaczmarz colour on (A - s_c M) x_c = b_c: each row r of colour c of
+// the distance-2 colouring projects x onto its equation, x += omega res / ||k_r||^2 k_r
+// with k_r = a_r - s m_r and ||k_r||^2 = na - 2 s nam + s^2 nm.  In place on X.
+template <typename T>
+void kaczmarz_colour_sweep(const Mesh& m, const Level& lv, int colour, const T* a, const T* mm, const T* na,
+                           const T* nam, const T* nm, T* X, const T* B, const T* shift, int ld, double omega,
+                           cudaStream_t s);
+// na, nam, nm of the operator values a, mm on mesh m's pattern
+template <typename T>
+void row_norms(const Mesh& m, const T* a, const T* mm, T* na, T* nam, T* nm, cudaStream_t s);
 template <typename T>
 void residual(const Mesh& m, const T* a, const T* mm, const T* X, const T* B, const T* shift,
               int ld, T* R, cudaStream_t s);

@@ -270,6 +270,85 @@ row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
   }
 }
 
+// ---- Kaczmarz projection of the rows of one colour --------------------------
+// Row r: res_c = b_c - (A x - s_c M x)_r, coef_c = omega res_c / (na - 2 s_c nam +
+// s_c^2 nm), then x_j += coef_c (a_rj - s_c m_rj) for every column j of the row.  Rows
+// of one colour of a distance-2 colouring share no column, so the updates of a launch
+// touch disjoint rows of X and no row they read is written by another row.
+template <typename T, int LPR, int CPL>
+__global__ void __launch_bounds__(512)
+kaczmarz_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col, const T* __restrict__ va,
+                const T* __restrict__ vm, const T* __restrict__ na, const T* __restrict__ nam,
+                const T* __restrict__ nm, const int* __restrict__ rows, int nrows, T* X,
+                const T* __restrict__ B, const T* __restrict__ shift, int nch, T omega) {
+  constexpr int W = Chunk<T>::W;
+  constexpr int RPW = 32 / LPR;
+  const int lane = threadIdx.x & 31, sl = lane % LPR;
+  const int w = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * RPW + lane / LPR;
+  const bool live = w < nrows;
+  const int row = live ? rows[w] : 0;
+  T aa[CPL][W], mm[CPL][W];
+#pragma unroll
+  for (int u = 0; u < CPL; ++u)
+#pragma unroll
+    for (int q = 0; q < W; ++q) { aa[u][q] = T(0); mm[u][q] = T(0); }
+  const int b = live ? row_ptr[row] : 0;
+  const int e = live ? row_ptr[row + 1] : 0;
+  gather_row<T, LPR, CPL>(col, va, vm, X, b, e - b, nch, sl, aa, mm);
+  if (!live) return;
+  const T n_a = na[row], n_am = nam[row], n_m = nm[row];
+  T coef[CPL][W], sv[CPL][W];
+#pragma unroll
+  for (int u = 0; u < CPL; ++u) {
+    const int c = sl + LPR * u;
+#pragma unroll
+    for (int q = 0; q < W; ++q) { coef[u][q] = T(0); sv[u][q] = T(0); }
+    if (c >= nch) continue;
+    ldv(shift, c, sv[u]);
+    T bb[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) bb[q] = T(0);
+    if (B) ldv(B, (size_t)row * nch + c, bb);
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      const T res = bb[q] - (aa[u][q] - sv[u][q] * mm[u][q]);
+      const T nrm = n_a - T(2) * sv[u][q] * n_am + sv[u][q] * sv[u][q] * n_m;
+      coef[u][q] = nrm > T(0) ? omega * res / nrm : T(0);
+    }
+  }
+  for (int p = b; p < e; ++p) {
+    const int j = col[p];
+    const T a = va[p], m = vm[p];
+#pragma unroll
+    for (int u = 0; u < CPL; ++u) {
+      const int c = sl + LPR * u;
+      if (c < nch) {
+        T x[W];
+        ldv(X, (size_t)j * nch + c, x);
+#pragma unroll
+        for (int q = 0; q < W; ++q) x[q] = fma(coef[u][q], a - sv[u][q] * m, x[q]);
+        stv(X, (size_t)j * nch + c, x);
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void row_norms_kernel(const int* __restrict__ row_ptr, const T* __restrict__ va,
+                                 const T* __restrict__ vm, int n, T* na, T* nam, T* nm) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T s1 = T(0), s2 = T(0), s3 = T(0);
+  for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
+    s1 = fma(va[p], va[p], s1);
+    s2 = fma(va[p], vm[p], s2);
+    s3 = fma(vm[p], vm[p], s3);
+  }
+  na[i] = s1;
+  nam[i] = s2;
+  nm[i] = s3;
+}
+
 // ---- transfers ----------------------------------------------------------------
 // Y[v] (+)= P Xc: parents (a, b) of fine vertex v; a == b: copy, else the mean.
 template <typename T>
@@ -825,9 +904,43 @@ void jacobi_sweep(const Mesh& m, const T* a, const T* mm, const T* da, const T* 
 template <typename T>
 void gs_colour_sweep(const Mesh& m, const Level& lv, int c, const T* a, const T* mm, const T* da,
                      const T* dm, T* X, const T* B, const T* shift, int ld, cudaStream_t s, T* scratch) {
-  const int b = lv.colour_ptr_host[c], e = lv.colour_ptr_host[c + 1];
-  row_update<T, 1>(m, a, mm, da, dm, lv.colour_rows.get() + b, e - b, lv.colour_nnz_host[c], X, X, B,
+  const int b = lv.col1.ptr_host[c], e = lv.col1.ptr_host[c + 1];
+  row_update<T, 1>(m, a, mm, da, dm, lv.col1.rows.get() + b, e - b, lv.col1.nnz_host[c], X, X, B,
                    shift, ld, 1.0, s, scratch);
+}
+
+template <typename T>
+void kaczmarz_colour_sweep(const Mesh& m, const Level& lv, int c, const T* a, const T* mm, const T* na,
+                           const T* nam, const T* nm, T* X, const T* B, const T* shift, int ld, double omega,
+                           cudaStream_t s) {
+  const int b = lv.col2.ptr_host[c], e = lv.col2.ptr_host[c + 1];
+  const int nrows = e - b;
+  if (nrows == 0) return;
+  const int nch = ld / Chunk<T>::W;
+  const int* rows = lv.col2.rows.get() + b;
+  constexpr int wpb = 8;
+  prof_begin(KC_SMOOTH, s);
+  // lanes per row and chunks per lane cover the row as the default row shape does
+  if (nch <= 32)
+    kaczmarz_kernel<T, 32, 1><<<blocks_for(nrows, wpb), wpb * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, na, nam,
+                                                                          nm, rows, nrows, X, B, shift, nch, (T)omega);
+  else if (nch <= 64)
+    kaczmarz_kernel<T, 32, 2><<<blocks_for(nrows, wpb), wpb * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, na, nam,
+                                                                          nm, rows, nrows, X, B, shift, nch, (T)omega);
+  else
+    kaczmarz_kernel<T, 32, 4><<<blocks_for(nrows, wpb), wpb * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, na, nam,
+                                                                          nm, rows, nrows, X, B, shift, nch, (T)omega);
+  check_launch("kaczmarz_kernel");
+  const double nnz = (double)lv.col2.nnz_host[c];
+  // matrix rows, norms, own-row b, gathered block and the written neighbour rows
+  prof_end(KC_SMOOTH, s, (4.0 + 2.0 * tb<T>()) * nnz + 3.0 * tb<T>() * nrows + tb<T>() * ld * (nrows + 3.0 * nnz),
+           8.0 * nnz * ld);
+}
+
+template <typename T>
+void row_norms(const Mesh& m, const T* a, const T* mm, T* na, T* nam, T* nm, cudaStream_t s) {
+  row_norms_kernel<T><<<blocks_for(m.n, 256), 256, 0, s>>>(m.row_ptr.get(), a, mm, m.n, na, nam, nm);
+  check_launch("row_norms_kernel");
 }
 
 template <typename T>
@@ -986,7 +1099,11 @@ std::string tuned_report() {
   template void eig_residuals<T>(const T*, const T*, const T*, const double*, int, int, int, double*,  \
                                  int, double*, cudaStream_t);                                          \
   template void expand<T>(const T*, const T*, const double*, int, int, int, int, T*, cudaStream_t);    \
-  template void scale_rhs<T>(const T*, const double*, int, int, int, T*, cudaStream_t);
+  template void scale_rhs<T>(const T*, const double*, int, int, int, T*, cudaStream_t);                \
+  template void kaczmarz_colour_sweep<T>(const Mesh&, const Level&, int, const T*, const T*, const T*,  \
+                                         const T*, const T*, T*, const T*, const T*, int, double,      \
+                                         cudaStream_t);                                                \
+  template void row_norms<T>(const Mesh&, const T*, const T*, T*, T*, T*, cudaStream_t);
 
 BMG_OPS_INSTANTIATE(double)
 BMG_OPS_INSTANTIATE(float)

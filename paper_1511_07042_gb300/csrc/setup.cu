@@ -490,6 +490,33 @@ __global__ void jp_round_kernel(const int* row_ptr, const int* col, int n, int* 
   colour[v] = c;
 }
 
+// The same round on the distance-2 graph (vertices within two edges): rows of one
+// colour then share no column, as a Kaczmarz sweep needs.  Equal to sequential
+// greedy colouring of that graph in descending priority.
+__global__ void jp2_round_kernel(const int* row_ptr, const int* col, int n, int* colour, int* remaining) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n) return;
+  if (colour[v] >= 0) return;
+  const uint64_t hv = splitmix64((uint64_t)v);
+  uint64_t used = 0;
+  for (int p = row_ptr[v]; p < row_ptr[v + 1]; ++p) {
+    const int u = col[p];
+    for (int q = row_ptr[u]; q < row_ptr[u + 1]; ++q) {
+      const int x = col[q];
+      if (x == v) continue;
+      const int cx = ((volatile int*)colour)[x];
+      if (cx < 0) {
+        if (higher(splitmix64((uint64_t)x), x, hv, v)) { atomicAdd(remaining, 1); return; }
+      } else if (cx < 64) {
+        used |= (1ull << cx);
+      }
+    }
+  }
+  int c = 0;
+  while (c < 64 && (used >> c) & 1ull) ++c;
+  colour[v] = c;
+}
+
 __global__ void flag_colour_kernel(const int* colour, int n, int c, int* flag) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) flag[i] = (colour[i] == c) ? 1 : 0;
@@ -505,15 +532,34 @@ __global__ void max_kernel(const int* x, int n, int* out) {
 }
 }  // namespace
 
-void colour_level(const Mesh& m, Level& lv, cudaStream_t s) {
+void colour_level(const Mesh& m, Level& lv, cudaStream_t s) { colour_mesh(m, lv.col1, false, s); }
+void colour_level2(const Mesh& m, Level& lv, cudaStream_t s) {
+  if (lv.col2.n_colours) return;
+  colour_mesh(m, lv.col2, true, s);
+  // rows of each colour in the Morton order of the level's row order (rank of a row)
+  std::vector<int> order(m.n), rank(m.n), rows(m.n);
+  BMG_CUDA(cudaMemcpyAsync(order.data(), m.row_order.get(), sizeof(int) * m.n, cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaMemcpyAsync(rows.data(), lv.col2.rows.get(), sizeof(int) * m.n, cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < m.n; ++i) rank[order[i]] = i;
+  for (int c = 0; c < lv.col2.n_colours; ++c)
+    std::sort(rows.begin() + lv.col2.ptr_host[c], rows.begin() + lv.col2.ptr_host[c + 1],
+              [&](int a, int b) { return rank[a] < rank[b]; });
+  BMG_CUDA(cudaMemcpyAsync(lv.col2.rows.get(), rows.data(), sizeof(int) * m.n, cudaMemcpyHostToDevice, s));
+  BMG_CUDA(cudaStreamSynchronize(s));
+}
+
+void colour_mesh(const Mesh& m, Colouring& cl, bool distance2, cudaStream_t s) {
   const int n = m.n;
-  lv.colour.alloc(n);
-  BMG_CUDA(cudaMemsetAsync(lv.colour.get(), 0xff, sizeof(int) * n, s));
+  cl.colour.alloc(n);
+  BMG_CUDA(cudaMemsetAsync(cl.colour.get(), 0xff, sizeof(int) * n, s));
   DBuf<int> rem(1);
   for (int round = 0; round < 100000; ++round) {
     BMG_CUDA(cudaMemsetAsync(rem.get(), 0, sizeof(int), s));
-    jp_round_kernel<<<grid_for(n, 256), 256, 0, s>>>(m.row_ptr.get(), m.col.get(), n, lv.colour.get(),
-                                                     rem.get());
+    if (distance2)
+      jp2_round_kernel<<<grid_for(n, 256), 256, 0, s>>>(m.row_ptr.get(), m.col.get(), n, cl.colour.get(), rem.get());
+    else
+      jp_round_kernel<<<grid_for(n, 256), 256, 0, s>>>(m.row_ptr.get(), m.col.get(), n, cl.colour.get(), rem.get());
     check_launch("jp_round_kernel");
     int h = 0;
     BMG_CUDA(cudaMemcpyAsync(&h, rem.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -522,37 +568,37 @@ void colour_level(const Mesh& m, Level& lv, cudaStream_t s) {
   }
   DBuf<int> mx(1);
   BMG_CUDA(cudaMemsetAsync(mx.get(), 0, sizeof(int), s));
-  max_kernel<<<grid_for(n, 256), 256, 0, s>>>(lv.colour.get(), n, mx.get());
+  max_kernel<<<grid_for(n, 256), 256, 0, s>>>(cl.colour.get(), n, mx.get());
   int hmax = 0;
   BMG_CUDA(cudaMemcpyAsync(&hmax, mx.get(), sizeof(int), cudaMemcpyDeviceToHost, s));
   BMG_CUDA(cudaStreamSynchronize(s));
   if (hmax >= 63) fail(BMG_ERR_MESH, "colouring needs more than 63 colours");
-  lv.n_colours = hmax + 1;
-  lv.colour_rows.alloc(n);
-  lv.colour_ptr.alloc(lv.n_colours + 1);
-  lv.colour_ptr_host.assign(lv.n_colours + 1, 0);
+  cl.n_colours = hmax + 1;
+  cl.rows.alloc(n);
+  cl.ptr.alloc(cl.n_colours + 1);
+  cl.ptr_host.assign(cl.n_colours + 1, 0);
   DBuf<int> flag(n), pos(n + 1);
   int base = 0;
-  for (int c = 0; c < lv.n_colours; ++c) {
-    flag_colour_kernel<<<grid_for(n, 256), 256, 0, s>>>(lv.colour.get(), n, c, flag.get());
+  for (int c = 0; c < cl.n_colours; ++c) {
+    flag_colour_kernel<<<grid_for(n, 256), 256, 0, s>>>(cl.colour.get(), n, c, flag.get());
     int cntc = 0;
     exclusive_scan(flag.get(), pos.get(), n, &cntc, s);
-    scatter_colour_kernel<<<grid_for(n, 256), 256, 0, s>>>(lv.colour.get(), n, c, pos.get(), base,
-                                                           lv.colour_rows.get());
-    lv.colour_ptr_host[c] = base;
+    scatter_colour_kernel<<<grid_for(n, 256), 256, 0, s>>>(cl.colour.get(), n, c, pos.get(), base,
+                                                           cl.rows.get());
+    cl.ptr_host[c] = base;
     base += cntc;
   }
-  lv.colour_ptr_host[lv.n_colours] = base;
-  BMG_CUDA(cudaMemcpyAsync(lv.colour_ptr.get(), lv.colour_ptr_host.data(),
-                           sizeof(int) * (lv.n_colours + 1), cudaMemcpyHostToDevice, s));
+  cl.ptr_host[cl.n_colours] = base;
+  BMG_CUDA(cudaMemcpyAsync(cl.ptr.get(), cl.ptr_host.data(),
+                           sizeof(int) * (cl.n_colours + 1), cudaMemcpyHostToDevice, s));
   std::vector<int> hrp(n + 1), hrows(n);
   BMG_CUDA(cudaMemcpyAsync(hrp.data(), m.row_ptr.get(), sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s));
-  BMG_CUDA(cudaMemcpyAsync(hrows.data(), lv.colour_rows.get(), sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaMemcpyAsync(hrows.data(), cl.rows.get(), sizeof(int) * n, cudaMemcpyDeviceToHost, s));
   BMG_CUDA(cudaStreamSynchronize(s));
-  lv.colour_nnz_host.assign(lv.n_colours, 0);
-  for (int c = 0; c < lv.n_colours; ++c)
-    for (int q = lv.colour_ptr_host[c]; q < lv.colour_ptr_host[c + 1]; ++q)
-      lv.colour_nnz_host[c] += hrp[hrows[q] + 1] - hrp[hrows[q]];
+  cl.nnz_host.assign(cl.n_colours, 0);
+  for (int c = 0; c < cl.n_colours; ++c)
+    for (int q = cl.ptr_host[c]; q < cl.ptr_host[c + 1]; ++q)
+      cl.nnz_host[c] += hrp[hrows[q] + 1] - hrp[hrows[q]];
 }
 
 // Processing order of the rows of mesh m for the row kernels: vertices sorted by the
@@ -566,7 +612,7 @@ void locality_order(Mesh& m, Level& lv, cudaStream_t s) {
   std::vector<double> v(3 * (size_t)n);
   std::vector<int> rows(n);
   BMG_CUDA(cudaMemcpyAsync(v.data(), m.verts.get(), sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
-  BMG_CUDA(cudaMemcpyAsync(rows.data(), lv.colour_rows.get(), sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+  BMG_CUDA(cudaMemcpyAsync(rows.data(), lv.col1.rows.get(), sizeof(int) * n, cudaMemcpyDeviceToHost, s));
   BMG_CUDA(cudaStreamSynchronize(s));
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
   for (int i = 0; i < n; ++i)
@@ -595,11 +641,11 @@ void locality_order(Mesh& m, Level& lv, cudaStream_t s) {
   std::vector<int> order(n);
   for (int i = 0; i < n; ++i) order[i] = i;
   std::sort(order.begin(), order.end(), before);
-  for (int c = 0; c < lv.n_colours; ++c)
-    std::sort(rows.begin() + lv.colour_ptr_host[c], rows.begin() + lv.colour_ptr_host[c + 1], before);
+  for (int c = 0; c < lv.col1.n_colours; ++c)
+    std::sort(rows.begin() + lv.col1.ptr_host[c], rows.begin() + lv.col1.ptr_host[c + 1], before);
   m.row_order.alloc(n);
   BMG_CUDA(cudaMemcpyAsync(m.row_order.get(), order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
-  BMG_CUDA(cudaMemcpyAsync(lv.colour_rows.get(), rows.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
+  BMG_CUDA(cudaMemcpyAsync(lv.col1.rows.get(), rows.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s));
   BMG_CUDA(cudaStreamSynchronize(s));
 }
 

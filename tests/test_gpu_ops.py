@@ -18,7 +18,7 @@ def env(gpu_bmg):
     v, t = inputs.icosahedron()
     prob = gpu_bmg.Problem(v, t, R)
     prob.hierarchy(R)
-    H = obmg.build_hierarchy(v, t, R)
+    H = obmg.build_hierarchy(v, t, R, colour2=True)
     return gpu_bmg, prob, H
 
 
@@ -57,7 +57,8 @@ def test_spmm(env, k, f, l):
 
 
 @pytest.mark.parametrize("k", [3, 20, 64])
-@pytest.mark.parametrize("smoother,nu,omega", [("jacobi", 2, 2 / 3), ("mcgs", 1, 1.0), ("mcsgs", 2, 1.0)])
+@pytest.mark.parametrize("smoother,nu,omega", [("jacobi", 2, 2 / 3), ("mcgs", 1, 1.0), ("mcsgs", 2, 1.0),
+                                               ("kaczmarz", 2, 1.0), ("kaczmarz", 1, 0.8)])
 @pytest.mark.parametrize("f,l", [(4, 4), (4, 3)])
 @pytest.mark.parametrize("with_b", [True, False])
 def test_smoothers(env, k, smoother, nu, omega, f, l, with_b):
@@ -75,6 +76,8 @@ def test_smoothers(env, k, smoother, nu, omega, f, l, with_b):
     prob.smooth(f, l, Xd, Bd if with_b else None, sd, k, smoother, nu, omega, work)
     if smoother == "jacobi":
         ref = multilevel.jacobi(A, M, X, B, s, omega, nu)
+    elif smoother == "kaczmarz":
+        ref = multilevel.kaczmarz(A, M, X, B, s, H.colour2[l], nu, omega)
     else:
         ref = multilevel.mc_gauss_seidel(A, M, X, B, s, H.colour[l], nu, symmetric=(smoother == "mcsgs"))
     assert rel(host(Xd, k), ref) < 1e-12

@@ -25,7 +25,7 @@ def env(gpu_bmg):
     v, t = inputs.icosahedron()
     prob = gpu_bmg.Problem(v, t, R)
     prob.hierarchy(R)
-    H = obmg.build_hierarchy(v, t, R)
+    H = obmg.build_hierarchy(v, t, R, colour2=True)
     return gpu_bmg, prob, H
 
 
@@ -64,7 +64,7 @@ def test_spmm_f32(env, k, f, l):
 
 
 @pytest.mark.parametrize("k", [3, 20, 64])
-@pytest.mark.parametrize("smoother,nu,omega", [("jacobi", 2, 2 / 3), ("mcsgs", 1, 1.0)])
+@pytest.mark.parametrize("smoother,nu,omega", [("jacobi", 2, 2 / 3), ("mcsgs", 1, 1.0), ("kaczmarz", 2, 1.0)])
 @pytest.mark.parametrize("with_b", [True, False])
 def test_smoothers_f32(env, k, smoother, nu, omega, with_b):
     bmg, prob, H = env
@@ -81,6 +81,8 @@ def test_smoothers_f32(env, k, smoother, nu, omega, with_b):
     prob.smooth_f32(f, l, Xd, Bd if with_b else None, sd, k, smoother, nu, omega, work)
     if smoother == "jacobi":
         ref = multilevel.jacobi(A, M, X, B, s, omega, nu)
+    elif smoother == "kaczmarz":
+        ref = multilevel.kaczmarz(A, M, X, B, s, H.colour2[l], nu, omega)
     else:
         ref = multilevel.mc_gauss_seidel(A, M, X, B, s, H.colour[l], nu, symmetric=True)
     # a sweep is a contraction of float32-rounded updates: relative 1e-5 of the block

@@ -53,6 +53,17 @@ def test_colouring_bit_exact(pair):
         assert np.array_equal(c, H.colour[l]) and nc == H.colour[l].max() + 1
 
 
+def test_distance2_colouring_bit_exact(pair):
+    """The Kaczmarz smoother's colouring: sequential greedy on the distance-2 graph in
+    the same priority order, computed by the oracle from the square of the pattern."""
+    prob, H, meshes, R = pair
+    for l in range(1, R + 1):
+        A = H.A[l]
+        want = multilevel.greedy_colouring(*multilevel.distance2_pattern(A.indptr, A.indices))
+        c, nc = prob.colouring2(l)
+        assert np.array_equal(c, want) and nc == want.max() + 1, l
+
+
 def test_galerkin_operators(pair):
     prob, H, meshes, R = pair
     for f in range(2, R + 1):

@@ -25,7 +25,9 @@ def solve(bmg, R, k, nw, sigma, tol, amp=0.0, seed=None, x0seed=1001, colour=Fal
                                 dict(smoother="mcsgs", nu=1, omega=1.0),
                                 dict(smoother="mcgs", nu=2, omega=1.0, form="homogeneous"),
                                 dict(smoother="jacobi", nu=2, omega=2 / 3, tensor_cores=False),
-                                dict(smoother="mcsgs", nu=1, omega=1.0, tensor_cores=False)])
+                                dict(smoother="mcsgs", nu=1, omega=1.0, tensor_cores=False),
+                                dict(smoother="kaczmarz", nu=2, omega=1.0),
+                                dict(smoother="kaczmarz", nu=2, omega=1.0, precision="fp32")])
 def test_sphere642_k20_matches_dense(gpu_bmg, kw):
     ev, U, rs, info, H = solve(gpu_bmg, 3, 20, 16, 0.0, 1e-10, **kw)
     assert info.converged == 1
@@ -39,8 +41,9 @@ def test_sphere642_k20_matches_dense(gpu_bmg, kw):
     assert np.allclose(U.T @ (M @ U), np.eye(16), atol=1e-10)
 
 
-def test_bumpy_interior_cluster_matches_dense(gpu_bmg):
-    ev, U, rs, info, H = solve(gpu_bmg, 3, 24, 9, 20.0, 1e-10, amp=0.1, seed=1003, x0seed=1013)
+@pytest.mark.parametrize("kw", [dict(), dict(smoother="kaczmarz", nu=2, omega=1.0)])
+def test_bumpy_interior_cluster_matches_dense(gpu_bmg, kw):
+    ev, U, rs, info, H = solve(gpu_bmg, 3, 24, 9, 20.0, 1e-10, amp=0.1, seed=1003, x0seed=1013, **kw)
     assert info.converged == 1
     A, M = H.A[3], H.M[3]
     w, V = certify.dense_pencil_eigs(A, M)
@@ -79,9 +82,12 @@ def test_sphere40962_k64_full_size(gpu_bmg):
     X0 = inputs.gaussian_block(inputs.n_vertices(2), 64, 1001)
     ref = obmg.bfmg(H, X0, 64, 49, 0.0, 1e-10, obmg.Options(smoother="mcsgs", nu=1, omega=1.0))
     assert np.max(np.abs(lam - np.sort(ref.lam[:49])) / np.maximum(np.abs(lam), 1)) <= 1e-10
-    # and spans the same invariant subspaces: M-principal angles per cluster
+    # and spans the same invariant subspaces: M-principal angles per cluster.  The
+    # icosahedral symmetry splits l = 3 into sub-multiplets of 3 and 4 a relative 1e-5
+    # apart; each one's own subspace is fixed only to residual / gap (Davis-Kahan),
+    # so clusters are formed at a relative gap of 1e-4, which keeps them together.
     o = np.argsort(ref.lam[:49])
-    err, ang = certify.compare_to_reference(M, ev, U, ref.lam[:49][o], ref.U[:, :49][:, o])
+    err, ang = certify.compare_to_reference(M, ev, U, ref.lam[:49][o], ref.U[:, :49][:, o], rel_gap=1e-4)
     print("40962-vertex solve: max eigenvalue error %.2e, max cluster angle %.2e" % (err.max(), ang.max()))
     assert err.max() <= 1e-10 and ang.max() <= 1e-8
 
@@ -133,3 +139,21 @@ def test_single_vector(gpu_bmg, precision):
     assert np.max(np.abs(u - u.mean())) <= 1e-8 * np.max(np.abs(u))
     M = obmg.build_hierarchy(v, t, 3, colour=False).M[3]
     assert abs(u @ (M @ u) - 1.0) <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_adaptive_shift_matches_oracle(gpu_bmg, precision):
+    """The adaptive shift (Alg. 3 step 4): from sigma = 32 on the 642-vertex sphere the
+    GPU solve follows the oracle's shift to the same final value and returns the 9
+    eigenpairs nearest it (LAPACK)."""
+    ev, U, rs, info, H = solve(gpu_bmg, 3, 20, 9, 32.0, 1e-10, adaptive_shift=True, max_cycles=100,
+                               precision=precision)
+    assert info.converged == 1
+    X0 = inputs.gaussian_block(162, 20, 1001)
+    ref = obmg.bfmg(H, X0, 20, 9, 32.0, 1e-10, obmg.Options(adaptive_shift=True, max_cycles=100))
+    assert abs(info.final_shift - ref.shifts[-1]) <= 1e-4 * abs(ref.shifts[-1])
+    A, M = H.A[3], H.M[3]
+    w, V = certify.dense_pencil_eigs(A, M)
+    wr, Vr = certify.nearest(w, V, info.final_shift, 9)
+    err, ang = certify.compare_to_reference(M, ev, U, wr, Vr)
+    assert err.max() <= 1e-10 and ang.max() <= 1e-8

@@ -110,3 +110,39 @@ def test_bfmg_rate_of_convergence_table1_analogue():
             errs.append(np.mean(np.abs(lv - lam)))
         r = np.log(errs[0] / errs[-1]) / np.log(dof[-1] / dof[0])
         assert abs(r - 1.0) < 0.05 and abs(r - r_gs) < 0.1, (lam, r)
+
+
+def test_mean_rayleigh_quotient_of_eigenvectors_is_mean_eigenvalue():
+    """Closed form of the shift update: for exact eigenvectors the mean Rayleigh
+    quotient is the mean of their eigenvalues."""
+    v, t = inputs.icosahedron()
+    H = bmg.build_hierarchy(v, t, 2, colour=False)
+    A, M = H.A[2], H.M[2]
+    w, V = certify.dense_pencil_eigs(A, M)
+    X = V[:, 10:30] * np.linspace(0.5, 3.0, 20)[None, :]        # any column scaling
+    assert abs(bmg.mean_rayleigh_quotient(X, A @ X, M @ X) - w[10:30].mean()) <= 1e-12 * w[29]
+
+
+def test_adaptive_shift_sec53_analogue():
+    """Sec. 5.3: a coarse shift of 32, updated after each cycle from the Rayleigh
+    quotients of the source solutions, moves towards the cluster it approximates (the
+    paper: 32 -> 24.99 while approximating lambda = 20).  On the 642-vertex sphere
+    (k = 20, 9 wanted) the shift leaves 32, settles between the l = 4 (~20) and l = 5
+    (~30) multiplets, and the 9 pairs are the l = 4 multiplet: the 9 eigenvalues
+    nearest the final shift by LAPACK, with their eigenvectors."""
+    v, t = inputs.icosahedron()
+    H = bmg.build_hierarchy(v, t, 3)
+    X0 = inputs.gaussian_block(162, 20, 1001)
+    res = bmg.bfmg(H, X0, 20, 9, 32.0, 1e-10, bmg.Options(adaptive_shift=True, max_cycles=100))
+    assert res.converged and res.shifts[0] == 32.0
+    mu = res.shifts[-1]
+    assert 20.0 < mu < 30.0 and all(20.0 < s_ < 32.0 for s_ in res.shifts[1:])
+    A, M = H.A[3], H.M[3]
+    w, V = certify.dense_pencil_eigs(A, M)
+    wr, Vr = certify.nearest(w, V, mu, 9)
+    err, ang = certify.compare_to_reference(M, res.lam[:9], res.U[:, :9], wr, Vr)
+    assert err.max() <= 1e-10 and ang.max() <= 1e-8
+    assert np.all(np.abs(wr - 20.0) < 1.0)                        # the l = 4 multiplet
+    # with the shift held at 32 the same start settles on the l = 5 multiplet instead
+    fixed = bmg.bfmg(H, X0, 20, 9, 32.0, 1e-10, bmg.Options(max_cycles=100))
+    assert np.sum(np.abs(fixed.lam[:9] - 31.0) < 1.0) >= 8

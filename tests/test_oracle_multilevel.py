@@ -114,3 +114,67 @@ def test_jacobi_on_diagonal_system_is_exact_with_unit_damping():
     b = np.array([[1.0], [2.0], [3.0]])
     x = multilevel.jacobi(A, M, np.zeros((3, 1)), b, [1.0], 1.0, 1)
     assert np.allclose(x[:, 0], [1.0, 1.0, 0.75])
+
+
+# ---- Kaczmarz relaxation (Sec. 5.3, Table 2) ------------------------------------
+def _k_level(R=3):
+    from oracle import bmg as _b
+    from paper_1511_07042_gb300 import inputs as _in
+    v, t = _in.icosahedron()
+    H = _b.build_hierarchy(v, t, R, colour2=True)
+    return H.A[R].tocsr(), H.M[R].tocsr(), H.colour2[R]
+
+
+def test_distance2_colouring_is_proper():
+    A, M, c2 = _k_level(2)
+    G = (A != 0).astype(np.int64).toarray()
+    near = (G @ G) > 0                                 # within two edges, brute force
+    np.fill_diagonal(near, False)
+    i, j = np.nonzero(near)
+    assert np.all(c2[i] != c2[j])
+
+
+def test_kaczmarz_multicolour_equals_sequential():
+    A, M, c2 = _k_level(3)
+    rng = np.random.default_rng(21)
+    x0, b = rng.standard_normal(A.shape[0]), rng.standard_normal(A.shape[0])
+    s = 20.0                                           # indefinite: A - 20 M has negative eigenvalues
+    seq = multilevel.kaczmarz_sequential(A, M, x0, b, s, c2, omega=0.9)
+    par = multilevel.kaczmarz(A, M, x0[:, None], b[:, None], np.array([s]), c2, 1, 0.9)[:, 0]
+    assert np.max(np.abs(par - seq)) <= 1e-12 * np.max(np.abs(seq))
+
+
+def test_kaczmarz_is_sor_on_the_normal_equations():
+    """Textbook identity: a Kaczmarz sweep from x0 is x0 + K^T y, y one SOR sweep from 0
+    on (K K^T) y = b - K x0 in the same row order (dense, independent arithmetic)."""
+    A, M, c2 = _k_level(2)
+    s, omega = 7.5, 0.8
+    K = (A - s * M).toarray()
+    rng = np.random.default_rng(22)
+    x0, b = rng.standard_normal(A.shape[0]), rng.standard_normal(A.shape[0])
+    KK = K @ K.T
+    rhs = b - K @ x0
+    y = np.zeros_like(b)
+    for i in sorted(range(A.shape[0]), key=lambda v: (int(c2[v]), v)):
+        y[i] += omega * (rhs[i] - KK[i] @ y) / KK[i, i]
+    want = x0 + K.T @ y
+    got = multilevel.kaczmarz(A, M, x0[:, None], b[:, None], np.array([s]), c2, 1, omega)[:, 0]
+    assert np.max(np.abs(got - want)) <= 1e-11 * np.max(np.abs(want))
+
+
+def test_kaczmarz_error_never_grows_on_an_indefinite_system():
+    """Each row step is an orthogonal projection onto a hyperplane through the
+    solution, so the 2-norm of the error cannot grow (omega = 1), for any shift."""
+    A, M, c2 = _k_level(3)
+    s = 20.0
+    K = (A - s * M).toarray()
+    assert np.min(np.linalg.eigvalsh(0.5 * (K + K.T))) < 0
+    rng = np.random.default_rng(23)
+    b = rng.standard_normal(A.shape[0])
+    xs = np.linalg.solve(K, b)
+    x = np.zeros((A.shape[0], 1))
+    errs = [np.linalg.norm(x[:, 0] - xs)]
+    for _ in range(10):
+        x = multilevel.kaczmarz(A, M, x, b[:, None], np.array([s]), c2, 1, 1.0)
+        errs.append(np.linalg.norm(x[:, 0] - xs))
+    assert all(e1 <= e0 * (1 + 1e-12) for e0, e1 in zip(errs, errs[1:])) and errs[-1] < errs[0]
