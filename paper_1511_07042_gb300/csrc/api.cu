@@ -653,9 +653,10 @@ __global__ void shifts_kernel(const double* theta, int k, int ld, double sigma, 
 // nu sweeps of the configured smoother on level j (operators of finest level f),
 // from Xin into Xout (Xin may equal Xout).  Jacobi alternates between Xout and work
 // so that the last sweep lands in Xout; Gauss-Seidel runs in place on Xout.
+// zero_shift: every shift is zero (shifted form at sigma = 0), so M is not read.
 template <typename T>
 void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, const T* Xin, T* Xout,
-                  const T* B, const T* shift, int ld, T* work, cudaStream_t s) {
+                  const T* B, const T* shift, int ld, T* work, cudaStream_t s, bool zero_shift) {
   const Mesh& m = p->meshOf(j);
   const T *a = Ops<T>::A(p, f, j), *mm = Ops<T>::M(p, f, j), *da = Ops<T>::DA(p, f, j), *dm = Ops<T>::DM(p, f, j);
   const size_t bytes = sizeof(T) * (size_t)m.n * ld;
@@ -666,14 +667,14 @@ void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, cons
       src = work;
       for (int it = 0; it < o.nu; ++it) {
         T* dst = (it % 2 == 0) ? Xout : work;
-        jacobi_sweep<T>(m, a, mm, da, dm, src, dst, B, shift, ld, o.omega, s);
+        jacobi_sweep<T>(m, a, mm, da, dm, src, dst, B, shift, ld, o.omega, s, zero_shift);
         src = dst;
       }
       return;
     }
     for (int it = 0; it < o.nu; ++it) {
       T* dst = ((o.nu - 1 - it) % 2 == 0) ? Xout : work;
-      jacobi_sweep<T>(m, a, mm, da, dm, src, dst, B, shift, ld, o.omega, s);
+      jacobi_sweep<T>(m, a, mm, da, dm, src, dst, B, shift, ld, o.omega, s, zero_shift);
       src = dst;
     }
     return;
@@ -688,9 +689,11 @@ void smooth_level(const bmg_problem* p, int f, int j, const bmg_options& o, cons
     return;
   }
   for (int it = 0; it < o.nu; ++it) {
-    for (int c = 0; c < lv.col1.n_colours; ++c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s, work);
+    for (int c = 0; c < lv.col1.n_colours; ++c)
+      gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s, work, zero_shift);
     if (o.smoother == BMG_SMOOTH_MCSGS)
-      for (int c = lv.col1.n_colours - 1; c >= 0; --c) gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s, work);
+      for (int c = lv.col1.n_colours - 1; c >= 0; --c)
+        gs_colour_sweep<T>(m, lv, c, a, mm, da, dm, Xout, B, shift, ld, s, work, zero_shift);
   }
 }
 
@@ -963,6 +966,8 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
     if (!(smax * w.ratio[f][j] < 1.0 - 0.25)) break;
     legs.push_back(j);
   }
+  // the shifted form at sigma = 0 smooths A x_i = theta_i M u_i: M not needed
+  const bool zs = o.form == BMG_FORM_SHIFTED && sigma == 0.0;
   auto part_b = [&]() {
     // 5: smoothing of the source problems from U, then the down-leg
     const T* Bp = nullptr;
@@ -972,18 +977,18 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
       prof_end(KC_SMALL, s, 2.0 * sizeof(T) * nf * ld, 1.0 * nf * ld);
       Bp = b.B;
     }
-    smooth_level<T>(p, f, f, o, b.U, b.X, Bp, b.shift, ld, b.W, s);
+    smooth_level<T>(p, f, f, o, b.U, b.X, Bp, b.shift, ld, b.W, s, zs);
     if (!legs.empty()) {
-      residual<T>(mf, Af, Mf, b.X, Bp, b.shift, ld, b.W, s);
+      residual<T>(mf, Af, Mf, b.X, Bp, b.shift, ld, b.W, s, zs);
       const T* rprev = b.W;
       for (size_t t = 0; t < legs.size(); ++t) {
         const int j = legs[t];
         const Mesh& mj = p->meshOf(j);
         restrict_<T>(mj, rprev, b.cA[j], ld, s);
         BMG_CUDA(cudaMemsetAsync(b.cB[j], 0, sizeof(T) * (size_t)mj.n * ld, s));
-        smooth_level<T>(p, f, j, o, b.cB[j], b.cB[j], b.cA[j], b.shift, ld, b.cD[j], s);
+        smooth_level<T>(p, f, j, o, b.cB[j], b.cB[j], b.cA[j], b.shift, ld, b.cD[j], s, zs);
         if (t + 1 < legs.size()) {
-          residual<T>(mj, Ops<T>::A(p, f, j), Ops<T>::M(p, f, j), b.cB[j], b.cA[j], b.shift, ld, b.cC[j], s);
+          residual<T>(mj, Ops<T>::A(p, f, j), Ops<T>::M(p, f, j), b.cB[j], b.cA[j], b.shift, ld, b.cC[j], s, zs);
           rprev = b.cC[j];
         }
       }

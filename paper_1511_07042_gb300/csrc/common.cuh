@@ -241,15 +241,17 @@ void project_input(Mesh& m, double amplitude, const double* sh_consts_dev,
 // an FP32 block has ld % 4 == 0, an FP64 block ld % 2 == 0.
 template <typename T>
 void spmm_am(const Mesh& m, const T* a, const T* mm, const T* X, int ld, T* AX, T* MX, cudaStream_t s);
+// zero_shift: every shift of the block is zero (M and its diagonal are not read)
 template <typename T>
 void jacobi_sweep(const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const T* X,
-                  T* Xout, const T* B, const T* shift, int ld, double omega, cudaStream_t s);
+                  T* Xout, const T* B, const T* shift, int ld, double omega, cudaStream_t s,
+                  bool zero_shift = false);
 // scratch: a free [N][ld] block of the level, used to time shape candidates on the
 // colour's rows (the sweep itself runs in place), or nullptr
 template <typename T>
 void gs_colour_sweep(const Mesh& m, const Level& lv, int colour, const T* a, const T* mm,
                      const T* da, const T* dm, T* X, const T* B, const T* shift, int ld,
-                     cudaStream_t s, T* scratch = nullptr);
+                     cudaStream_t s, T* scratch = nullptr, bool zero_shift = false);
 // One multicolour Kaczmarz colour on (A - s_c M) x_c = b_c: each row r of colour c of
 // the distance-2 colouring projects x onto its equation, x += omega res / ||k_r||^2 k_r
 // with k_r = a_r - s m_r and ||k_r||^2 = na - 2 s nam + s^2 nm.  In place on X.
@@ -262,7 +264,7 @@ template <typename T>
 void row_norms(const Mesh& m, const T* a, const T* mm, T* na, T* nam, T* nm, cudaStream_t s);
 template <typename T>
 void residual(const Mesh& m, const T* a, const T* mm, const T* X, const T* B, const T* shift,
-              int ld, T* R, cudaStream_t s);
+              int ld, T* R, cudaStream_t s, bool zero_shift = false);
 template <typename T>
 void prolong(const Mesh& fine, const T* Xc, T* Y, int ld, bool add, cudaStream_t s);
 template <typename T>

@@ -79,18 +79,19 @@ struct GatherWidth {
   static constexpr int G0 = 32 / regs < 2 ? 2 : 32 / regs;
   static constexpr int G = G0 < LPR ? G0 : LPR;
 };
-template <typename T, int LPR, int CPL>
+template <typename T, int LPR, int CPL, bool WITH_M = true>
 __device__ __forceinline__ void gather_row(const int* __restrict__ col, const T* __restrict__ va,
                                            const T* __restrict__ vm, const T* __restrict__ X, int b, int len,
                                            int nch, int sl, T (&aa)[CPL][Chunk<T>::W],
                                            T (&mm)[CPL][Chunk<T>::W]) {
+  // WITH_M = false: only A x (mm untouched), for shifted problems with shift 0
   constexpr int W = Chunk<T>::W;
   if (sizeof(T) == 8) {
     // float64 blocks: the sweeps are bound by the FP64 pipe, not by memory latency,
     // so one nonzero at a time (no shuffles competing for issue slots)
     for (int p = b; p < b + len; ++p) {
       const int j = __ldcs(col + p);
-      const T a = __ldcs(va + p), m = __ldcs(vm + p);
+      const T a = __ldcs(va + p), m = WITH_M ? __ldcs(vm + p) : T(0);
 #pragma unroll
       for (int u = 0; u < CPL; ++u) {
         const int c = sl + LPR * u;
@@ -98,7 +99,10 @@ __device__ __forceinline__ void gather_row(const int* __restrict__ col, const T*
           T x[W];
           ldv_ro(X, (size_t)j * nch + c, x);
 #pragma unroll
-          for (int z = 0; z < W; ++z) { aa[u][z] = fma(a, x[z], aa[u][z]); mm[u][z] = fma(m, x[z], mm[u][z]); }
+          for (int z = 0; z < W; ++z) {
+            aa[u][z] = fma(a, x[z], aa[u][z]);
+            if (WITH_M) mm[u][z] = fma(m, x[z], mm[u][z]);
+          }
         }
       }
     }
@@ -113,7 +117,7 @@ __device__ __forceinline__ void gather_row(const int* __restrict__ col, const T*
     if (sl < G && sl < cnt) {
       jl = __ldcs(col + b + p0 + sl);
       al = __ldcs(va + b + p0 + sl);
-      ml = __ldcs(vm + b + p0 + sl);
+      if (WITH_M) ml = __ldcs(vm + b + p0 + sl);
     }
     T x[G][CPL][W];
 #pragma unroll
@@ -133,13 +137,16 @@ __device__ __forceinline__ void gather_row(const int* __restrict__ col, const T*
 #pragma unroll
     for (int q = 0; q < G; ++q) {
       const T a = __shfl_sync(0xffffffffu, al, q, LPR);
-      const T m = __shfl_sync(0xffffffffu, ml, q, LPR);
+      const T m = WITH_M ? __shfl_sync(0xffffffffu, ml, q, LPR) : T(0);
       if (q < cnt) {
 #pragma unroll
         for (int u = 0; u < CPL; ++u)
           if (sl + LPR * u < nch) {
 #pragma unroll
-            for (int z = 0; z < W; ++z) { aa[u][z] = fma(a, x[q][u][z], aa[u][z]); mm[u][z] = fma(m, x[q][u][z], mm[u][z]); }
+            for (int z = 0; z < W; ++z) {
+              aa[u][z] = fma(a, x[q][u][z], aa[u][z]);
+              if (WITH_M) mm[u][z] = fma(m, x[q][u][z], mm[u][z]);
+            }
           }
       }
     }
@@ -209,7 +216,9 @@ spmm_am_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
 //   MODE 0 (Jacobi):   xout = x + omega r / d
 //   MODE 1 (GS):       x    = x + r / d          (in place, rows of one colour)
 //   MODE 2 (residual): out  = r
-template <typename T, int LPR, int CPL, int MODE>
+// ZS: every shift is zero (the shifted problems of a solve at sigma = 0): r = b - A x
+// and d = dA_i, so M and its diagonal are not read and 1/d is formed once per row.
+template <typename T, int LPR, int CPL, int MODE, bool ZS>
 __global__ void __launch_bounds__(512)
 row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
                   const T* __restrict__ va, const T* __restrict__ vm,
@@ -234,17 +243,23 @@ row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
 #pragma unroll
       for (int q = 0; q < W; ++q) { aa[u][q] = T(0); mm[u][q] = T(0); }
     const int b = live ? row_ptr[row] : 0;
-    gather_row<T, LPR, CPL>(col, va, vm, X, b, live ? row_ptr[row + 1] - b : 0, nch, sl, aa, mm);
+    gather_row<T, LPR, CPL, !ZS>(col, va, vm, X, b, live ? row_ptr[row + 1] - b : 0, nch, sl, aa, mm);
     if (!live) continue;
-    const T dai = da[row], dmi = dm[row];
+    const T dai = da[row], dmi = ZS ? T(0) : dm[row];
+    const T rd0 = (ZS && MODE != 2) ? recip(dai) : T(0);
 #pragma unroll
     for (int u = 0; u < CPL; ++u) {
       const int c = sl + LPR * u;
       if (c >= nch) continue;
       T s[W], r[W];
-      ldv(shift, c, s);
+      if (ZS) {
 #pragma unroll
-      for (int q = 0; q < W; ++q) r[q] = -(aa[u][q] - s[q] * mm[u][q]);
+        for (int q = 0; q < W; ++q) s[q] = T(0);
+      } else {
+        ldv(shift, c, s);
+      }
+#pragma unroll
+      for (int q = 0; q < W; ++q) r[q] = ZS ? -aa[u][q] : -(aa[u][q] - s[q] * mm[u][q]);
       const size_t idx = (size_t)row * nch + c;
       if (B) {
         T bb[W];
@@ -259,8 +274,7 @@ row_update_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
         ldv_ro(X, idx, x);   // a row of the running colour is read only by its own lanes
 #pragma unroll
         for (int q = 0; q < W; ++q) {
-          const T d = dai - s[q] * dmi;
-          const T rd = recip(d);
+          const T rd = ZS ? rd0 : recip(dai - s[q] * dmi);
           o[q] = (MODE == 0) ? x[q] + omega * (r[q] * rd) : x[q] + r[q] * rd;
         }
         // padding columns carry zero shift, zero data and stay zero
@@ -717,10 +731,12 @@ int resident_blocks(const void* kernel, int threads) {
   return v;
 }
 // Grid of a row kernel over `items` row groups of `rows_per_group` rows: at most one
-// wave of resident CTAs, dealt chunks of about `chunk` consecutive rows.
+// wave of resident CTAs, dealt chunks of about `chunk` consecutive rows; shorter chunks
+// when there would be fewer chunks than resident CTAs (small launches, such as the
+// rows of one colour, keep every SM busy).
 void row_grid(const void* kernel, int threads, int items, int rows_per_group, int chunk, int& grid, int& groups) {
   const int wave = resident_blocks(kernel, threads);
-  groups = std::max(1, chunk / rows_per_group);
+  groups = std::max(1, std::min(chunk / rows_per_group, items / wave));
   const int chunks = (items + groups - 1) / groups;
   grid = std::max(1, std::min(chunks, wave));
 }
@@ -751,29 +767,29 @@ void spmm_launch(RowCfg c, const Mesh& m, const T* a, const T* mm, const T* X, i
   }
 }
 
-template <typename T, int LPR, int CPL, int MODE>
+template <typename T, int LPR, int CPL, int MODE, bool ZS>
 void row_shape(int wpb, int chunk, const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const int* rows,
                int nrows, const T* X, T* Out, const T* B, const T* shift, int nch, double omega, cudaStream_t s) {
   const int per_block = wpb * (32 / LPR);
   int grid, groups;
-  row_grid((const void*)row_update_kernel<T, LPR, CPL, MODE>, wpb * 32, blocks_for(nrows, per_block), per_block,
+  row_grid((const void*)row_update_kernel<T, LPR, CPL, MODE, ZS>, wpb * 32, blocks_for(nrows, per_block), per_block,
            chunk, grid, groups);
-  row_update_kernel<T, LPR, CPL, MODE><<<grid, wpb * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, da, dm, rows,
+  row_update_kernel<T, LPR, CPL, MODE, ZS><<<grid, wpb * 32, 0, s>>>(m.row_ptr.get(), m.col.get(), a, mm, da, dm, rows,
                                                                  nrows, X, Out, B, shift, nch, (T)omega, groups);
   check_launch("row_update_kernel");
 }
-template <typename T, int MODE>
+template <typename T, int MODE, bool ZS>
 void row_launch(RowCfg c, const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const int* rows,
                 int nrows, const T* X, T* Out, const T* B, const T* shift, int nch, double omega, cudaStream_t s) {
   switch (c.shape) {
-    case 0: row_shape<T, 32, 1, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 1: row_shape<T, 32, 2, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 2: row_shape<T, 32, 4, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 3: row_shape<T, 16, 1, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 4: row_shape<T, 16, 2, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 5: row_shape<T, 8, 1, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    case 6: row_shape<T, 8, 2, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
-    default: row_shape<T, 4, 1, MODE>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 0: row_shape<T, 32, 1, MODE, ZS>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 1: row_shape<T, 32, 2, MODE, ZS>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 2: row_shape<T, 32, 4, MODE, ZS>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 3: row_shape<T, 16, 1, MODE, ZS>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 4: row_shape<T, 16, 2, MODE, ZS>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 5: row_shape<T, 8, 1, MODE, ZS>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    case 6: row_shape<T, 8, 2, MODE, ZS>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
+    default: row_shape<T, 4, 1, MODE, ZS>(c.wpb, c.chunk, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s); break;
   }
 }
 
@@ -862,9 +878,20 @@ template <typename T, int MODE>
 static void row_update(const Mesh& m, const T* a, const T* mm, const T* da, const T* dm,
                        const int* rows, int nrows, long long nnz_rows, const T* X, T* Out,
                        const T* B, const T* shift, int ld, double omega, cudaStream_t s,
-                       T* scratch = nullptr) {
+                       T* scratch = nullptr, bool zero_shift = false) {
   const int nch = ld / Chunk<T>::W;
   if (nrows == 0) return;
+  auto launch = [&](RowCfg q, int mode_override, T* out) {
+    // mode_override: the residual form of a Gauss-Seidel colour, timed on a scratch block
+    if (mode_override == 2) {
+      if (zero_shift) row_launch<T, 2, true>(q, m, a, mm, da, dm, rows, nrows, X, out, B, shift, nch, omega, s);
+      else row_launch<T, 2, false>(q, m, a, mm, da, dm, rows, nrows, X, out, B, shift, nch, omega, s);
+    } else if (zero_shift) {
+      row_launch<T, MODE, true>(q, m, a, mm, da, dm, rows, nrows, X, out, B, shift, nch, omega, s);
+    } else {
+      row_launch<T, MODE, false>(q, m, a, mm, da, dm, rows, nrows, X, out, B, shift, nch, omega, s);
+    }
+  };
   // Gauss-Seidel sweeps run in place and are not re-run for timing: with a scratch
   // block they take the shape tuned for the residual kernel on the same rows (same
   // gathers, written to the scratch block), else the one of the level's residual or
@@ -872,9 +899,7 @@ static void row_update(const Mesh& m, const T* a, const T* mm, const T* da, cons
   const int kind = (MODE == 2) ? 2 : 1;
   RowCfg c = default_cfg(nch);
   if (MODE == 1 && scratch) {
-    c = tune_rows(3, (int)sizeof(T), nch, nrows, s, [&](RowCfg q) {
-      row_launch<T, 2>(q, m, a, mm, da, dm, rows, nrows, X, scratch, B, shift, nch, omega, s);
-    });
+    c = tune_rows(3, (int)sizeof(T), nch, nrows, s, [&](RowCfg q) { launch(q, 2, scratch); });
   } else if (MODE == 1 && autotune_enabled()) {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     for (int kd : {2, 1}) {
@@ -882,31 +907,33 @@ static void row_update(const Mesh& m, const T* a, const T* mm, const T* da, cons
       if (it != g_tuned.end()) { c = it->second; break; }
     }
   } else {
-    c = tune_rows(kind, (int)sizeof(T), nch, nrows, s, [&](RowCfg q) {
-      row_launch<T, MODE>(q, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s);
-    });
+    c = tune_rows(kind, (int)sizeof(T), nch, nrows, s, [&](RowCfg q) { launch(q, MODE, Out); });
   }
   const int cls = (MODE == 2) ? KC_RESID : KC_SMOOTH;
   prof_begin(cls, s);
-  row_launch<T, MODE>(c, m, a, mm, da, dm, rows, nrows, X, Out, B, shift, nch, omega, s);
+  launch(c, MODE, Out);
   // matrix rows, diagonals, own-row read + write, one share of the gathered block, B
-  const double bytes = (4.0 + 2.0 * tb<T>()) * nnz_rows + 2.0 * tb<T>() * nrows +
+  // (without M and its diagonal when every shift is zero)
+  const double vals = zero_shift ? 1.0 : 2.0;
+  const double bytes = (4.0 + vals * tb<T>()) * nnz_rows + vals * tb<T>() * nrows +
                        tb<T>() * nrows * ld * (B ? 4.0 : 3.0);
-  prof_end(cls, s, bytes, 4.0 * nnz_rows * ld + 6.0 * nrows * ld);
+  prof_end(cls, s, bytes, (zero_shift ? 2.0 : 4.0) * nnz_rows * ld + 6.0 * nrows * ld);
 }
 
 template <typename T>
 void jacobi_sweep(const Mesh& m, const T* a, const T* mm, const T* da, const T* dm, const T* X,
-                  T* Xout, const T* B, const T* shift, int ld, double omega, cudaStream_t s) {
-  row_update<T, 0>(m, a, mm, da, dm, m.row_order.get(), m.n, m.nnz, X, Xout, B, shift, ld, omega, s);
+                  T* Xout, const T* B, const T* shift, int ld, double omega, cudaStream_t s, bool zero_shift) {
+  row_update<T, 0>(m, a, mm, da, dm, m.row_order.get(), m.n, m.nnz, X, Xout, B, shift, ld, omega, s, nullptr,
+                   zero_shift);
 }
 
 template <typename T>
 void gs_colour_sweep(const Mesh& m, const Level& lv, int c, const T* a, const T* mm, const T* da,
-                     const T* dm, T* X, const T* B, const T* shift, int ld, cudaStream_t s, T* scratch) {
+                     const T* dm, T* X, const T* B, const T* shift, int ld, cudaStream_t s, T* scratch,
+                     bool zero_shift) {
   const int b = lv.col1.ptr_host[c], e = lv.col1.ptr_host[c + 1];
   row_update<T, 1>(m, a, mm, da, dm, lv.col1.rows.get() + b, e - b, lv.col1.nnz_host[c], X, X, B,
-                   shift, ld, 1.0, s, scratch);
+                   shift, ld, 1.0, s, scratch, zero_shift);
 }
 
 template <typename T>
@@ -945,9 +972,10 @@ void row_norms(const Mesh& m, const T* a, const T* mm, T* na, T* nam, T* nm, cud
 
 template <typename T>
 void residual(const Mesh& m, const T* a, const T* mm, const T* X, const T* B, const T* shift, int ld,
-              T* R, cudaStream_t s) {
+              T* R, cudaStream_t s, bool zero_shift) {
   // the diagonal is not used in residual mode; pass the matrix values as placeholders
-  row_update<T, 2>(m, a, mm, a, mm, m.row_order.get(), m.n, m.nnz, X, R, B, shift, ld, 0.0, s);
+  row_update<T, 2>(m, a, mm, a, mm, m.row_order.get(), m.n, m.nnz, X, R, B, shift, ld, 0.0, s, nullptr,
+                   zero_shift);
 }
 
 template <typename T>
@@ -1089,11 +1117,11 @@ std::string tuned_report() {
 #define BMG_OPS_INSTANTIATE(T)                                                                          \
   template void spmm_am<T>(const Mesh&, const T*, const T*, const T*, int, T*, T*, cudaStream_t);      \
   template void jacobi_sweep<T>(const Mesh&, const T*, const T*, const T*, const T*, const T*, T*,     \
-                                const T*, const T*, int, double, cudaStream_t);                        \
+                                const T*, const T*, int, double, cudaStream_t, bool);                  \
   template void gs_colour_sweep<T>(const Mesh&, const Level&, int, const T*, const T*, const T*,       \
-                                   const T*, T*, const T*, const T*, int, cudaStream_t, T*);           \
+                                   const T*, T*, const T*, const T*, int, cudaStream_t, T*, bool);     \
   template void residual<T>(const Mesh&, const T*, const T*, const T*, const T*, const T*, int, T*,    \
-                            cudaStream_t);                                                             \
+                            cudaStream_t, bool);                                                       \
   template void prolong<T>(const Mesh&, const T*, T*, int, bool, cudaStream_t);                        \
   template void restrict_<T>(const Mesh&, const T*, T*, int, cudaStream_t);                            \
   template void eig_residuals<T>(const T*, const T*, const T*, const double*, int, int, int, double*,  \
