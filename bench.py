@@ -381,25 +381,30 @@ def batched_form_extra(bmg, inputs, np, torch):
 
 def interior_extra(bmg, inputs, np):
     """The interior workload: perturbed sphere r = 1 + 0.1 sum c_lm Y_lm (seed 1003),
-    163842 vertices, 7 levels, k = 48, 21 pairs nearest sigma = 110, Jacobi, 40-cycle cap."""
+    163842 vertices, 7 levels, k = 48, 21 pairs nearest sigma = 110, 40-cycle cap:
+    damped Jacobi (the workload's smoother) and five multicolour Kaczmarz sweeps (the
+    paper's smoother for interior problems, Sec. 5.3)."""
     wl = inputs.WORKLOADS["bumpy163842_k48_s110"]
     v, t = inputs.icosahedron()
     prob = bmg.Problem(v, t, wl["refinements"], wl["amplitude"], inputs.sh_coefficients(wl["coef_seed"]))
     prob.hierarchy(wl["refinements"])
     X0 = inputs.gaussian_block(inputs.n_vertices(2), wl["k"], wl["seed"])
-    ta = time.perf_counter()
-    ev, _, rs, info = prob.solve(X0, wl["k"], wl["n_wanted"], wl["sigma"], wl["tol"],
-                                 bmg.options(smoother=wl["smoother"], nu=wl["nu"], omega=wl["omega"],
-                                             max_cycles=40), evecs=False)
-    dt = time.perf_counter() - ta
+    out = {"workload": "bumpy163842_k48_s110"}
+    for name, kw in (("jacobi", dict(smoother=wl["smoother"], nu=wl["nu"], omega=wl["omega"])),
+                     ("kaczmarz5", dict(smoother="kaczmarz", nu=5, omega=1.0))):
+        ta = time.perf_counter()
+        ev, _, rs, info = prob.solve(X0, wl["k"], wl["n_wanted"], wl["sigma"], wl["tol"],
+                                     bmg.options(max_cycles=40, **kw), evecs=False)
+        dt = time.perf_counter() - ta
+        out[name] = {"converged": bool(info.converged), "cycles": info.total_cycles, "max_resid": float(rs.max()),
+                     "ritz_min": float(np.min(ev)), "ritz_max": float(np.max(ev)), "ms": dt * 1e3}
     prob.close()
-    return {"workload": "bumpy163842_k48_s110", "converged": bool(info.converged), "cycles": info.total_cycles,
-            "max_resid": float(rs.max()), "ritz_min": float(np.min(ev)), "ritz_max": float(np.max(ev)),
-            "ms": dt * 1e3,
-            "oracle_verdict": "the FP64 oracle does not reach the cluster either: on the same surface at "
-                              "refinement 4 its Ritz values settle far below the 21 eigenvalues nearest 110 "
-                              "(LAPACK and Sylvester inertia: [99.6, 119.5]) with Jacobi and MC-SGS "
-                              "(tests/test_oracle_interior.py)"}
+    out["oracle_verdict"] = ("the FP64 oracle does not reach the cluster either: on the same surface at refinement 4 "
+                             "(LAPACK and Sylvester inertia put the 21 eigenvalues nearest 110 in [99.6, 119.5]) its "
+                             "Ritz values settle far below it with Jacobi and MC-SGS, and five Kaczmarz sweeps crawl "
+                             "(residual 3e-4 after 200 cycles) with pairs outside the cluster "
+                             "(tests/test_oracle_interior.py)")
+    return out
 
 
 def run_ours(args):
