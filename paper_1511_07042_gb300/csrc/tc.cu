@@ -162,33 +162,51 @@ template <> struct Fmt<float> {
   }
 };
 
-// BF16 bits of a small integer (|d| <= 64): float32 by the 1.5 2^23 trick, top half.
-__device__ __forceinline__ uint32_t bf16_of_int(int d) {
-  const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
-  return __float_as_uint(f) >> 16;
+// 64 sum_{s < S-1} 2^(7 s): the bias 64 in each of the S - 1 lower digits
+__host__ __device__ constexpr long long digit_bias(int S) {
+  long long b = 0;
+  for (int s = 0; s + 1 < S; ++s) b = b * 128 + 64;
+  return b;
 }
 
-// Balanced base-2^7 digits of the 8 integers v[0..7]: writes S planes of 16 bytes
-// (8 BF16 values each) at dst + s * plane_stride, s = 0 the most significant digit.
+// float32 value u - 64 of a 7-bit field u = (x >> sh) & 127 (exact): the field is put
+// into the low mantissa bits of 1.5 2^23 (one LOP3) and 1.5 2^23 + 64 subtracted.
+__device__ __forceinline__ float biased_digit(uint32_t x_shifted) {
+  return __uint_as_float((x_shifted & 127u) | 0x4B400000u) - 12582976.0f;
+}
+// two float32 integers of at most 8 significant bits as one BF16 pair (exact): the
+// top halves of their bit patterns, the first in the low half
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  return __byte_perm(__float_as_uint(lo), __float_as_uint(hi), 0x7632);
+}
+
+// Balanced base-2^7 digits of the 8 integers v[0..7] (|v| <= 2^(7 S - 1)): writes S
+// planes of 16 bytes (8 BF16 values each) at dst + s * plane_stride, s = 0 the most
+// significant digit.  With the bias B = 64 sum_{s < S-1} 2^(7 s), w = v + B holds
+// the digits d_s + 64 in [0, 127] as its ordinary base-2^7 digits below the top one,
+// and the top digit d_{S-1} = w >> 7 (S - 1) (arithmetic): the digits of the
+// division-by-2^7 recursion d = ((v + 64) mod 2^7) - 64, v <- (v - d) / 2^7, each
+// read by one shift of w.
 template <int S>
-__device__ __forceinline__ void store_digits(long long (&v)[8], unsigned char* dst, int plane_stride) {
+__device__ __forceinline__ void store_digits(const long long (&v)[8], unsigned char* dst, int plane_stride) {
+  constexpr long long B = digit_bias(S);
   uint32_t packed[S][4];
 #pragma unroll
-  for (int s = S - 1; s >= 0; --s) {
+  for (int q = 0; q < 8; q += 2) {
+    const long long w0 = v[q] + B, w1 = v[q + 1] + B;
+    const uint32_t l0 = (uint32_t)w0, h0 = (uint32_t)((unsigned long long)w0 >> 32);
+    const uint32_t l1 = (uint32_t)w1, h1 = (uint32_t)((unsigned long long)w1 >> 32);
 #pragma unroll
-    for (int q = 0; q < 8; q += 2) {
-      int d0, d1;
-      if (s > 0) {
-        d0 = (((int)v[q] + 64) & 127) - 64;
-        d1 = (((int)v[q + 1] + 64) & 127) - 64;
-        v[q] = (v[q] - d0) >> kBeta;
-        v[q + 1] = (v[q + 1] - d1) >> kBeta;
-      } else {
-        d0 = (int)v[q];
-        d1 = (int)v[q + 1];
-      }
-      packed[s][q >> 1] = bf16_of_int(d0) | (bf16_of_int(d1) << 16);
+    for (int s = 0; s < S - 1; ++s) {   // s-th least significant digit -> plane S - 1 - s
+      const int sh = kBeta * s;
+      const uint32_t x0 = sh < 32 ? __funnelshift_r(l0, h0, sh) : (h0 >> (sh - 32));
+      const uint32_t x1 = sh < 32 ? __funnelshift_r(l1, h1, sh) : (h1 >> (sh - 32));
+      packed[S - 1 - s][q >> 1] = pack_bf16(biased_digit(x0), biased_digit(x1));
     }
+    constexpr int top = kBeta * (S - 1);
+    const int t0 = (int)(w0 >> top), t1 = (int)(w1 >> top);
+    packed[0][q >> 1] = pack_bf16(__int_as_float(0x4B400000 + t0) - 12582912.0f,
+                                  __int_as_float(0x4B400000 + t1) - 12582912.0f);
   }
 #pragma unroll
   for (int s = 0; s < S; ++s)
