@@ -50,7 +50,10 @@
 namespace bmg {
 namespace {
 
-constexpr int kTcThreads = 512;          // 16 warps; warps w, w+4, w+8, w+12 share TMEM lanes
+constexpr int kWorkers = 512;             // 16 warps forming digits and reading TMEM back; warps w,
+                                         // w+4, w+8, w+12 share TMEM lanes
+constexpr int kTcThreads = kWorkers + 32; // and one warp that issues the MMAs
+constexpr int kMmaWarp = kWorkers / 32;
 constexpr int kKsub = 32;                // K rows per sub-chunk (two MMA K-steps of 16)
 constexpr int kWindow = 128;             // K rows per exact accumulation window (Gram)
 constexpr int kNB = 64;                  // output columns per CTA (N of the MMA)
@@ -187,12 +190,13 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
 // and the top digit d_{S-1} = w >> 7 (S - 1) (arithmetic): the digits of the
 // division-by-2^7 recursion d = ((v + 64) mod 2^7) - 64, v <- (v - d) / 2^7, each
 // read by one shift of w.
-template <int S>
-__device__ __forceinline__ void store_digits(const long long (&v)[8], unsigned char* dst, int plane_stride) {
+template <int S, int NV>
+__device__ __forceinline__ void store_digits(const long long (&v)[NV], unsigned char* dst, int plane_stride) {
+  static_assert(NV == 4 || NV == 8, "4 or 8 values (8 or 16 bytes per plane)");
   constexpr long long B = digit_bias(S);
-  uint32_t packed[S][4];
+  uint32_t packed[S][NV / 2];
 #pragma unroll
-  for (int q = 0; q < 8; q += 2) {
+  for (int q = 0; q < NV; q += 2) {
     const long long w0 = v[q] + B, w1 = v[q + 1] + B;
     const uint32_t l0 = (uint32_t)w0, h0 = (uint32_t)((unsigned long long)w0 >> 32);
     const uint32_t l1 = (uint32_t)w1, h1 = (uint32_t)((unsigned long long)w1 >> 32);
@@ -209,9 +213,17 @@ __device__ __forceinline__ void store_digits(const long long (&v)[8], unsigned c
                                   __int_as_float(0x4B400000 + t1) - 12582912.0f);
   }
 #pragma unroll
-  for (int s = 0; s < S; ++s)
-    *reinterpret_cast<uint4*>(dst + s * plane_stride) = make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
+  for (int s = 0; s < S; ++s) {
+    if constexpr (NV == 8)
+      *reinterpret_cast<uint4*>(dst + s * plane_stride) = make_uint4(packed[s][0], packed[s][1], packed[s][2], packed[s][3]);
+    else
+      *reinterpret_cast<uint2*>(dst + s * plane_stride) = make_uint2(packed[s][0], packed[s][1]);
+  }
 }
+
+// byte offset of the 4 K-elements starting at (row, k4) (k4 % 4 == 0): the low or
+// high half of a core-matrix row
+__device__ __forceinline__ int quad_off(int row, int k4) { return cm_off(row, k4 & ~7) + (k4 & 4) * 2; }
 
 // Issues the MMAs of one sub-chunk: every digit pair (s, t) with s + t <= T into the
 // accumulator of its diagonal (columns (s + t - 2) * kNB of the allocation).
@@ -324,7 +336,8 @@ template <> struct Epi<float> {
 };
 
 struct TcShared {
-  uint64_t bar[2];
+  uint64_t bar[2];    // stage b free again: the commit of its MMAs (one arrival)
+  uint64_t full[2];   // stage b holds digits: one arrival per worker warp
   uint32_t tmem_slot;
   int abort_flag;
   int exA[128];     // exponents of the 128 A rows (Gram: columns of X; expand: rows of X)
@@ -343,6 +356,13 @@ __host__ __device__ constexpr uint32_t tmem_cols() {
   return (T - 1) * kNB <= 32 ? 32 : (T - 1) * kNB <= 64 ? 64 : (T - 1) * kNB <= 128 ? 128 : (T - 1) * kNB <= 256 ? 256 : 512;
 }
 
+// barrier of the worker warps only (the MMA warp does not take part)
+__device__ __forceinline__ void workers_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kWorkers) : "memory"); }
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(su32(bar)) : "memory");
+}
+
 template <int T>
 __device__ __forceinline__ void tc_setup(TcShared& sh, unsigned char* smem, int bytes) {
   const int tid = threadIdx.x;
@@ -350,6 +370,8 @@ __device__ __forceinline__ void tc_setup(TcShared& sh, unsigned char* smem, int 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sh.bar[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sh.bar[1])));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.full[0])), "n"(kWorkers / 32));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.full[1])), "n"(kWorkers / 32));
     sh.abort_flag = 0;
   }
   if ((tid >> 5) == 0) {
@@ -363,13 +385,15 @@ __device__ __forceinline__ void tc_setup(TcShared& sh, unsigned char* smem, int 
   fence_after();
 }
 
+// End of a tensor-core kernel, reached by every thread.  The issuing thread first
+// waits (bounded) for the last commit of each stage, so that no MMA is in flight when
+// the tensor memory is freed (after a timed-out wait the MMAs may still run).
 template <int T>
-__device__ __forceinline__ void tc_teardown(TcShared& sh, int g, int* err) {
-  // outstanding MMAs (a timed-out wait): bounded wait for the last commit of each stage
-  if (sh.abort_flag && threadIdx.x == 0) {
+__device__ __forceinline__ void tc_teardown(TcShared& sh, int issued, int* err) {
+  if (threadIdx.x == kWorkers) {
     for (int b = 0; b < 2; ++b) {
-      const int uses = (g - b + 1) / 2;   // commits made on stage b
-      if (uses > 0) mbar_wait(&sh.bar[b], (uint32_t)((uses - 1) & 1));
+      const int uses = (issued - b + 1) / 2;   // commits made on stage b
+      if (uses > 0 && !mbar_wait(&sh.bar[b], (uint32_t)((uses - 1) & 1))) atomicExch(&sh.abort_flag, 1);
     }
   }
   fence_before();
@@ -381,16 +405,50 @@ __device__ __forceinline__ void tc_teardown(TcShared& sh, int g, int* err) {
   if (sh.abort_flag && threadIdx.x == 0) atomicExch(err, 1);
 }
 
-// Waits (every thread) for the commit of sub-chunk gi; raises the shared abort flag
-// on expiry.  The flag is read only after the next barrier, so that all threads
+// Waits (every worker) for the commit of sub-chunk gi; raises the shared abort flag
+// on expiry.  Workers read the flag only right after a worker barrier, so that they
 // leave their loops together.
 __device__ __forceinline__ void wait_sub(TcShared& sh, int gi) {
   if (!mbar_wait(&sh.bar[gi & 1], (uint32_t)((gi >> 1) & 1))) atomicExch(&sh.abort_flag, 1);
 }
 
+// The MMA warp's part for sub-chunk g (sc: its index in the accumulation window):
+// lane 0 waits for the workers' digits of stage g & 1, issues the MMAs and commits
+// them to the stage's free barrier.  Returns false (warp-uniform) when the wait expired.
+template <int S, int T>
+__device__ __forceinline__ bool mma_step(TcShared& sh, unsigned char* smem, uint32_t tmem, int g, int sc) {
+  const int lane = threadIdx.x & 31;
+  const int b = g & 1;
+  int ok = 1;
+  if (lane == 0) ok = mbar_wait(&sh.full[b], (uint32_t)((g >> 1) & 1)) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) {
+    if (lane == 0) atomicExch(&sh.abort_flag, 1);
+    return false;
+  }
+  if (lane == 0) {
+    fence_after();
+    const uint32_t sA = su32(stage_ptr<S>(smem, b));
+    issue_mmas<S, T>(tmem, sA, sA + S * kAPlane, sc == 0);
+    mma_commit(&sh.bar[b]);
+  }
+  __syncwarp();
+  return true;
+}
+
+// A worker warp hands stage b to the MMA warp: every lane's digit stores made visible
+// to the tensor cores' (async) proxy, then one arrival for the warp.
+__device__ __forceinline__ void hand_over(TcShared& sh, int b) {
+  fence_async_smem();
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(&sh.full[b]);
+}
+
 // ------------------------------------------------------------ Gram kernel -----
 // blockIdx.x: row part [r0, r1); blockIdx.y: block of kNB columns of Y.
 // partial[part][i * k + j] = (X[r0:r1, i])^T Y[r0:r1, j] for i < k and j in the block.
+// Warps 0-15 form the digits of each 32-row sub-chunk (three 4-value quads per thread:
+// two of X, one of Y) and read the window sums back; warp 16 issues the MMAs.
 template <typename TI, int S, int T>
 __global__ void __launch_bounds__(kTcThreads, 1)
 gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k, int ld, int rows_per_part,
@@ -404,6 +462,19 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
   constexpr int F = kBeta * S - 1;
   tc_setup<T>(sh, smem, 2 * stage_bytes(S));
   const uint32_t tmem = sh.tmem_slot;
+  if (warp == kMmaWarp) {
+    int g = 0;
+    bool ok = true;
+    for (int w0 = r0; w0 < r1 && ok; w0 += kWindow) {
+      const int nsub = (min(r1, w0 + kWindow) - w0 + kKsub - 1) / kKsub;
+      for (int sc = 0; sc < nsub && ok; ++sc) {
+        ok = mma_step<S, T>(sh, smem, tmem, g, sc);
+        if (ok) ++g;
+      }
+    }
+    tc_teardown<T>(sh, g, err);
+    return;
+  }
   if (tid < kNB) sh.gRun[tid] = 0;
   // readback ownership: TMEM lane i = row of the output block, 16 columns
   const int i_out = (warp & 3) * 32 + lane;
@@ -414,70 +485,64 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
   for (int q = 0; q < 16; ++q) { Rh[q] = 0; Rl[q] = 0; }
   int e_run = 0;
   int g = 0;
-  for (int w0 = r0; w0 < r1 && !sh.abort_flag; w0 += kWindow) {
+  for (int w0 = r0; w0 < r1; w0 += kWindow) {
     const int w1 = min(r1, w0 + kWindow);
     // group exponents of the window: columns of X (A rows) and of the Y block (B rows)
-    __syncthreads();
+    workers_sync();
+    if (sh.abort_flag) break;
     if (tid < 128) sh.exA[tid] = 0;
     if (tid < kNB) sh.exB[tid] = 0;
-    __syncthreads();
+    workers_sync();
     {
       const int c = tid & 127;
       int m = 0;
       if (c < k)
-        for (int r = w0 + (tid >> 7); r < w1; r += kTcThreads / 128) m = max(m, Fmt<TI>::expo(X[(size_t)r * ld + c]));
+        for (int r = w0 + (tid >> 7); r < w1; r += kWorkers / 128) m = max(m, Fmt<TI>::expo(X[(size_t)r * ld + c]));
       if (m) atomicMax(&sh.exA[c], m);
       const int j = tid & (kNB - 1);
       int mb = 0;
       if (jb + j < k)
-        for (int r = w0 + (tid / kNB); r < w1; r += kTcThreads / kNB) mb = max(mb, Fmt<TI>::expo(Y[(size_t)r * ld + jb + j]));
+        for (int r = w0 + (tid / kNB); r < w1; r += kWorkers / kNB) mb = max(mb, Fmt<TI>::expo(Y[(size_t)r * ld + jb + j]));
       if (mb) atomicMax(&sh.exB[j], mb);
     }
-    __syncthreads();
+    workers_sync();
     const int nsub = (w1 - w0 + kKsub - 1) / kKsub;
-    for (int sc = 0; sc < nsub; ++sc) {
+    for (int sc = 0; sc < nsub; ++sc, ++g) {
       const int b = g & 1;
       if (g >= 2) wait_sub(sh, g - 2);
       unsigned char* st = stage_ptr<S>(smem, b);
       const int rb = w0 + sc * kKsub;
-      // A digits: task (column c of X, 8-row group rg)
-      for (int task = tid; task < 4 * 128; task += kTcThreads) {
-        const int c = task & 127, rg = task >> 7;
-        if (c >= k) continue;
-        const int E = sh.exA[c];
-        long long v[8];
+      // X quads: column c, rows rq * 4 .. rq * 4 + 3 of the sub-chunk
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int r = rb + rg * 8 + q;
-          v[q] = (r < w1) ? Fmt<TI>::fixed(X[(size_t)r * ld + c], E, F) : 0;
-        }
-        store_digits<S>(v, st + cm_off(c, rg * 8), kAPlane);
-      }
-      // B digits: task (column jb + j of Y, 8-row group rg)
-      for (int task = tid; task < 4 * kNB; task += kTcThreads) {
-        const int j = task & (kNB - 1), rg = task / kNB;
-        if (jb + j >= k) continue;
-        const int E = sh.exB[j];
-        long long v[8];
+      for (int h = 0; h < 2; ++h) {
+        const int c = tid & 127, rq = (tid >> 7) + 4 * h;
+        if (c < k) {
+          const int E = sh.exA[c];
+          long long v[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int r = rb + rg * 8 + q;
-          v[q] = (r < w1) ? Fmt<TI>::fixed(Y[(size_t)r * ld + jb + j], E, F) : 0;
+          for (int q = 0; q < 4; ++q) {
+            const int r = rb + rq * 4 + q;
+            v[q] = (r < w1) ? Fmt<TI>::fixed(X[(size_t)r * ld + c], E, F) : 0;
+          }
+          store_digits<S, 4>(v, st + quad_off(c, rq * 4), kAPlane);
         }
-        store_digits<S>(v, st + S * kAPlane + cm_off(j, rg * 8), kBPlane);
       }
-      fence_async_smem();
-      __syncthreads();
-      if (sh.abort_flag) break;
-      if (tid == 0) {
-        fence_after();
-        const uint32_t sA = su32(st);
-        issue_mmas<S, T>(tmem, sA, sA + S * kAPlane, sc == 0);
-        mma_commit(&sh.bar[b]);
+      // Y quad: column jb + j
+      {
+        const int j = tid & (kNB - 1), rq = tid / kNB;
+        if (jb + j < k) {
+          const int E = sh.exB[j];
+          long long v[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int r = rb + rq * 4 + q;
+            v[q] = (r < w1) ? Fmt<TI>::fixed(Y[(size_t)r * ld + jb + j], E, F) : 0;
+          }
+          store_digits<S, 4>(v, st + S * kAPlane + quad_off(j, rq * 4), kBPlane);
+        }
       }
-      ++g;
+      hand_over(sh, b);
     }
-    if (sh.abort_flag) break;
     wait_sub(sh, g - 1);
     fence_after();
     // exponent alignment of the running sums
@@ -486,7 +551,7 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
       sh.gR[tid] = newG - sh.gRun[tid];
       sh.gW[tid] = newG - sh.exB[tid];
     }
-    __syncthreads();
+    workers_sync();
     if (sh.abort_flag) break;
     const int eA = sh.exA[i_out];
     const int newE = max(e_run, eA);
@@ -506,10 +571,10 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
       }
     }
     fence_before();
-    __syncthreads();
+    workers_sync();
     if (tid < kNB) sh.gRun[tid] = max(sh.gRun[tid], sh.exB[tid]);
   }
-  __syncthreads();
+  workers_sync();
   if (!sh.abort_flag && i_out < k) {
     constexpr int off = value_offset<TI, TI, S, T>();
     double* out = partial + (size_t)blockIdx.x * k * k + (size_t)i_out * k;
@@ -522,7 +587,7 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
                      : pair_value(Rh[q], Rl[q], e_run + sh.gRun[c_base + q] + off);
     }
   }
-  tc_teardown<T>(sh, g, err);
+  tc_teardown<T>(sh, 0, err);
 }
 
 // ------------------------------------------------------------ expand ----------
@@ -553,12 +618,14 @@ __global__ void expand_prep_kernel(const double* __restrict__ Yx, int k, int ldy
       v[t] = (jb + j < k && q < k) ? Fmt<double>::fixed(Yx[(size_t)q * ldy + jb + j], ex[j], F) : 0;
     }
     unsigned char* blk = dig + ((size_t)blockIdx.x * nsub + sc) * S * kBPlane;
-    store_digits<S>(v, blk + cm_off(j, qg * 8), kBPlane);
+    store_digits<S, 8>(v, blk + cm_off(j, qg * 8), kBPlane);
   }
 }
 
 // U[r][j] = Z[r][j] + sum_q X[r][q] Yx[q][j] for the rows of 128-row tiles and the
-// columns of kNB-column blocks, tiles taken in turn by persistent CTAs.
+// columns of kNB-column blocks, tiles taken in turn by persistent CTAs.  Warps 0-15
+// form the X digits of each 32-value sub-chunk (two 4-value quads per thread), copy
+// the prepared Yx digits and write U; warp 16 issues the MMAs.
 template <typename TI, int S, int T>
 __global__ void __launch_bounds__(kTcThreads, 1)
 expand_tc_kernel(const TI* __restrict__ Z, const TI* __restrict__ X, const unsigned char* __restrict__ dig,
@@ -570,65 +637,68 @@ expand_tc_kernel(const TI* __restrict__ Z, const TI* __restrict__ X, const unsig
   constexpr int F = kBeta * S - 1;
   tc_setup<T>(sh, smem, 2 * stage_bytes(S));
   const uint32_t tmem = sh.tmem_slot;
+  const int ntiles = (n + 127) / 128;
+  if (warp == kMmaWarp) {
+    int g = 0;
+    bool ok = true;
+    for (int task = blockIdx.x; task < ntiles * njb && ok; task += gridDim.x)
+      for (int sc = 0; sc < nsub && ok; ++sc) {
+        ok = mma_step<S, T>(sh, smem, tmem, g, sc);
+        if (ok) ++g;
+      }
+    tc_teardown<T>(sh, g, err);
+    return;
+  }
   const int i_out = (warp & 3) * 32 + lane;
   const int c_base = (warp >> 2) * 16;
   const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c_base;
-  const int ntiles = (n + 127) / 128;
   int g = 0;
-  for (int task = blockIdx.x; task < ntiles * njb && !sh.abort_flag; task += gridDim.x) {
+  for (int task = blockIdx.x; task < ntiles * njb; task += gridDim.x) {
     const int rt = task / njb, jbi = task % njb;
     const int row0 = rt * 128, jb = jbi * kNB;
     // row exponents of the tile (4 threads per row)
-    __syncthreads();
+    workers_sync();
+    if (sh.abort_flag) break;
     if (tid < 128) sh.exA[tid] = 0;
     if (tid < kNB) sh.exB[tid] = gexp[jb + tid];
-    __syncthreads();
+    workers_sync();
     {
       const int rl = tid & 127, r = row0 + rl;
       int m = 0;
       if (r < n)
-        for (int q = (tid >> 7); q < k; q += kTcThreads / 128) m = max(m, Fmt<TI>::expo(X[(size_t)r * ld + q]));
+        for (int q = (tid >> 7); q < k; q += kWorkers / 128) m = max(m, Fmt<TI>::expo(X[(size_t)r * ld + q]));
       if (m) atomicMax(&sh.exA[rl], m);
     }
-    __syncthreads();
-    for (int sc = 0; sc < nsub; ++sc) {
+    workers_sync();
+    for (int sc = 0; sc < nsub; ++sc, ++g) {
       const int b = g & 1;
       if (g >= 2) wait_sub(sh, g - 2);
       unsigned char* st = stage_ptr<S>(smem, b);
-      // A digits: task (row rl of the tile, 8-value group qg)
-      for (int t = tid; t < 4 * 128; t += kTcThreads) {
-        const int rl = t & 127, qg = t >> 7;
+      // X quads: row rl of the tile, values qd * 4 .. qd * 4 + 3 of the sub-chunk
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rl = tid & 127, qd = (tid >> 7) + 4 * h;
         const int r = row0 + rl;
         const int E = sh.exA[rl];
-        long long v[8];
+        long long v[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int qq = sc * kKsub + qg * 8 + q;
+        for (int q = 0; q < 4; ++q) {
+          const int qq = sc * kKsub + qd * 4 + q;
           v[q] = (r < n && qq < k) ? Fmt<TI>::fixed(X[(size_t)r * ld + qq], E, F) : 0;
         }
-        store_digits<S>(v, st + cm_off(rl, qg * 8), kAPlane);
+        store_digits<S, 4>(v, st + quad_off(rl, qd * 4), kAPlane);
       }
-      // B digits: copy of the prepared planes of this column block and sub-chunk
+      // Yx digits: copy of the prepared planes of this column block and sub-chunk
       {
         const uint4* src = reinterpret_cast<const uint4*>(dig + ((size_t)jbi * nsub + sc) * S * kBPlane);
         uint4* dst = reinterpret_cast<uint4*>(st + S * kAPlane);
-        for (int q = tid; q < S * kBPlane / 16; q += kTcThreads) dst[q] = src[q];
+        for (int q = tid; q < S * kBPlane / 16; q += kWorkers) dst[q] = src[q];
       }
-      fence_async_smem();
-      __syncthreads();
-      if (sh.abort_flag) break;
-      if (tid == 0) {
-        fence_after();
-        const uint32_t sA = su32(st);
-        issue_mmas<S, T>(tmem, sA, sA + S * kAPlane, sc == 0);
-        mma_commit(&sh.bar[b]);
-      }
-      ++g;
+      hand_over(sh, b);
     }
-    if (sh.abort_flag) break;
     wait_sub(sh, g - 1);
     fence_after();
-    __syncthreads();
+    workers_sync();
     if (sh.abort_flag) break;
     const int r = row0 + i_out;
     const int eA = sh.exA[i_out];
@@ -651,9 +721,9 @@ expand_tc_kernel(const TI* __restrict__ Z, const TI* __restrict__ X, const unsig
       }
     }
     fence_before();
-    __syncthreads();
   }
-  tc_teardown<T>(sh, g, err);
+  workers_sync();
+  tc_teardown<T>(sh, 0, err);
 }
 
 template <typename TI> struct TcDigits;
