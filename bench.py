@@ -226,29 +226,48 @@ def read_traffic(name):
     return None
 
 
-def dominant_roofline(prof, hbm_peak, peak_kind):
-    """Roofline of the kernel class with the largest device time in the timed region:
-    FP64 arithmetic classes against the nominal FP64 peak when their algorithmic flops
-    take longer there than their bytes at the HBM peak, else against the HBM peak."""
-    name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
+# Kernel classes of the library's profiler that are one kernel each (the smoother
+# sweeps and the residuals are both row_update_kernel launches); dense_eig (about 15
+# kernels per call) and small are aggregates and are reported on their own.
+SINGLE_KERNELS = {"row_update_kernel": ("smooth_sweep", "residual"), "spmm_am_kernel": ("spmm_am",),
+                  "gram_tc_kernel": ("gram",), "expand_tc_kernel": ("expand",)}
+
+
+def class_roofline(name, d, hbm_peak, peak_kind):
+    """Roofline of one kernel (or class) from its summed profiler record: float64
+    arithmetic against the nominal FP64 peak when its algorithmic flops take longer
+    there than its bytes at the HBM peak, else against the HBM peak."""
     if d["launches"] == 0 or d["ms"] <= 0:
         return None
     per_launch_s = d["ms"] * 1e-3 / d["launches"]
     b = d["bytes"] / d["launches"]
     fl = d["flops"] / d["launches"]
     traffic = read_traffic(name)
+    common = {"traffic": traffic, "kernel": name, "algorithmic_flops_per_launch": fl,
+              "algorithmic_bytes_per_launch": b, "launches": d["launches"], "avg_launch_us": per_launch_s * 1e6}
     if fl / (FP64_NOMINAL_TFLOPS * 1e12) >= b / (hbm_peak * 1e9):
         ach = fl / per_launch_s / 1e12
-        return {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": traffic, "kernel": name,
-                "peak_source": "nominal FP64 (1.25 TFLOP/s at 2070 MHz, 152 SMs)",
-                "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": b,
-                "launches": d["launches"], "avg_launch_us": per_launch_s * 1e6}
-    ach = b / per_launch_s / 1e9
-    return {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-            "traffic": traffic, "kernel": name, "peak_source": peak_kind + " copy bandwidth",
-            "algorithmic_flops_per_launch": fl, "algorithmic_bytes_per_launch": b,
-            "launches": d["launches"], "avg_launch_us": per_launch_s * 1e6}
+        out = {"bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+               "frac": ach / FP64_NOMINAL_TFLOPS, "peak_source": "nominal FP64 (1.25 TFLOP/s at 2070 MHz, 152 SMs)"}
+    else:
+        ach = b / per_launch_s / 1e9
+        out = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+               "peak_source": peak_kind + " copy bandwidth"}
+    out.update(common)
+    return out
+
+
+def dominant_roofline(prof, hbm_peak, peak_kind):
+    """Roofline of the single kernel with the largest device time in the timed region."""
+    merged = {}
+    for kern, classes in SINGLE_KERNELS.items():
+        d = {"ms": 0.0, "launches": 0, "bytes": 0.0, "flops": 0.0}
+        for c in classes:
+            for key in d:
+                d[key] += prof.get(c, {}).get(key, 0)
+        merged[kern] = d
+    name, d = max(merged.items(), key=lambda kv: kv[1]["ms"])
+    return class_roofline(name, d, hbm_peak, peak_kind)
 
 
 def kernels_finest(bmg, prob, torch, hbm_peak, reps=10):
@@ -494,6 +513,7 @@ def run_ours(args):
     ms_max, e2e_max, value, e2e_value = whole_job(ms_total, e2e_total, conv_total, e2e_conv, dist, dev)
     hbm_peak, peak_kind = load_peaks()
     roof = dominant_roofline(prof, hbm_peak, peak_kind)
+    dense_roof = class_roofline("dense_eig", prof["dense_eig"], hbm_peak, peak_kind)
     extras = {}
     if rank == 0 and not args.no_extras:
         del Ud, Uh_t, flush
@@ -520,6 +540,8 @@ def run_ours(args):
                         "d2h_bytes_per_step": int(nL * nw * 8 + 2 * nw * 8)},
                 "gpu_launches": int(launches),
                 "roofline": roof,
+                "roofline_dense_eig": dense_roof,
+                "dense_eig_share": prof["dense_eig"]["ms"] / max(sum(v["ms"] for v in prof.values()), 1e-9),
                 "kernel_classes": class_table(prof, hbm_peak),
                 "kernel_timing": "per-class CUDA events over a second pass of the same steps",
                 "cpu_baseline": cpu,
@@ -535,13 +557,53 @@ def run_case(args):
     """Small fixed cases for profiler captures (no timing line of the metric):
     precision_r7 -- one precision-form solve, icosphere refined 7 times (163842
     vertices), 7 levels, k=128, 100 pairs, tol 1e-8, Jacobi nu=2, float32 blocks;
-    fp64_r7 -- the same in plain float64 (enriched problems of n = 170)."""
+    fp64_r7 -- the same in plain float64 (enriched problems of n = 170);
+    tc_163842 -- two tensor-core Grams and two expansions, 163842 x 128, float64 then
+    float32 blocks (seeded Gaussian data);
+    rows_655362 -- the SpMM [AX | MX] and one Jacobi sweep on the finest level of the
+    655362-vertex sphere, k = 128, float64 then float32 blocks."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1511_07042_gb300 import bmg, inputs
-    if args.case not in ("precision_r7", "fp64_r7"):
-        raise SystemExit("unknown case " + args.case)
+    cases = ("precision_r7", "fp64_r7", "tc_163842", "rows_655362")
+    if args.case not in cases:
+        raise SystemExit("unknown case %s (one of %s)" % (args.case, ", ".join(cases)))
+    if args.case == "tc_163842":
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        n, k = 163842, 128
+        for dt in (torch.float64, torch.float32):
+            X = torch.randn((n, k), dtype=dt, device="cuda", generator=gen)
+            Y = torch.randn((n, k), dtype=dt, device="cuda", generator=gen)
+            Yx = torch.randn((k, k), dtype=torch.float64, device="cuda", generator=gen)
+            U = torch.empty_like(X)
+            G = torch.empty((k, k), dtype=torch.float64, device="cuda")
+            gram = bmg.gram_tc if dt == torch.float64 else bmg.gram_tc_f32
+            for _ in range(2):
+                gram(X, Y, k, G)
+                bmg.expand(None, X, Yx, k, U, True)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "ok": True}), flush=True)
+        return 0
+    if args.case == "rows_655362":
+        v, t = inputs.icosahedron()
+        prob = bmg.Problem(v, t, 8)
+        prob.hierarchy(8)
+        n = prob.sizes(8)[0]
+        gen = torch.Generator(device="cuda").manual_seed(7)
+        for dt in (torch.float64, torch.float32):
+            X = torch.randn((n, 128), dtype=dt, device="cuda", generator=gen)
+            AX, MX, W = torch.empty_like(X), torch.empty_like(X), torch.empty_like(X)
+            s = torch.zeros(128, dtype=dt, device="cuda")
+            spmm = prob.spmm if dt == torch.float64 else prob.spmm_f32
+            smooth = prob.smooth if dt == torch.float64 else prob.smooth_f32
+            for _ in range(2):
+                spmm(8, 8, X, 128, AX, MX)
+                smooth(8, 8, X, None, s, 128, "jacobi", 1, 2.0 / 3.0, W)
+            del X, AX, MX, W
+        torch.cuda.synchronize()
+        print(json.dumps({"case": args.case, "ok": True}), flush=True)
+        return 0
     v, t = inputs.icosahedron()
     prob = bmg.Problem(v, t, 7)
     prob.hierarchy(7)
@@ -565,7 +627,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the measurements after the timed region")
-    ap.add_argument("--case", default=None, help="profiling case: precision_r7 | fp64_r7")
+    ap.add_argument("--case", default=None,
+                    help="profiling case: precision_r7 | fp64_r7 | tc_163842 | rows_655362")
     args = ap.parse_args()
     if args.case:
         return run_case(args)

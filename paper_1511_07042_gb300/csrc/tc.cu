@@ -299,6 +299,12 @@ __device__ __forceinline__ void pair_sra(long long& hi, long long& lo, int sh) {
   }
 }
 
+// The same value hi 2^28 + lo with lo reduced into [0, 2^28), so that it fits an int32.
+__device__ __forceinline__ void pair_norm(long long& hi, long long& lo) {
+  hi += lo >> kLoShift;
+  lo &= (1ll << kLoShift) - 1;
+}
+
 // v 2^e for a float64 v, by a power-of-two factor when 2^e is a normal number
 __device__ __forceinline__ double scale2(double v, int e) {
   if (e >= -1022 && e <= 1023) return v * __longlong_as_double((long long)(e + 1023) << 52);
@@ -480,7 +486,9 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
   const int i_out = (warp & 3) * 32 + lane;
   const int c_base = (warp >> 2) * 16;
   const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c_base;
-  long long Rh[16], Rl[16];
+  // running sums of the 16 outputs of this thread: Rh 2^28 + Rl, Rl in [0, 2^28)
+  long long Rh[16];
+  int Rl[16];
 #pragma unroll
   for (int q = 0; q < 16; ++q) { Rh[q] = 0; Rl[q] = 0; }
   int e_run = 0;
@@ -496,13 +504,17 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
     {
       const int c = tid & 127;
       int m = 0;
-      if (c < k)
+      if (c < k) {
+#pragma unroll 8
         for (int r = w0 + (tid >> 7); r < w1; r += kWorkers / 128) m = max(m, Fmt<TI>::expo(X[(size_t)r * ld + c]));
+      }
       if (m) atomicMax(&sh.exA[c], m);
       const int j = tid & (kNB - 1);
       int mb = 0;
-      if (jb + j < k)
+      if (jb + j < k) {
+#pragma unroll 8
         for (int r = w0 + (tid / kNB); r < w1; r += kWorkers / kNB) mb = max(mb, Fmt<TI>::expo(Y[(size_t)r * ld + jb + j]));
+      }
       if (mb) atomicMax(&sh.exB[j], mb);
     }
     workers_sync();
@@ -512,34 +524,41 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
       if (g >= 2) wait_sub(sh, g - 2);
       unsigned char* st = stage_ptr<S>(smem, b);
       const int rb = w0 + sc * kKsub;
-      // X quads: column c, rows rq * 4 .. rq * 4 + 3 of the sub-chunk
+      // X quads (column c, rows rq * 4 .. rq * 4 + 3 of the sub-chunk) and the Y quad
+      // (column jb + j): the 12 values are loaded first, so that their loads are in
+      // flight together
+      const int c = tid & 127, j = tid & (kNB - 1), rqy = tid / kNB;
+      TI xa[2][4], yb[4];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int c = tid & 127, rq = (tid >> 7) + 4 * h;
-        if (c < k) {
-          const int E = sh.exA[c];
-          long long v[4];
+        const int rq = (tid >> 7) + 4 * h;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int r = rb + rq * 4 + q;
-            v[q] = (r < w1) ? Fmt<TI>::fixed(X[(size_t)r * ld + c], E, F) : 0;
-          }
-          store_digits<S, 4>(v, st + quad_off(c, rq * 4), kAPlane);
+        for (int q = 0; q < 4; ++q) {
+          const int r = rb + rq * 4 + q;
+          xa[h][q] = (c < k && r < w1) ? X[(size_t)r * ld + c] : TI(0);
         }
       }
-      // Y quad: column jb + j
-      {
-        const int j = tid & (kNB - 1), rq = tid / kNB;
-        if (jb + j < k) {
-          const int E = sh.exB[j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = rb + rqy * 4 + q;
+        yb[q] = (jb + j < k && r < w1) ? Y[(size_t)r * ld + jb + j] : TI(0);
+      }
+      if (c < k) {
+        const int E = sh.exA[c];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
           long long v[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const int r = rb + rq * 4 + q;
-            v[q] = (r < w1) ? Fmt<TI>::fixed(Y[(size_t)r * ld + jb + j], E, F) : 0;
-          }
-          store_digits<S, 4>(v, st + S * kAPlane + quad_off(j, rq * 4), kBPlane);
+          for (int q = 0; q < 4; ++q) v[q] = Fmt<TI>::fixed(xa[h][q], E, F);
+          store_digits<S, 4>(v, st + quad_off(c, ((tid >> 7) + 4 * h) * 4), kAPlane);
         }
+      }
+      if (jb + j < k) {
+        const int E = sh.exB[j];
+        long long v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = Fmt<TI>::fixed(yb[q], E, F);
+        store_digits<S, 4>(v, st + S * kAPlane + quad_off(j, rqy * 4), kBPlane);
       }
       hand_over(sh, b);
     }
@@ -563,11 +582,15 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
       read_window<T>(tlane + ch * 4, wh, wl);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int j = c_base + ch * 4 + q;
-        pair_sra(Rh[ch * 4 + q], Rl[ch * 4 + q], dR + sh.gR[j]);
-        pair_sra(wh[q], wl[q], dW + sh.gW[j]);
-        Rh[ch * 4 + q] += wh[q];
-        Rl[ch * 4 + q] += wl[q];
+        const int jj = c_base + ch * 4 + q;
+        long long rh = Rh[ch * 4 + q], rl = Rl[ch * 4 + q];
+        pair_sra(rh, rl, dR + sh.gR[jj]);
+        pair_sra(wh[q], wl[q], dW + sh.gW[jj]);
+        rh += wh[q];
+        rl += wl[q];
+        pair_norm(rh, rl);
+        Rh[ch * 4 + q] = rh;
+        Rl[ch * 4 + q] = (int)rl;
       }
     }
     fence_before();
@@ -584,7 +607,7 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
       if (j < k)
         out[j] = (e_run == Fmt<TI>::emax || sh.gRun[c_base + q] == Fmt<TI>::emax)
                      ? __longlong_as_double(0x7FF8000000000000ll)
-                     : pair_value(Rh[q], Rl[q], e_run + sh.gRun[c_base + q] + off);
+                     : pair_value(Rh[q], (long long)Rl[q], e_run + sh.gRun[c_base + q] + off);
     }
   }
   tc_teardown<T>(sh, 0, err);
@@ -656,36 +679,46 @@ expand_tc_kernel(const TI* __restrict__ Z, const TI* __restrict__ X, const unsig
   for (int task = blockIdx.x; task < ntiles * njb; task += gridDim.x) {
     const int rt = task / njb, jbi = task % njb;
     const int row0 = rt * 128, jb = jbi * kNB;
-    // row exponents of the tile (4 threads per row)
+    // row exponents of the tile: 4 consecutive lanes per row, reading consecutive
+    // values, reduced by shuffles
     workers_sync();
     if (sh.abort_flag) break;
-    if (tid < 128) sh.exA[tid] = 0;
     if (tid < kNB) sh.exB[tid] = gexp[jb + tid];
-    workers_sync();
     {
-      const int rl = tid & 127, r = row0 + rl;
+      const int rl = tid >> 2, part = tid & 3, r = row0 + rl;
       int m = 0;
-      if (r < n)
-        for (int q = (tid >> 7); q < k; q += kWorkers / 128) m = max(m, Fmt<TI>::expo(X[(size_t)r * ld + q]));
-      if (m) atomicMax(&sh.exA[rl], m);
+      if (r < n) {
+#pragma unroll 8
+        for (int q = part; q < k; q += 4) m = max(m, Fmt<TI>::expo(X[(size_t)r * ld + q]));
+      }
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 1));
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, 2));
+      if (part == 0) sh.exA[rl] = m;
     }
     workers_sync();
     for (int sc = 0; sc < nsub; ++sc, ++g) {
       const int b = g & 1;
       if (g >= 2) wait_sub(sh, g - 2);
       unsigned char* st = stage_ptr<S>(smem, b);
-      // X quads: row rl of the tile, values qd * 4 .. qd * 4 + 3 of the sub-chunk
+      // X quads: row rl of the tile, values qd * 4 .. qd * 4 + 3 of the sub-chunk; 8
+      // consecutive lanes cover the 32 values of one row (coalesced), both quads
+      // loaded before either is converted
+      const int qd = tid & 7;
+      const int q0 = sc * kKsub + qd * 4;
+      TI xa[2][4];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const int rl = tid & 127, qd = (tid >> 7) + 4 * h;
-        const int r = row0 + rl;
+        const int r = row0 + (tid >> 3) + 64 * h;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) xa[h][q] = (r < n && q0 + q < k) ? X[(size_t)r * ld + q0 + q] : TI(0);
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rl = (tid >> 3) + 64 * h;
         const int E = sh.exA[rl];
         long long v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int qq = sc * kKsub + qd * 4 + q;
-          v[q] = (r < n && qq < k) ? Fmt<TI>::fixed(X[(size_t)r * ld + qq], E, F) : 0;
-        }
+        for (int q = 0; q < 4; ++q) v[q] = Fmt<TI>::fixed(xa[h][q], E, F);
         store_digits<S, 4>(v, st + quad_off(rl, qd * 4), kAPlane);
       }
       // Yx digits: copy of the prepared planes of this column block and sub-chunk
