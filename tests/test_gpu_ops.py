@@ -126,7 +126,8 @@ def _dense(bmg, Ah, Mh, sigma, k):
     return th.cpu().numpy(), Y.cpu().numpy(), int(rk.item())
 
 
-@pytest.mark.parametrize("n,k,sigma", [(10, 4, 0.0), (62, 20, 0.0), (106, 64, 1.5), (170, 128, 0.0)])
+@pytest.mark.parametrize("n,k,sigma", [(10, 4, 0.0), (62, 20, 0.0), (106, 64, 1.5), (170, 128, 0.0), (192, 150, 0.0),
+                                         (194, 150, 0.5), (200, 160, 0.0), (202, 160, 0.0)])
 def test_dense_eig_well_conditioned(env, n, k, sigma):
     bmg, prob, H = env
     rng = np.random.default_rng(n)
