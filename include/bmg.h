@@ -323,6 +323,16 @@ bmg_status bmg_gram_tc(const double* X, const double* Y, int n, int k, int ld, d
 bmg_status bmg_gram_tc_f32(const float* X, const float* Y, int n, int k, int ld, double* G,
                            void* stream);
 
+/* Test of the bounded waits inside the tensor-core kernels (every wait on an
+ * mbarrier gives up after a clock limit, frees the kernel's tensor memory and raises
+ * an error flag).  Runs a float64 Gram of a zero 4096 x 64 block whose MMA-issuing warp
+ * issues nothing, with a wait limit of about 1 ms, so that the waits for the MMA
+ * commits expire.  Returns BMG_ERR_TIMEOUT, as a product call after such an expiry
+ * does; BMG_ERR_CUDA if the waits did not expire.  The CUDA context stays usable
+ * (the tests run a normal Gram after it).  Allocates and frees its own buffers.
+ * Synchronous.                                                                      */
+bmg_status bmg_tc_timeout_selftest(void* stream);
+
 /* Ritz vectors in the enriched space V_{h1} + span X (Alg. 2 step 4; Alg. 3
  * step 5): U = Z + X Yx for X, Z, U [n][ld] device blocks (Z may be NULL: U = X Yx)
  * and Yx [k][ldy] device float64 coefficients; columns k..ld-1 of U are set to

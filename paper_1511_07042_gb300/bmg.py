@@ -86,6 +86,7 @@ def _load():
         "bmg_gram_noalloc": (i, [vp, vp, i, i, i, vp, vp]),
         "bmg_gram_tc": (i, [vp, vp, i, i, i, vp, vp]),
         "bmg_gram_tc_f32": (i, [vp, vp, i, i, i, vp, vp]),
+        "bmg_tc_timeout_selftest": (i, [vp]),
         "bmg_expand": (i, [vp, vp, vp, i, i, i, i, vp, i, vp]),
         "bmg_expand_f32": (i, [vp, vp, vp, i, i, i, i, vp, i, vp]),
         "bmg_dense_eig": (i, [vp, vp, i, d, i, vp, vp, vp, vp]),
@@ -392,6 +393,11 @@ def gram_tc(X, Y, k, G):
 def gram_tc_f32(X, Y, k, G):
     """G (float64) = X^T Y for float32 blocks on the tensor cores (k <= 128)."""
     _check(LIB.bmg_gram_tc_f32(_ptr(X), _ptr(Y), X.shape[0], k, X.shape[1], _ptr(G), _stream()))
+
+
+def tc_timeout_selftest():
+    """Status code of bmg_tc_timeout_selftest (BMG_ERR_TIMEOUT when the waits expired)."""
+    return int(LIB.bmg_tc_timeout_selftest(_stream()))
 
 
 def expand(Z, X, Yx, k, U, tensor_cores=True):

@@ -442,6 +442,22 @@ extern "C" bmg_status bmg_gram_tc_f32(const float* X, const float* Y, int n, int
   });
 }
 
+// Test of the tensor-core kernels' bounded waits: a Gram whose waits are made to
+// expire (gram_tc_timeout_selftest).  Returns what a product call returns after such
+// an expiry, BMG_ERR_TIMEOUT, once the kernel has returned; the context stays usable.
+extern "C" bmg_status bmg_tc_timeout_selftest(void* stream) {
+  return guarded([&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    DBuf<double> X((size_t)4096 * 64), G((size_t)64 * 64), partial((size_t)gram_tc_parts(4096, 64) * 64 * 64);
+    DBuf<int> flag(1);
+    BMG_CUDA(cudaMemsetAsync(X.get(), 0, sizeof(double) * 4096 * 64, s));
+    BMG_CUDA(cudaMemsetAsync(flag.get(), 0, sizeof(int), s));
+    gram_tc_timeout_selftest(X.get(), G.get(), partial.get(), flag.get(), s);
+    check_tc_flag(flag.get(), s);
+    fail(BMG_ERR_CUDA, "tc timeout self-test: the bounded waits did not expire");
+  });
+}
+
 template <typename T>
 static void expand_entry(const T* Z, const T* X, const double* Yx, int n, int k, int ld, int ldy, T* U,
                          int tensor_cores, void* stream) {
@@ -877,8 +893,7 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
     const T* ca = b.AX;
     const T* cm = b.MX;
     for (int j = f; j >= 2; --j) {
-      restrict_<T>(p->meshOf(j - 1), ca, b.cA[j - 1], ld, s);
-      restrict_<T>(p->meshOf(j - 1), cm, b.cB[j - 1], ld, s);
+      restrict2_<T>(p->meshOf(j - 1), ca, b.cA[j - 1], cm, b.cB[j - 1], ld, s);
       ca = b.cA[j - 1];
       cm = b.cB[j - 1];
     }

@@ -269,6 +269,8 @@ template <typename T>
 void prolong(const Mesh& fine, const T* Xc, T* Y, int ld, bool add, cudaStream_t s);
 template <typename T>
 void restrict_(const Mesh& coarse, const T* R, T* Zc, int ld, cudaStream_t s);
+template <typename T>
+void restrict2_(const Mesh& coarse, const T* R, T* Zc, const T* R2, T* Zc2, int ld, cudaStream_t s);
 // sym: Y = S X with S symmetric, so G is symmetric: only the 4x4 tiles on and above
 // the diagonal are formed (half the products) and the rest mirrored.
 void gram(const double* X, const double* Y, int n, int k, int ld, double* G, double* partial,
@@ -304,6 +306,9 @@ void gram_tc(const TI* X, const TI* Y, int n, int k, int ld, double* G, double* 
 template <typename TI>
 void expand_tc(const TI* Zf, const TI* X, const double* Yx, int n, int k, int ld, int ldy, TI* U,
                unsigned char* scratch, int* err, cudaStream_t s);
+// A float64 Gram of the zero 4096 x 64 block X whose bounded waits are made to expire
+// (see tc.cu); raises *err.
+void gram_tc_timeout_selftest(const double* X, double* G, double* partial, int* err, cudaStream_t s);
 template <typename T>
 void eig_residuals(const T* AU, const T* MU, const T* U, const double* lam, int n, int k, int ld,
                    double* partial, int nparts, double* out, cudaStream_t s);

@@ -365,13 +365,16 @@ __global__ void row_norms_kernel(const int* __restrict__ row_ptr, const T* __res
 
 // ---- transfers ----------------------------------------------------------------
 // Y[v] (+)= P Xc: parents (a, b) of fine vertex v; a == b: copy, else the mean.
+// order (optional): the fine rows in Morton order of their positions, so that the
+// parents gathered by neighbouring threads are near one another in space and found in
+// L2 (each row is computed alone: the result does not depend on the order).
 template <typename T>
 __global__ void prolong_kernel(const int* __restrict__ par, int nf, const T* __restrict__ Xc,
-                               T* __restrict__ Y, int nch, int add) {
+                               T* __restrict__ Y, int nch, int add, const int* __restrict__ order) {
   constexpr int W = Chunk<T>::W;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)nf * nch) return;
-  const int v = (int)(t / nch), c = (int)(t % nch);
+  const int v = order ? order[t / nch] : (int)(t / nch), c = (int)(t % nch);
   const int a = par[2 * v], b = par[2 * v + 1];
   T r[W];
   ldv(Xc, (size_t)a * nch + c, r);
@@ -391,14 +394,18 @@ __global__ void prolong_kernel(const int* __restrict__ par, int nf, const T* __r
 }
 
 // Zc[i] = R[i] + sum over edges (i, j): R[mid(i,j)] / 2, in ascending fine index.
+// order (optional): the coarse rows in Morton order, as in prolong_kernel.
 template <typename T>
 __global__ void restrict_kernel(const int* __restrict__ row_ptr, const int* __restrict__ col,
                                 const int* __restrict__ mid, int nc, const T* __restrict__ R,
-                                T* __restrict__ Z, int nch) {
+                                T* __restrict__ Z, const T* __restrict__ R2, T* __restrict__ Z2, int nch,
+                                const int* __restrict__ order) {
+  // blockIdx.y = 1: the second block pair of a two-block launch
+  if (blockIdx.y == 1) { R = R2; Z = Z2; }
   constexpr int W = Chunk<T>::W;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)nc * nch) return;
-  const int i = (int)(t / nch), c = (int)(t % nch);
+  const int i = order ? order[t / nch] : (int)(t / nch), c = (int)(t % nch);
   T acc[W];
   ldv(R, (size_t)i * nch + c, acc);
   for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p) {
@@ -983,7 +990,8 @@ void prolong(const Mesh& fine, const T* Xc, T* Y, int ld, bool add, cudaStream_t
   const int nch = ld / Chunk<T>::W;
   const size_t total = (size_t)fine.n * nch;
   prof_begin(KC_TRANSFER, s);
-  prolong_kernel<T><<<blocks_for(total, 256), 256, 0, s>>>(fine.parents.get(), fine.n, Xc, Y, nch, add ? 1 : 0);
+  prolong_kernel<T><<<blocks_for(total, 256), 256, 0, s>>>(fine.parents.get(), fine.n, Xc, Y, nch, add ? 1 : 0,
+                                                            fine.row_order.get());
   check_launch("prolong_kernel");
   const double nc = (fine.n + 6) / 4.0;  // vertices of the coarse level of a refined sphere
   prof_end(KC_TRANSFER, s, 8.0 * fine.n + tb<T>() * ld * (nc + fine.n * (add ? 2.0 : 1.0)), 1.0 * fine.n * ld);
@@ -991,14 +999,22 @@ void prolong(const Mesh& fine, const T* Xc, T* Y, int ld, bool add, cudaStream_t
 
 template <typename T>
 void restrict_(const Mesh& coarse, const T* R, T* Zc, int ld, cudaStream_t s) {
+  restrict2_<T>(coarse, R, Zc, nullptr, nullptr, ld, s);
+}
+
+// Zc = P^T R and, when R2 is given, Zc2 = P^T R2 in the same launch.
+template <typename T>
+void restrict2_(const Mesh& coarse, const T* R, T* Zc, const T* R2, T* Zc2, int ld, cudaStream_t s) {
   const int nch = ld / Chunk<T>::W;
   const size_t total = (size_t)coarse.n * nch;
+  const int pairs = R2 ? 2 : 1;
   prof_begin(KC_TRANSFER, s);
-  restrict_kernel<T><<<blocks_for(total, 256), 256, 0, s>>>(coarse.row_ptr.get(), coarse.col.get(), coarse.mid.get(),
-                                                             coarse.n, R, Zc, nch);
+  restrict_kernel<T><<<dim3((unsigned)blocks_for(total, 256), pairs), 256, 0, s>>>(
+      coarse.row_ptr.get(), coarse.col.get(), coarse.mid.get(), coarse.n, R, Zc, R2, Zc2, nch,
+      coarse.row_order.get());
   check_launch("restrict_kernel");
   const double nf = 4.0 * coarse.n - 6.0;
-  prof_end(KC_TRANSFER, s, 8.0 * coarse.nnz + tb<T>() * ld * (nf + coarse.n), 2.0 * nf * ld);
+  prof_end(KC_TRANSFER, s, pairs * (8.0 * coarse.nnz + tb<T>() * ld * (nf + coarse.n)), pairs * 2.0 * nf * ld);
 }
 
 int gram_parts(int n) { return std::max(1, std::min(304, (n + 63) / 64)); }
@@ -1124,6 +1140,7 @@ std::string tuned_report() {
                             cudaStream_t, bool);                                                       \
   template void prolong<T>(const Mesh&, const T*, T*, int, bool, cudaStream_t);                        \
   template void restrict_<T>(const Mesh&, const T*, T*, int, cudaStream_t);                            \
+  template void restrict2_<T>(const Mesh&, const T*, T*, const T*, T*, int, cudaStream_t);             \
   template void eig_residuals<T>(const T*, const T*, const T*, const double*, int, int, int, double*,  \
                                  int, double*, cudaStream_t);                                          \
   template void expand<T>(const T*, const T*, const double*, int, int, int, int, T*, cudaStream_t);    \

@@ -103,9 +103,9 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// Waits for the completion of the phase with the given parity; false after about
-// kWaitCycles clocks without it.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Waits for the completion of the phase with the given parity; false after `limit`
+// clocks without it (kWaitCycles, about 2 s, except in the timeout self-test).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
   while (true) {
     uint32_t done;
@@ -116,7 +116,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(su32(bar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > kWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -341,7 +341,16 @@ template <> struct Epi<float> {
   }
 };
 
+// Launch controls: the limit of every bounded wait, and (timeout self-test only) an
+// MMA warp that issues nothing, so that the workers' waits for commits expire.
+struct TcCtl {
+  long long wait_cycles;
+  int no_mma;
+};
+
 struct TcShared {
+  long long wait_limit;
+  int no_mma;
   uint64_t bar[2];    // stage b free again: the commit of its MMAs (one arrival)
   uint64_t full[2];   // stage b holds digits: one arrival per worker warp
   uint32_t tmem_slot;
@@ -370,10 +379,12 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 template <int T>
-__device__ __forceinline__ void tc_setup(TcShared& sh, unsigned char* smem, int bytes) {
+__device__ __forceinline__ void tc_setup(TcShared& sh, unsigned char* smem, int bytes, const TcCtl& ctl) {
   const int tid = threadIdx.x;
   for (int q = tid; q < bytes / 16; q += blockDim.x) reinterpret_cast<uint4*>(smem)[q] = make_uint4(0, 0, 0, 0);
   if (tid == 0) {
+    sh.wait_limit = ctl.wait_cycles;
+    sh.no_mma = ctl.no_mma;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sh.bar[0])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&sh.bar[1])));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&sh.full[0])), "n"(kWorkers / 32));
@@ -399,7 +410,7 @@ __device__ __forceinline__ void tc_teardown(TcShared& sh, int issued, int* err) 
   if (threadIdx.x == kWorkers) {
     for (int b = 0; b < 2; ++b) {
       const int uses = (issued - b + 1) / 2;   // commits made on stage b
-      if (uses > 0 && !mbar_wait(&sh.bar[b], (uint32_t)((uses - 1) & 1))) atomicExch(&sh.abort_flag, 1);
+      if (uses > 0 && !mbar_wait(&sh.bar[b], (uint32_t)((uses - 1) & 1), sh.wait_limit)) atomicExch(&sh.abort_flag, 1);
     }
   }
   fence_before();
@@ -415,7 +426,7 @@ __device__ __forceinline__ void tc_teardown(TcShared& sh, int issued, int* err) 
 // on expiry.  Workers read the flag only right after a worker barrier, so that they
 // leave their loops together.
 __device__ __forceinline__ void wait_sub(TcShared& sh, int gi) {
-  if (!mbar_wait(&sh.bar[gi & 1], (uint32_t)((gi >> 1) & 1))) atomicExch(&sh.abort_flag, 1);
+  if (!mbar_wait(&sh.bar[gi & 1], (uint32_t)((gi >> 1) & 1), sh.wait_limit)) atomicExch(&sh.abort_flag, 1);
 }
 
 // The MMA warp's part for sub-chunk g (sc: its index in the accumulation window):
@@ -426,13 +437,13 @@ __device__ __forceinline__ bool mma_step(TcShared& sh, unsigned char* smem, uint
   const int lane = threadIdx.x & 31;
   const int b = g & 1;
   int ok = 1;
-  if (lane == 0) ok = mbar_wait(&sh.full[b], (uint32_t)((g >> 1) & 1)) ? 1 : 0;
+  if (lane == 0) ok = mbar_wait(&sh.full[b], (uint32_t)((g >> 1) & 1), sh.wait_limit) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   if (!ok) {
     if (lane == 0) atomicExch(&sh.abort_flag, 1);
     return false;
   }
-  if (lane == 0) {
+  if (lane == 0 && !sh.no_mma) {
     fence_after();
     const uint32_t sA = su32(stage_ptr<S>(smem, b));
     issue_mmas<S, T>(tmem, sA, sA + S * kAPlane, sc == 0);
@@ -458,7 +469,7 @@ __device__ __forceinline__ void hand_over(TcShared& sh, int b) {
 template <typename TI, int S, int T>
 __global__ void __launch_bounds__(kTcThreads, 1)
 gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k, int ld, int rows_per_part,
-               double* __restrict__ partial, int* err) {
+               double* __restrict__ partial, int* err, TcCtl ctl) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ TcShared sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -466,7 +477,7 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
   const int r0 = blockIdx.x * rows_per_part;
   const int r1 = min(n, r0 + rows_per_part);
   constexpr int F = kBeta * S - 1;
-  tc_setup<T>(sh, smem, 2 * stage_bytes(S));
+  tc_setup<T>(sh, smem, 2 * stage_bytes(S), ctl);
   const uint32_t tmem = sh.tmem_slot;
   if (warp == kMmaWarp) {
     int g = 0;
@@ -478,7 +489,7 @@ gram_tc_kernel(const TI* __restrict__ X, const TI* __restrict__ Y, int n, int k,
         if (ok) ++g;
       }
     }
-    tc_teardown<T>(sh, g, err);
+    tc_teardown<T>(sh, sh.no_mma ? 0 : g, err);
     return;
   }
   if (tid < kNB) sh.gRun[tid] = 0;
@@ -653,12 +664,12 @@ template <typename TI, int S, int T>
 __global__ void __launch_bounds__(kTcThreads, 1)
 expand_tc_kernel(const TI* __restrict__ Z, const TI* __restrict__ X, const unsigned char* __restrict__ dig,
                  const int* __restrict__ gexp, int n, int k, int ld, int nsub, int njb, TI* __restrict__ U,
-                 int* err) {
+                 int* err, TcCtl ctl) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ TcShared sh;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int F = kBeta * S - 1;
-  tc_setup<T>(sh, smem, 2 * stage_bytes(S));
+  tc_setup<T>(sh, smem, 2 * stage_bytes(S), ctl);
   const uint32_t tmem = sh.tmem_slot;
   const int ntiles = (n + 127) / 128;
   if (warp == kMmaWarp) {
@@ -669,7 +680,7 @@ expand_tc_kernel(const TI* __restrict__ Z, const TI* __restrict__ X, const unsig
         ok = mma_step<S, T>(sh, smem, tmem, g, sc);
         if (ok) ++g;
       }
-    tc_teardown<T>(sh, g, err);
+    tc_teardown<T>(sh, sh.no_mma ? 0 : g, err);
     return;
   }
   const int i_out = (warp & 3) * 32 + lane;
@@ -789,9 +800,10 @@ size_t expand_tc_scratch_bytes(int k) {
   return (size_t)njb * nsub * TcDigits<double>::S * kBPlane + sizeof(int) * njb * kNB + 256;
 }
 
+namespace {
 template <typename TI>
-void gram_tc(const TI* X, const TI* Y, int n, int k, int ld, double* G, double* partial, int nparts, int* err,
-             cudaStream_t s, bool sym) {
+void gram_tc_launch(const TI* X, const TI* Y, int n, int k, int ld, double* G, double* partial, int nparts,
+                    int* err, cudaStream_t s, bool sym, TcCtl ctl) {
   if (k > kTcMaxK) fail(BMG_ERR_INVALID_ARG, "gram_tc: k > 128");
   constexpr int S = TcDigits<TI>::S, T = TcDigits<TI>::T;
   const int njb = (k + kNB - 1) / kNB;
@@ -802,10 +814,27 @@ void gram_tc(const TI* X, const TI* Y, int n, int k, int ld, double* G, double* 
   check_cuda(cudaFuncSetAttribute(gram_tc_kernel<TI, S, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem),
              "cudaFuncSetAttribute(gram_tc_kernel)");
   prof_begin(KC_GRAM, s);
-  gram_tc_kernel<TI, S, T><<<dim3(parts, njb), kTcThreads, smem, s>>>(X, Y, n, k, ld, rows, partial, err);
+  gram_tc_kernel<TI, S, T><<<dim3(parts, njb), kTcThreads, smem, s>>>(X, Y, n, k, ld, rows, partial, err, ctl);
   check_launch("gram_tc_kernel");
   gram_reduce(partial, parts, k, G, sym, s);
   prof_end(KC_GRAM, s, 2.0 * sizeof(TI) * n * ld + 16.0 * parts * k * k + 8.0 * k * k, 2.0 * n * k * k);
+}
+}  // namespace
+
+template <typename TI>
+void gram_tc(const TI* X, const TI* Y, int n, int k, int ld, double* G, double* partial, int nparts, int* err,
+             cudaStream_t s, bool sym) {
+  gram_tc_launch<TI>(X, Y, n, k, ld, G, partial, nparts, err, s, sym, TcCtl{kWaitCycles, 0});
+}
+
+// The bounded waits of the tensor-core kernels, made to run out: a float64 Gram of a
+// zero 4096 x 64 block whose MMA warp issues nothing, with waits of about 1 ms.  The
+// workers' waits for the commits expire; the kernel must raise *err, free its tensor
+// memory and return.  Buffers are the caller's (partial: gram_tc_parts(4096, 64) * 64^2
+// doubles).
+void gram_tc_timeout_selftest(const double* X, double* G, double* partial, int* err, cudaStream_t s) {
+  gram_tc_launch<double>(X, X, 4096, 64, 64, G, partial, gram_tc_parts(4096, 64), err, s, true,
+                         TcCtl{2000000LL, 1});
 }
 
 template <typename TI>
@@ -823,7 +852,8 @@ void expand_tc(const TI* Zf, const TI* X, const double* Yx, int n, int k, int ld
   prof_begin(KC_EXPAND, s);
   expand_prep_kernel<S><<<njb, 256, 0, s>>>(Yx, k, ldy, nsub, scratch, gexp);
   check_launch("expand_prep_kernel");
-  expand_tc_kernel<TI, S, T><<<grid, kTcThreads, smem, s>>>(Zf, X, scratch, gexp, n, k, ld, nsub, njb, U, err);
+  expand_tc_kernel<TI, S, T><<<grid, kTcThreads, smem, s>>>(Zf, X, scratch, gexp, n, k, ld, nsub, njb, U, err,
+                                                             TcCtl{kWaitCycles, 0});
   check_launch("expand_tc_kernel");
   prof_end(KC_EXPAND, s, 3.0 * sizeof(TI) * n * ld + 8.0 * k * k, 2.0 * n * k * k);
 }

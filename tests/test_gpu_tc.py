@@ -144,3 +144,19 @@ def test_tc_non_finite_inputs_give_nan(gpu_bmg, dtype):
     gpu_bmg.expand(None, Xd, Yx, k, U, True)
     Uh = U[:, :k].cpu().numpy()
     assert np.all(np.isnan(Uh[200])) and np.all(np.isfinite(np.delete(Uh, 200, axis=0)))
+
+
+def test_bounded_wait_expiry_returns_timeout_and_context_stays_usable(gpu_bmg):
+    """A Gram whose MMA warp issues nothing, with waits of about 1 ms: the workers'
+    waits for the commits expire, the kernel frees its tensor memory and returns, and
+    the host sees BMG_ERR_TIMEOUT (9).  A normal Gram afterwards is exact."""
+    assert gpu_bmg.tc_timeout_selftest() == 9
+    assert "bounded wait" in gpu_bmg.LIB.bmg_last_error().decode()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    n, k = 4099, 64
+    X, Y = rng.standard_normal((n, k)), rng.standard_normal((n, k))
+    G = torch.empty((k, k), dtype=torch.float64, device="cuda")
+    gpu_bmg.gram_tc(torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda(), k, G)
+    err = np.abs(G.cpu().numpy() - X.T @ Y)
+    assert np.all(err <= 2.0 ** -48 * (np.abs(X).T @ np.abs(Y)))
