@@ -109,12 +109,27 @@ typedef struct {
                              /*    columns of X (the previous shift plus the mean   */
                              /*    shifted quotient; Alg. 3 step 4, Sec. 5.3); the  */
                              /*    first cycle uses sigma.  0: sigma throughout.    */
+  int selection;             /* Ritz pairs kept by every Rayleigh-Ritz (Sec. 5.2):  */
+                             /*    0: the k smallest |theta| (index-updating: the   */
+                             /*    enrichment follows the spectrum near the shift); */
+                             /*    1: index-fixed, positions index_first ..         */
+                             /*    index_first + k - 1 of the ascending Ritz values */
+                             /*    (moved down when past the top of the values      */
+                             /*    present); the wanted pairs are the n_wanted of   */
+                             /*    the window nearest the shift.                    */
+  int index_first;           /* first position of the index-fixed window (>= 0)   */
+  int coarse_start;          /* 1: X0 is ignored (may be NULL) and the start block  */
+                             /*    is the k eigenvectors of the level-1 problem     */
+                             /*    (the Galerkin pair of level 2 on level 1) chosen */
+                             /*    by `selection`, prolongated to level 2 (Alg. 4   */
+                             /*    step 1); needs k <= N_1.  0: X0 as given.        */
 } bmg_options;
 
 /* Fills the defaults: Jacobi, nu=2, omega=2/3, shifted form, full depth,
  * 6 intermediate cycles, no intermediate tolerance, 200 finest cycles, float64,
  * switch_tol 1e-7 (near the float32 floor of the relative residual), no stop,
- * no resume, tensor cores, autotuned shapes and CUDA graphs on, fixed shift.  autotune and
+ * no resume, tensor cores, autotuned shapes and CUDA graphs on, fixed shift,
+ * index-updating selection, start block X0.  autotune and
  * graphs change no result (the tests check bit-identical outputs); tensor_cores
  * changes the rounding of the products.                                          */
 void bmg_default_options(bmg_options* opt);

@@ -62,6 +62,18 @@ class Options:
     tol_intermediate: float = -1.0   # early stop on levels 2..L-1 (negative: none)
     max_cycles: int = 200
     adaptive_shift: bool = False     # Alg. 3 step 4: shift from the Rayleigh quotients of X
+    # Which Ritz pairs are kept (Sec. 5.2): "nearest" -- the k smallest |theta| in every
+    # Rayleigh-Ritz (the enrichment follows the spectrum near the shift: index-updating);
+    # "index" -- positions index_first .. index_first + k - 1 of the ascending Ritz
+    # values in every Rayleigh-Ritz (index-fixed), the wanted ones being those of the
+    # window nearest the shift.
+    selection: str = "nearest"
+    index_first: int = 0
+    # Start block (Alg. 4 step 1): "given" -- X0 on level 2 as passed; "coarse" -- the
+    # eigenvectors of the level-1 problem (the Galerkin pair of level 2 on level 1)
+    # selected as above (an index window past the 42 coarse values moved down to the
+    # top k of them), prolongated to level 2 (k <= 42).
+    init: str = "given"
 
 
 @dataclass
@@ -126,8 +138,28 @@ def select_order(theta: np.ndarray) -> np.ndarray:
     return np.lexsort((idx, theta, np.abs(theta)))
 
 
-def svqb_eig(Ahat, Mhat, sigma: float, k: int, tau: float = SVQB_TAU):
-    """Smallest-|theta| k pairs of (Ahat - sigma Mhat) y = theta Mhat y via SVQB.
+def select_pairs(theta: np.ndarray, k: int, selection: str = "nearest", first: int = 0) -> np.ndarray:
+    """Indices of the k kept pairs, ordered by (|theta|, theta, index).
+
+    "nearest": the k smallest |theta|.  "index": positions first .. first + k - 1 of
+    the values in ascending order (ties by index), then put in the same order; a window
+    that runs past the top of the r values present is moved down to positions
+    r - k .. r - 1 (a rank-deficient enriched space, or the coarse problem alone).
+    """
+    if selection == "nearest":
+        return select_order(theta)[:k]
+    if selection != "index":
+        raise ValueError(selection)
+    asc = np.lexsort((np.arange(theta.shape[0]), theta))
+    first = min(max(first, 0), theta.shape[0] - k)
+    win = asc[first:first + k]
+    return win[select_order(theta[win])]
+
+
+def svqb_eig(Ahat, Mhat, sigma: float, k: int, tau: float = SVQB_TAU, selection: str = "nearest",
+             first: int = 0):
+    """k pairs of (Ahat - sigma Mhat) y = theta Mhat y via SVQB: the smallest |theta|,
+    or a window of positions of the ascending spectrum (select_pairs).
 
     Returns (theta [k], Y [n,k]) with Y^T Mhat Y = I.
     """
@@ -143,7 +175,7 @@ def svqb_eig(Ahat, Mhat, sigma: float, k: int, tau: float = SVQB_TAU):
     At = B.T @ (Ahat - sigma * Mhat) @ B
     At = 0.5 * (At + At.T)
     theta, W = sla.eigh(At)
-    sel = select_order(theta)[:k]
+    sel = select_pairs(theta, k, selection, first)
     return theta[sel], B @ W[:, sel]
 
 
@@ -248,7 +280,7 @@ def cycle(H: Hierarchy, f: int, X, sigma: float, k: int, n_wanted: int, tol: flo
     if opt.adaptive_shift and not first:
         sigma = mean_rayleigh_quotient(X, AX, MX)
     Ahat, Mhat = enriched_matrices(H, f, X, AX, MX)
-    theta, Y = svqb_eig(Ahat, Mhat, sigma, k)
+    theta, Y = svqb_eig(Ahat, Mhat, sigma, k, selection=opt.selection, first=opt.index_first)
     lam = theta + sigma
     n1 = H.A[1].shape[0]
     U = prolong_chain(H, Y[:n1], 1, f) + X @ Y[n1:]
@@ -261,6 +293,19 @@ def cycle(H: Hierarchy, f: int, X, sigma: float, k: int, n_wanted: int, tol: flo
     if not conv or smooth_if_converged:
         Xn = source_smoothing(H, f, U, MU, theta, lam, sigma, opt)
     return CycleResult(lam, U, resid, Xn, sigma), conv
+
+
+def coarse_start(H: Hierarchy, sigma: float, k: int, opt: Options):
+    """Alg. 4 step 1: the level-1 eigenpairs of (A - sigma M) y = theta M y for the
+    Galerkin pair of level 2 (P_2^T A_2 P_2, P_2^T M_2 P_2), k of them kept as in every
+    Rayleigh-Ritz (select_pairs), prolongated to level 2."""
+    A1 = H.GA[2][1].toarray()
+    M1 = H.GM[2][1].toarray()
+    if k > A1.shape[0]:
+        raise ValueError("coarse start: k = %d > %d coarse vertices" % (k, A1.shape[0]))
+    theta, V = sla.eigh(0.5 * (A1 + A1.T) - sigma * 0.5 * (M1 + M1.T), 0.5 * (M1 + M1.T))
+    sel = select_pairs(theta, k, opt.selection, opt.index_first)
+    return H.P[2] @ V[:, sel]
 
 
 @dataclass
@@ -279,6 +324,8 @@ def bfmg(H: Hierarchy, X0, k: int, n_wanted: int, sigma: float, tol: float,
          opt: Options = Options(), verbose=False) -> SolveResult:
     """Alg. 4: cycles on levels 2..L, prolongating the Ritz vectors between levels."""
     L = H.levels
+    if opt.init == "coarse":
+        X0 = coarse_start(H, sigma, k, opt)
     X = np.array(X0, dtype=np.float64, copy=True)
     cycles, history, level_lams, shifts = [], [], [], []
     res = None

@@ -37,7 +37,8 @@ class Options(C.Structure):
                 ("tol_intermediate", C.c_double), ("max_cycles", C.c_int), ("precision", C.c_int),
                 ("switch_tol", C.c_double), ("stop_after_cycles", C.c_int), ("resume", C.c_int),
                 ("tensor_cores", C.c_int), ("autotune", C.c_int), ("graphs", C.c_int),
-                ("adaptive_shift", C.c_int)]
+                ("adaptive_shift", C.c_int), ("selection", C.c_int), ("index_first", C.c_int),
+                ("coarse_start", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -140,7 +141,7 @@ def _stream():
 def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_depth=99,
             cycles_intermediate=6, tol_intermediate=-1.0, max_cycles=200, precision="fp64",
             switch_tol=1e-7, stop_after_cycles=0, resume=False, tensor_cores=True, autotune=True,
-            graphs=True, adaptive_shift=False) -> Options:
+            graphs=True, adaptive_shift=False, selection="nearest", index_first=0, init="given") -> Options:
     o = Options()
     LIB.bmg_default_options(C.byref(o))
     o.smoother = SMOOTHERS[smoother]
@@ -159,6 +160,9 @@ def options(smoother="jacobi", nu=2, omega=2.0 / 3.0, form="shifted", vcycle_dep
     o.autotune = int(bool(autotune))
     o.graphs = int(bool(graphs))
     o.adaptive_shift = int(bool(adaptive_shift))
+    o.selection = {"nearest": 0, "index": 1}[selection]
+    o.index_first = int(index_first)
+    o.coarse_start = {"given": 0, "coarse": 1}[init]
     return o
 
 
@@ -265,7 +269,8 @@ class Problem:
 
     def solve(self, X0, k, n_wanted, sigma, tol, opt=None, evecs=True, evecs_device=None):
         """BFMG solve.  X0: numpy [N_2, k] (host) or torch CUDA tensor (device); None
-        with options(resume=True), which continues from the state given to set_state.
+        with options(resume=True), which continues from the state given to set_state,
+        or with options(init="coarse"), which starts from the coarse eigenvectors.
 
         Returns (evals, evecs, resid, info) with evecs a numpy array, or the
         caller's torch tensor `evecs_device` when given.

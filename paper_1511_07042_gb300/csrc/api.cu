@@ -118,6 +118,9 @@ extern "C" void bmg_default_options(bmg_options* o) {
   o->autotune = 1;
   o->graphs = 1;
   o->adaptive_shift = 0;
+  o->selection = 0;
+  o->index_first = 0;
+  o->coarse_start = 0;
 }
 
 extern "C" const char* bmg_last_error(void) { return g_last_error.c_str(); }
@@ -909,7 +912,8 @@ bool run_cycle(bmg_problem* p, SolveWork& w, Blocks<T>& b, int f, const bmg_opti
     prof_end(KC_SMALL, s, 32.0 * nh * nh, 0.0);
     // 3: enriched eigensolve
     dense_eig(w.Ahat.get(), w.Mhat.get(), nh, sigma, k, w.theta.get(), w.Y.get(), w.rank.get(), w.dense.get(),
-              w.dquality.get(), sizeof(T) == sizeof(float) ? kDropFP32 : kDropFP64, n1, s);
+              w.dquality.get(), sizeof(T) == sizeof(float) ? kDropFP32 : kDropFP64, n1, s,
+              o.selection ? o.index_first : -1);
     prof_begin(KC_SMALL, s);
     shifts_kernel<T><<<grid_of(ld, 128), 128, 0, s>>>(w.theta.get(), k, ld, sigma, o.form, w.lam.get(), b.shift);
     check_launch("shifts_kernel");
@@ -1031,13 +1035,16 @@ bmg_options checked_options(const bmg_problem* p, int k, int n_wanted, double si
   const int n1 = p->meshOf(1).n, n2 = p->meshOf(2).n;
   if (k < 1 || k > 160 || n_wanted < 1 || n_wanted > k || k > n2 || n1 + k > 224)
     fail(BMG_ERR_INVALID_ARG, "need 1 <= n_wanted <= k <= min(N_2, 160) and N_1 + k <= 224");
-  if ((!X0 && o.resume != 1) || !evals) fail(BMG_ERR_INVALID_ARG, "X0 (unless resuming) and evals are required");
+  if ((!X0 && o.resume != 1 && o.coarse_start != 1) || !evals)
+    fail(BMG_ERR_INVALID_ARG, "X0 (unless resuming or starting from the coarse eigenvectors) and evals are required");
+  if (o.coarse_start == 1 && k > n1) fail(BMG_ERR_INVALID_ARG, "coarse_start needs k <= N_1");
   if (!(tol > 0.0) || !std::isfinite(sigma)) fail(BMG_ERR_INVALID_ARG, "bad tol or sigma");
   if (o.nu < 1 || o.nu > 64 || o.smoother < 0 || o.smoother > 3 || o.form < 0 || o.form > 1 ||
       o.max_cycles < 1 || o.cycles_intermediate < 1 || !(o.omega > 0.0) || o.precision < 0 ||
       o.precision > 1 || !(o.switch_tol > 0.0) || o.stop_after_cycles < 0 || o.resume < 0 || o.resume > 1 ||
       o.tensor_cores < 0 || o.tensor_cores > 1 || o.autotune < 0 || o.autotune > 1 || o.graphs < 0 || o.graphs > 1 ||
-      o.adaptive_shift < 0 || o.adaptive_shift > 1)
+      o.adaptive_shift < 0 || o.adaptive_shift > 1 || o.selection < 0 || o.selection > 1 || o.index_first < 0 ||
+      o.coarse_start < 0 || o.coarse_start > 1)
     fail(BMG_ERR_INVALID_ARG, "bad options");
   return o;
 }
@@ -1055,9 +1062,10 @@ struct StateHead {
   double omega, tol_intermediate, switch_tol;
   int32_t adaptive_shift, pad3;
   double mu;                       // shift of the next cycle (adaptive_shift)
+  int32_t selection, index_first, coarse_start, pad4;
 };
 constexpr uint32_t kStateMagic = 0x53474d42u;   // "BMGS"
-constexpr uint32_t kStateVersion = 2;
+constexpr uint32_t kStateVersion = 3;
 size_t state_bytes(const StateHead& h) {
   return sizeof(StateHead) + sizeof(double) * ((size_t)h.n_hist + h.n_info + 2 * (size_t)h.k + (size_t)h.n_f * h.k) +
          sizeof(int32_t) * 2 * (size_t)h.n_info;
@@ -1067,6 +1075,9 @@ void head_options(StateHead& h, const bmg_options& o) {
   h.cycles_intermediate = o.cycles_intermediate; h.max_cycles = o.max_cycles; h.precision = o.precision;
   h.tensor_cores = o.tensor_cores;
   h.adaptive_shift = o.adaptive_shift;
+  h.selection = o.selection;
+  h.index_first = o.index_first;
+  h.coarse_start = o.coarse_start;
   h.omega = o.omega; h.tol_intermediate = o.tol_intermediate; h.switch_tol = o.switch_tol;
 }
 bool same_options(const StateHead& h, const bmg_options& o) {
@@ -1075,6 +1086,7 @@ bool same_options(const StateHead& h, const bmg_options& o) {
   return g.smoother == h.smoother && g.nu == h.nu && g.form == h.form && g.vcycle_depth == h.vcycle_depth &&
          g.cycles_intermediate == h.cycles_intermediate && g.max_cycles == h.max_cycles &&
          g.precision == h.precision && g.tensor_cores == h.tensor_cores && g.adaptive_shift == h.adaptive_shift &&
+         g.selection == h.selection && g.index_first == h.index_first && g.coarse_start == h.coarse_start &&
          g.omega == h.omega && g.tol_intermediate == h.tol_intermediate &&
          g.switch_tol == h.switch_tol;
 }
@@ -1115,7 +1127,8 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
   const int ld = w.ld;
   // the cycle graphs hold these values as launch arguments: recapture when they change
   const std::vector<double> sig = {sigma, (double)o.form, (double)o.smoother, (double)o.nu, o.omega,
-                                   (double)o.vcycle_depth, (double)o.precision, (double)o.tensor_cores};
+                                   (double)o.vcycle_depth, (double)o.precision, (double)o.tensor_cores,
+                                   (double)(o.selection ? o.index_first : -1)};
   if (sig != w.gsig) {
     BMG_CUDA(cudaStreamSynchronize(s));
     w.drop_graphs();
@@ -1171,6 +1184,22 @@ bool solve_impl(bmg_problem* p, SolveWork& w, int k, int n_wanted, double sigma,
     BMG_CUDA(cudaMemcpy2DAsync(w.X.get(), sizeof(double) * ld, q, sizeof(double) * k, sizeof(double) * k, h.n_f,
                                cudaMemcpyHostToDevice, s));
     if (fp32) convert_block(w.X.get(), ld, b32.X, b32.ld, h.n_f, k, s);
+  } else if (o.coarse_start) {
+    // Alg. 4 step 1: the eigenvectors of the level-1 problem for the Galerkin pair of
+    // level 2, k of them kept as every Rayleigh-Ritz keeps its pairs, prolongated to
+    // level 2 (own eigensolve workspace: the cycle's holds a cached factor)
+    const int n1 = p->meshOf(1).n;
+    const size_t cwn = dense_work_doubles(n1);
+    DBuf<double> cw(cwn), cth(k), cy((size_t)n1 * k), cq(1);
+    DBuf<int> crk(1);
+    BMG_CUDA(cudaMemsetAsync(cw.get(), 0, sizeof(double) * cwn, s));
+    dense_eig(w.AQ[2].get(), w.MQ[2].get(), n1, sigma, k, cth.get(), cy.get(), crk.get(), cw.get(), cq.get(),
+              kDropFP64, 0, s, o.selection ? o.index_first : -1);
+    pack_coarse_kernel<double><<<grid_of((size_t)n1 * ld, 256), 256, 0, s>>>(cy.get(), n1, k, ld, b64.cC[1]);
+    check_launch("pack_coarse_kernel");
+    prolong<double>(p->meshOf(2), b64.cC[1], w.X.get(), ld, false, s);
+    if (fp32) convert_block(w.X.get(), ld, b32.X, b32.ld, n2, k, s);
+    BMG_CUDA(cudaStreamSynchronize(s));   // the local buffers are freed on return
   } else {
     // X0 -> X on level 2 (ld-strided; padding columns stay zero)
     BMG_CUDA(cudaMemsetAsync(w.X.get(), 0, sizeof(double) * (size_t)n2 * ld, s));

@@ -327,8 +327,11 @@ constexpr double kDropFP32 = 1e-5;
 // nq > 0: the leading nq x nq block of Mhat repeats from call to call on the same
 // work buffer (the coarse space's mass matrix), whose factor is then kept in `work`
 // (zero-filled before its first use).
+// sel_first < 0: the k pairs of smallest |theta| (index-updating); >= 0: positions
+// sel_first .. sel_first + k - 1 of the ascending values (index-fixed; moved down when
+// past the top), ordered by (|theta|, theta, index) like the former.
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k,
                double* theta, double* Y, int* rank, double* work, double* quality, double drop_tol,
-               int nq, cudaStream_t s);
+               int nq, cudaStream_t s, int sel_first = -1);
 size_t dense_work_doubles(int n);
 }  // namespace bmg

@@ -1402,7 +1402,11 @@ cluster_kernel(int n, DW w) {
 }
 
 // ------------------------------------------- 5. selection and back-transform --
-__global__ void select_kernel(int k, int n, const double* acc, DW w, double* __restrict__ theta) {
+// sel_first < 0: the k pairs of smallest |theta|.  sel_first >= 0: the pairs at
+// positions f .. f + k - 1 of the ascending values (ties by index), f = min(sel_first,
+// r - k) (a window past the top of the r values present moves down).  Either way the
+// kept pairs are ordered by (|theta|, theta, index).
+__global__ void select_kernel(int k, int n, const double* acc, DW w, double* __restrict__ theta, int sel_first) {
   const int r = *w.rank;
   for (int c = threadIdx.x; c < k; c += blockDim.x) w.order[c] = 0;   // rank < k: stays in bounds
   __shared__ double red[32];
@@ -1415,17 +1419,34 @@ __global__ void select_kernel(int k, int n, const double* acc, DW w, double* __r
   // order by (|lam|, lam, index) through integer keys: the magnitude's bits, then a
   // bit that puts a negative value before a positive one of the same magnitude
   __shared__ unsigned long long key[kMaxN];
+  __shared__ unsigned char keep[kMaxN];
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(w.lam[i]);
     key[i] = ((b & 0x7FFFFFFFFFFFFFFFull) << 1) | ((b >> 63) ^ 1ull);
+    keep[i] = 1;
   }
   __syncthreads();
+  if (sel_first >= 0) {
+    // index window: position of each value in ascending order (order_key is monotone)
+    const int f = max(0, min(sel_first, r - k));
+    for (int i = threadIdx.x; i < r; i += blockDim.x) {
+      const unsigned long long ki = order_key(w.lam[i]);
+      int pos = 0;
+      for (int j = 0; j < r; ++j) {
+        const unsigned long long kj = order_key(w.lam[j]);
+        pos += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+      }
+      keep[i] = (pos >= f && pos < f + k) ? 1 : 0;
+    }
+    __syncthreads();
+  }
   for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    if (!keep[i]) continue;
     const unsigned long long ki = key[i];
     int rk = 0;
     for (int j = 0; j < r; ++j) {
       const unsigned long long kj = key[j];
-      rk += (kj < ki || (kj == ki && j < i)) ? 1 : 0;
+      rk += (keep[j] && (kj < ki || (kj == ki && j < i))) ? 1 : 0;
     }
     if (rk < k) w.order[rk] = i;
   }
@@ -1587,7 +1608,8 @@ size_t dense_work_doubles(int n) {
 }
 
 void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int k, double* theta,
-               double* Y, int* rank, double* work, double* quality, double drop_tol, int nq, cudaStream_t s) {
+               double* Y, int* rank, double* work, double* quality, double drop_tol, int nq, cudaStream_t s,
+               int sel_first) {
   if (n < 1 || n > kMaxDense || k < 1 || k > n) fail(BMG_ERR_INVALID_ARG, "dense_eig: need 1 <= k <= n <= 224");
   TraceRange trace("enriched eigensolve");
   prof_begin(KC_DENSE, s);
@@ -1670,7 +1692,7 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
     gemm({w.W, w.W, w.G, nullptr, 1, 0, 0, 1}, {w.W, w.P, w.SS, nullptr, 1, 0, 0, 2}, 2, w, n, nacc, s);
   }
   // 5. selection and back-transform
-  select_kernel<<<1, 512, 0, s>>>(k, n, accs + 3 * nsteps, w, theta);
+  select_kernel<<<1, 512, 0, s>>>(k, n, accs + 3 * nsteps, w, theta, sel_first);
   check_launch("select_kernel");
   backsub(n, k, w, Y, s);
   copy_out_kernel<<<1, 1, 0, s>>>(w, rank, quality);

@@ -157,3 +157,79 @@ def test_adaptive_shift_matches_oracle(gpu_bmg, precision):
     wr, Vr = certify.nearest(w, V, info.final_shift, 9)
     err, ang = certify.compare_to_reference(M, ev, U, wr, Vr)
     assert err.max() <= 1e-10 and ang.max() <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_coarse_start_matches_oracle(gpu_bmg, precision):
+    """Alg. 4 step 1 on the GPU (X0 not given): the level-1 eigenvectors of the level-2
+    Galerkin pair, prolongated, then BFMG; the 16 lowest pairs of the 642-vertex sphere
+    against LAPACK, and the oracle's cycle counts from the same start."""
+    v, t = inputs.icosahedron()
+    prob = gpu_bmg.Problem(v, t, 3)
+    prob.hierarchy(3)
+    ev, U, rs, info = prob.solve(None, 20, 16, 0.0, 1e-10, gpu_bmg.options(init="coarse", precision=precision))
+    assert info.converged == 1
+    H = obmg.build_hierarchy(v, t, 3, colour=False)
+    A, M = H.A[3], H.M[3]
+    w, V = certify.dense_pencil_eigs(A, M)
+    err, ang = certify.compare_to_reference(M, ev, U, w[:16], V[:, :16])
+    assert err.max() <= 1e-10 and ang.max() <= 1e-8
+    if precision == "fp64":
+        ref = obmg.bfmg(H, None, 20, 16, 0.0, 1e-10, obmg.Options(init="coarse"))
+        assert abs(info.total_cycles - sum(ref.cycles)) <= 1
+
+
+@pytest.mark.parametrize("init", ["coarse", "given"])
+def test_index_fixed_window_matches_dense(gpu_bmg, init):
+    """Sec. 5.2's index-fixed enrichment on the GPU: k = 20 Ritz pairs kept at positions
+    16..35 of the ascending spectrum in every Rayleigh-Ritz, 9 wanted: the l = 4
+    multiplet of the 2562-vertex sphere (LAPACK eigenvalues 16..24) with its subspace."""
+    v, t = inputs.icosahedron()
+    prob = gpu_bmg.Problem(v, t, 4)
+    prob.hierarchy(4)
+    X0 = None if init == "coarse" else inputs.gaussian_block(inputs.n_vertices(2), 20, 1001)
+    ev, U, rs, info = prob.solve(X0, 20, 9, 0.0, 1e-10, gpu_bmg.options(init=init, selection="index", index_first=16,
+                                                                        max_cycles=60))
+    assert info.converged == 1
+    H = obmg.build_hierarchy(v, t, 4, colour=False)
+    A, M = H.A[4], H.M[4]
+    w, V = certify.dense_pencil_eigs(A, M)
+    err, ang = certify.compare_to_reference(M, ev, U, w[16:25], V[:, 16:25], rel_gap=1e-4)
+    assert err.max() <= 1e-10 and ang.max() <= 1e-8
+    ref = obmg.bfmg(H, X0, 20, 9, 0.0, 1e-10, obmg.Options(init=init, selection="index", index_first=16,
+                                                           max_cycles=60))
+    assert abs(info.total_cycles - sum(ref.cycles)) <= 1
+
+
+def test_coarse_start_argument_checks(gpu_bmg):
+    v, t = inputs.icosahedron()
+    prob = gpu_bmg.Problem(v, t, 3)
+    prob.hierarchy(3)
+    with pytest.raises(gpu_bmg.BmgError) as e:
+        prob.solve(None, 48, 16, 0.0, 1e-10, gpu_bmg.options(init="coarse"))
+    assert e.value.code == 1
+    with pytest.raises(gpu_bmg.BmgError) as e:
+        prob.solve(None, 20, 16, 0.0, 1e-10, gpu_bmg.options())          # X0 required without it
+    assert e.value.code == 1
+
+
+@pytest.mark.parametrize("kw", [dict(smoother="jacobi", nu=2, omega=2 / 3),
+                                dict(smoother="mcsgs", nu=1, omega=1.0),
+                                dict(smoother="jacobi", nu=2, omega=2 / 3, vcycle_depth=0, max_cycles=60)])
+def test_convergence_history_follows_the_oracle(gpu_bmg, kw):
+    """The per-cycle largest wanted residual of the GPU solve against the oracle's on
+    the 2562-vertex sphere (k = 20, 16 pairs, tol 1e-10): the same cycles on every
+    level, and every cycle's residual within a factor 2 of the oracle's while it is
+    above 1e-12.  With the down-leg (pinned in the oracle: h-independent rate) and
+    without it (vcycle_depth = 0, slower), so the GPU's coarse corrections follow the
+    oracle's cycle by cycle, not only at convergence (without the down-leg neither
+    reaches the tolerance within 60 finest cycles)."""
+    ev, U, rs, info, H = solve(gpu_bmg, 4, 20, 16, 0.0, 1e-10, colour=True, **kw)
+    X0 = inputs.gaussian_block(inputs.n_vertices(2), 20, 1001)
+    ref = obmg.bfmg(H, X0, 20, 16, 0.0, 1e-10, obmg.Options(**kw))
+    assert bool(info.converged) == ref.converged == ("vcycle_depth" not in kw)
+    gh = info.history()
+    assert [f for f, _, _ in gh] == [h[0] for h in ref.history]
+    for (f, _, rg), (fr, c, ro) in zip(gh, ref.history):
+        if ro > 1e-12:
+            assert 0.5 <= rg / ro <= 2.0, (f, c, rg, ro)

@@ -146,3 +146,59 @@ def test_adaptive_shift_sec53_analogue():
     # with the shift held at 32 the same start settles on the l = 5 multiplet instead
     fixed = bmg.bfmg(H, X0, 20, 9, 32.0, 1e-10, bmg.Options(max_cycles=100))
     assert np.sum(np.abs(fixed.lam[:9] - 31.0) < 1.0) >= 8
+
+
+def test_select_pairs_nearest_and_index_windows():
+    """Sec. 5.2's two enrichment rules on a fixed spectrum: index-updating keeps the k
+    smallest |theta|; index-fixed keeps a window of positions of the ascending values
+    (moved down when it runs past the top), both returned by (|theta|, theta, index)."""
+    theta = np.array([5.0, -1.0, 3.0, 0.5, -4.0, 2.0, 9.0, 7.0])
+    assert list(bmg.select_pairs(theta, 3)) == [3, 1, 5]                       # 0.5, -1, 2
+    # ascending: -4(4) -1(1) 0.5(3) 2(5) 3(2) 5(0) 7(7) 9(6)
+    assert list(bmg.select_pairs(theta, 3, "index", 2)) == [3, 5, 2]           # 0.5, 2, 3
+    assert sorted(bmg.select_pairs(theta, 3, "index", 0)) == [1, 3, 4]
+    assert sorted(bmg.select_pairs(theta, 3, "index", 7)) == [0, 6, 7]        # moved down to 5..7
+    assert list(bmg.select_pairs(theta, 3, "index", 7)) == [0, 7, 6]
+
+
+def test_coarse_start_converges_to_dense_pairs():
+    """Alg. 4 step 1: starting from the level-1 eigenvectors (the Galerkin pair of level
+    2) prolongated to level 2, BFMG reaches the 16 lowest pairs of the 642-vertex sphere."""
+    H = bmg.build_hierarchy(*inputs.icosahedron(), 3)
+    A, M = H.A[3], H.M[3]
+    w = sla.eigh(A.toarray(), M.toarray(), eigvals_only=True)
+    res = bmg.bfmg(H, None, 20, 16, 0.0, 1e-10, bmg.Options(init="coarse"))
+    assert res.converged
+    assert np.max(np.abs(np.sort(res.lam[:16]) - w[:16]) / np.maximum(w[:16], 1.0)) < 1e-12
+    X0 = bmg.coarse_start(H, 0.0, 20, bmg.Options())
+    # the start block lies in the span of the prolongated coarse space
+    Q = H.P[2].toarray()
+    coef = np.linalg.lstsq(Q, X0, rcond=None)[0]
+    assert np.max(np.abs(Q @ coef - X0)) < 1e-12
+
+
+@pytest.mark.parametrize("R", [3, 4])
+@pytest.mark.parametrize("init", ["coarse", "given"])
+def test_index_fixed_window_recovers_a_multiplet(R, init):
+    """Sec. 5.2's index-fixed enrichment: a window of 20 kept Ritz pairs at positions
+    16..35 (l = 4 and its neighbours), 9 wanted, recovers the l = 4 multiplet
+    (eigenvalues 16..24 of the pencil, LAPACK) with k = 20 vectors, without the 16
+    eigenpairs below it in X."""
+    H = bmg.build_hierarchy(*inputs.icosahedron(), R)
+    A, M = H.A[R], H.M[R]
+    w = sla.eigh(A.toarray(), M.toarray(), eigvals_only=True)
+    X0 = None if init == "coarse" else inputs.gaussian_block(162, 20, 1001)
+    res = bmg.bfmg(H, X0, 20, 9, 0.0, 1e-10, bmg.Options(init=init, selection="index", index_first=16,
+                                                            max_cycles=60))
+    assert res.converged
+    assert np.max(np.abs(np.sort(res.lam[:9]) - w[16:25]) / w[16:25]) < 1e-10
+
+
+def test_index_fixed_window_past_the_coarse_resolution_does_not_converge():
+    """The same rule for the l = 6 multiplet (positions 36..48), which the 42-vertex
+    coarse space does not resolve, stalls: the paper likewise finds the recoverable
+    eigenvalues bounded by the coarse space (Sec. 5.2, 54 coarse DoF)."""
+    H = bmg.build_hierarchy(*inputs.icosahedron(), 3)
+    res = bmg.bfmg(H, None, 20, 13, 0.0, 1e-10, bmg.Options(init="coarse", selection="index", index_first=36,
+                                                              max_cycles=40))
+    assert not res.converged and res.resid[:13].max() > 1e-6
