@@ -327,11 +327,11 @@ bmg_status bmg_gram_f32(const float* X, const float* Y, int n, int k, int ld, do
 /* The Rayleigh-Ritz block products of Sec. 4.1 (G = X^T Y, same arguments and
  * result as bmg_gram / bmg_gram_f32) on the tcgen05 tensor cores, 1 <= k <= 128.
  * Each value is turned into an integer relative to the largest exponent of its
- * column over a window of 128 rows and cut into balanced 7-bit digits (BF16 values
+ * column over a window of 256 rows and cut into balanced 7-bit digits (BF16 values
  * exactly); the digit products are summed exactly in float32 tensor memory and
  * combined in int64, so only the digit pairs left out and the rounding of the
  * integers contribute error: below 2^-53 (float64 blocks, 8 digits, 36 pairs) or
- * 2^-33 (float32 blocks, 5 digits, 15 pairs) of 128 max|x| max|y| per window.
+ * 2^-33 (float32 blocks, 5 digits, 15 pairs) of 256 max|x| max|y| per window.
  * Synchronous.  BMG_ERR_TIMEOUT if a bounded wait inside the kernel expired.     */
 bmg_status bmg_gram_tc(const double* X, const double* Y, int n, int k, int ld, double* G,
                        void* stream);

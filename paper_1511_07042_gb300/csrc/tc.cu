@@ -13,7 +13,7 @@
 // multiplication"), but with the exactness carried by integer arithmetic:
 //
 //  1. Scaling.  Every value x of a scaling group (Gram: one column of X or Y over a
-//     window of 128 rows; expand: one row of X over its k values, one column of Yx)
+//     window of 256 rows; expand: one row of X over its k values, one column of Yx)
 //     with group exponent E (the largest biased exponent in the group, so that
 //     |x| < 2^(E - bias + 1)) is turned into the integer V = round(x 2^(F - E + bias
 //     - 1)), |V| <= 2^F, F = 7 S - 1.
@@ -22,8 +22,8 @@
 //  3. Products.  For every digit pair (s, t) with s + t <= T the tensor cores
 //     accumulate sum_r d_s(x_r) d_t(y_r) in float32 in tensor memory; pairs with
 //     the same diagonal s + t share an accumulator.  A diagonal holds at most 8
-//     pairs over at most 128 terms of magnitude <= 2^12, so every partial sum is an
-//     integer of magnitude <= 2^22 and the float32 accumulation is exact.
+//     pairs over at most 256 terms of magnitude <= 2^12, so every partial sum is an
+//     integer of magnitude <= 2^23 and the float32 accumulation is exact.
 //  4. Combination.  The diagonals of a window are read back (tcgen05.ld), turned
 //     into int32 exactly, and combined with shifts into one int64 per output
 //     element; windows are added in int64 after aligning their exponents.  Only the
@@ -55,7 +55,7 @@ constexpr int kWorkers = 512;             // 16 warps forming digits and reading
 constexpr int kTcThreads = kWorkers + 32; // and one warp that issues the MMAs
 constexpr int kMmaWarp = kWorkers / 32;
 constexpr int kKsub = 32;                // K rows per sub-chunk (two MMA K-steps of 16)
-constexpr int kWindow = 128;             // K rows per exact accumulation window (Gram)
+constexpr int kWindow = 256;             // K rows per exact accumulation window (Gram)
 constexpr int kNB = 64;                  // output columns per CTA (N of the MMA)
 constexpr int kBeta = 7;                 // digit width
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
@@ -122,10 +122,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// exact int32 of a float32 integer of magnitude <= 2^22
-__device__ __forceinline__ int f2i_exact(uint32_t bits) {
-  return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
-}
+// int32 of a float32 holding an integer (exact: |value| <= 2^23 here)
+__device__ __forceinline__ int f2i_exact(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
 
 // ------------------------------------------------------------ digits ----------
 template <typename T> struct Fmt;
@@ -253,7 +251,7 @@ __device__ __forceinline__ void issue_mmas(uint32_t tmem, uint32_t sA, uint32_t 
 // Exact combination of the diagonals of one output element into two int64 words:
 //   lo = sum_{dg = T-3..T} A_dg 2^((T - dg) beta),  hi = sum_{dg = 2..T-4} A_dg 2^((T - 4 - dg) beta),
 //   sum_dg A_dg 2^((T - dg) beta) = hi 2^(4 beta) + lo,
-// each word below 2^43 in magnitude for |A_dg| <= 2^22 (no bit is dropped).
+// each word below 2^44 in magnitude for |A_dg| <= 2^23 (no bit is dropped).
 constexpr int kLoShift = 4 * kBeta;
 __device__ __forceinline__ long long sra(long long x, int sh) { return sh >= 63 ? (x < 0 ? -1 : 0) : (x >> sh); }
 

@@ -1,7 +1,7 @@
 """Tensor-core (tcgen05) Gram products and Ritz-vector expansion from exact digit
 slices, against float64 references on the CPU.
 
-The claimed error (include/bmg.h, bmg_gram_tc): each window of K <= 128 rows
+The claimed error (include/bmg.h, bmg_gram_tc): each window of K <= 256 rows
 contributes at most about 2^-53 K max|x| max|y| (float64 blocks) or 2^-33 K max|x|
 max|y| (float64 accumulation of float32 blocks), the maxima over the window's column;
 the expansion likewise with k terms and the maxima over a row of X and a column of Yx.
@@ -24,7 +24,7 @@ def dev(X, dtype=torch.float64):
     return T
 
 
-def window_bound(X, Y, w=128):
+def window_bound(X, Y, w=256):
     """sum over windows of w rows of w_rows * max|x_i| * max|y_j| (k x k)."""
     n = X.shape[0]
     b = np.zeros((X.shape[1], Y.shape[1]))
