@@ -517,6 +517,8 @@ __device__ __forceinline__ float start_value(int a, int j) {
 }
 // Solves per eigenvector (each followed by orthonormalisation inside the clusters).
 constexpr int kInvIters = 3;
+// NS = ceil(n / 32): row and column slots per thread of the tridiagonalisation.
+template <int NS>
 __global__ void __launch_bounds__(kBig)
 eig32_kernel(int n, DW w) {
   extern __shared__ float fsm[];
@@ -525,7 +527,8 @@ eig32_kernel(int n, DW w) {
   const int r = *w.rank;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int nwarps = kBig / 32;
-  float* A = fsm;                                   // r x r
+  float* A = fsm;                                   // r x r, row stride ld (odd)
+  constexpr int ld = 32 * NS + 1;
   // T is symmetric in exact arithmetic; its two triangular solves leave rounding
   // asymmetry.  Symmetrise it in place (each pair i <= j by one thread) for the FP64
   // refinement, whose symmetric products assume it, and take its FP32 copy.
@@ -535,95 +538,135 @@ eig32_kernel(int n, DW w) {
       const double v = 0.5 * (w.T[i * n + j] + w.T[j * n + i]);
       w.T[i * n + j] = v;
       w.T[j * n + i] = v;
-      A[i * r + j] = (float)v;
-      A[j * r + i] = (float)v;
+      A[i * ld + j] = (float)v;
+      A[j * ld + i] = (float)v;
     }
   }
+  for (int q = tid; q < r * (ld - r); q += kBig) A[(q / (ld - r)) * ld + r + q % (ld - r)] = 0.f;
   __syncthreads();
   // --- Householder tridiagonalisation, v_j stored in column j below the subdiagonal.
-  // The squared norm of the next column below its subdiagonal is summed per warp
-  // while the rank-2 update of the current step writes it (colsq, double-buffered),
-  // so a step needs no separate block reduction.
-  // The first kTriDiagWarps warps run the reduction, synchronised by a named barrier
-  // (the others, if any, wait at the block barrier after it; 32 warps measured faster
-  // than 8).  A step has two barriers: every warp forms the reflector's scalars itself
-  // (norm from the per-warp column sums, beta, tau) and reads v from column j as it
-  // goes, so the product p = tau A22 v starts at once; warp 0 also stores v, which the
-  // rank-2 update reads after the first barrier and which is written into column j
-  // (for the back-transformation) before the second.
+  // Ownership is 2-D cyclic and fixed for the whole reduction: warp w holds the rows
+  // w + 32 q and lane l the columns l + 32 i (q, i < NS) of A.  Rows have the stride
+  // ld = 32 NS + 1: every lane's column slots exist in every row (the columns from r
+  // on are zero), so a step touches the thread's whole slot set at fixed offsets from
+  // a row base with no per-element test; the columns left of the trailing block enter
+  // with v = w = 0 and keep their values.  The odd stride keeps the column reads of v
+  // conflict-free.  A step has two barriers.  Every warp forms the reflector's scalars
+  // itself, from the per-warp sums of the column's squares that the previous step left
+  // in colsq (double-buffered), then:
+  //   p = t A22 v: per live row of the warp, NS products per lane, and the row sums of
+  //   the warp in one transposing reduction (9 shuffles for up to 8 rows);
+  //   barrier;  K = (t/2) p.v,  A22 -= v w^T + w v^T (w = p - K v) on the thread's
+  //   elements, v_j into column j, the next column's squares by its owner lane;
+  //   barrier.
+  static_assert(kTriDiagWarps == 32 && kBig == 1024, "rows are dealt to 32 warps");
+  static_assert(NS <= 8, "the row sums are reduced as eight slots");
   __shared__ float colsq[2][32];
-  constexpr int tdw = kTriDiagWarps;
-  if (wid < tdw) {
-    for (int j = 0; j + 2 < r; ++j) {
-      const int m = r - j - 1;
-      const float a0 = A[(j + 1) * r + j];
-      float xn2;
-      if (j == 0) {
-        float part = 0.f;
-        for (int i = j + 2 + lane; i < r; i += 32) part += A[i * r + j] * A[i * r + j];
-        xn2 = warp_sumf(part);
-      } else {
-        xn2 = warp_sumf(lane < tdw ? colsq[j & 1][lane] : 0.f);
-      }
-      float beta = a0, t = 0.f, scale = 0.f;
-      if (xn2 > 0.f) {
-        beta = -copysignf(sqrtf(a0 * a0 + xn2), a0);
-        t = (beta - a0) / beta;
-        scale = 1.f / (a0 - beta);
-      }
-      const float* colj = A + (j + 1) * r + j;      // colj[q * r] = A[j + 1 + q][j]
-      if (wid == 0) {
-        for (int q = lane; q < m; q += 32) vb[q] = (q == 0) ? 1.f : colj[q * r] * scale;
-        if (lane == 0) { d[j] = A[j * r + j]; e[j] = beta; tau[j] = t; }
-      }
-      if (t != 0.f) {
-        // p = t A22 v: 8 lanes per row, 4 rows per warp (the row loop is uniform over
-        // the warp, so every lane reaches the shuffles)
-        for (int a0r = 4 * wid; a0r < m; a0r += 4 * tdw) {
-          const int a = a0r + (lane >> 3);
-          float sv = 0.f;
-          if (a < m) {
-            const float* Ar = A + (j + 1 + a) * r + (j + 1);
-            for (int b = lane & 7; b < m; b += 8) sv = fmaf(Ar[b], (b == 0) ? 1.f : colj[b * r] * scale, sv);
-          }
-          sv += __shfl_xor_sync(0xffffffffu, sv, 1);
-          sv += __shfl_xor_sync(0xffffffffu, sv, 2);
-          sv += __shfl_xor_sync(0xffffffffu, sv, 4);
-          if ((lane & 7) == 0 && a < m) pv[a] = t * sv;
-        }
-      }
-      tridiag_sync();
-      if (t != 0.f) {
-        float kk = 0.f;                                 // K = (t/2) p.v, per warp
-        for (int a = lane; a < m; a += 32) kk += pv[a] * vb[a];
-        kk = 0.5f * t * warp_sumf(kk);
-        float sq = 0.f;                                 // next column, rows a >= 2
-        for (int a = wid; a < m; a += tdw) {           // A22 -= v w^T + w v^T, w = p - K v
-          float* Ar = A + (j + 1 + a) * r + (j + 1);
-          const float va = vb[a], wa = pv[a] - kk * va;
-          for (int b = lane; b < m; b += 32) Ar[b] -= va * (pv[b] - kk * vb[b]) + wa * vb[b];
-          if (lane == 0 && a >= 2) sq += Ar[0] * Ar[0];
-        }
-        if (lane == 0) colsq[(j + 1) & 1][wid] = sq;
-      } else {
-        float sq = 0.f;
-        for (int a = wid; a < m; a += tdw)
-          if (lane == 0 && a >= 2) sq += A[(j + 1 + a) * r + (j + 1)] * A[(j + 1 + a) * r + (j + 1)];
-        if (lane == 0) colsq[(j + 1) & 1][wid] = sq;
-      }
-      if (wid == 0)                                     // v_j into column j, below the subdiagonal
-        for (int q = 1 + lane; q < m; q += 32) A[(j + 1 + q) * r + j] = vb[q];
-      tridiag_sync();
+  for (int j = 0; j + 2 < r; ++j) {
+    const int j1 = j + 1;
+    float xn2;
+    if (j == 0) {
+      float part = 0.f;
+      for (int g = 2 + lane; g < r; g += 32) part = fmaf(A[g * ld], A[g * ld], part);
+      xn2 = warp_sumf(part);
+    } else {
+      xn2 = warp_sumf(colsq[j & 1][lane]);
     }
+    const float a0 = A[j1 * ld + j];
+    float beta = a0, t = 0.f, scale = 0.f;
+    if (xn2 > 0.f) {
+      beta = -copysignf(sqrtf(a0 * a0 + xn2), a0);
+      t = (beta - a0) / beta;
+      scale = 1.f / (a0 - beta);
+    }
+    if (tid == 0) { d[j] = A[j * ld + j]; e[j] = beta; tau[j] = t; }
+    float vc[NS], vr[NS];
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+      const int c = lane + 32 * i, g = wid + 32 * i;
+      vc[i] = (c == j1) ? 1.f : ((c > j1 && c < r) ? A[c * ld + j] * scale : 0.f);
+      vr[i] = (g == j1) ? 1.f : ((g > j1 && g < r) ? A[g * ld + j] * scale : 0.f);
+    }
+    if (t != 0.f) {
+      float s[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        s[q] = 0.f;
+        const int g = wid + 32 * q;
+        if (q < NS && g >= j1 && g < r) {               // warp-uniform
+          const float* Ar = A + g * ld + lane;
+#pragma unroll
+          for (int i = 0; i < NS; ++i) s[q] = fmaf(Ar[32 * i], vc[i], s[q]);
+        }
+      }
+      // transposing reduction: after it, lane l holds the warp sum of row slot
+      // 4 b4 + 2 b3 + b2 (b = the bits of l)
+      const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+      float u[4], x2[2];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float keep = b4 ? s[k + 4] : s[k], send = b4 ? s[k] : s[k + 4];
+        u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float keep = b3 ? u[k + 2] : u[k], send = b3 ? u[k] : u[k + 2];
+        x2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+      }
+      float sum;
+      {
+        const float keep = b2 ? x2[1] : x2[0], send = b2 ? x2[0] : x2[1];
+        sum = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+      }
+      sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+      const int qs = (lane >> 2) & 7;
+      const int gs = wid + 32 * qs;
+      if ((lane & 3) == 0 && qs < NS && gs >= j1 && gs < r) pv[gs] = t * sum;
+    }
+    tridiag_sync();
+    const int own = j1 & 31;                            // owner lane of column j + 1
+    float sq = 0.f;
+    if (t != 0.f) {
+      float kk = 0.f;                                   // K = (t/2) p.v, per warp
+      float wc[NS];
+#pragma unroll
+      for (int i = 0; i < NS; ++i) {
+        const int c = lane + 32 * i;
+        const float pc = (c >= j1 && c < r) ? pv[c] : 0.f;
+        kk = fmaf(pc, vc[i], kk);
+        wc[i] = pc;
+      }
+      kk = 0.5f * t * warp_sumf(kk);
+#pragma unroll
+      for (int i = 0; i < NS; ++i) wc[i] = fmaf(-kk, vc[i], wc[i]);
+#pragma unroll
+      for (int q = 0; q < NS; ++q) {
+        const int g = wid + 32 * q;
+        if (g >= j1 && g < r) {                         // warp-uniform
+          float* Ar = A + g * ld + lane;
+          const float va = vr[q], wa = fmaf(-kk, va, pv[g]);
+#pragma unroll
+          for (int i = 0; i < NS; ++i) Ar[32 * i] = fmaf(-va, wc[i], fmaf(-wa, vc[i], Ar[32 * i]));
+          if (lane == (j & 31) && g > j1) A[g * ld + j] = va;   // v_j into column j (its owner lane)
+          if (lane == own && g >= j + 3) sq = fmaf(A[g * ld + j1], A[g * ld + j1], sq);
+        }
+      }
+    } else if (lane == own) {
+      for (int g = wid; g < r; g += 32)
+        if (g >= j + 3) sq = fmaf(A[g * ld + j1], A[g * ld + j1], sq);
+    }
+    if (lane == own) colsq[j1 & 1][wid] = sq;
+    tridiag_sync();
   }
   __syncthreads();
   if (tid == 0) {
     if (r >= 2) {
-      d[r - 2] = A[(r - 2) * r + (r - 2)];
-      e[r - 2] = A[(r - 1) * r + (r - 2)];
+      d[r - 2] = A[(r - 2) * ld + (r - 2)];
+      e[r - 2] = A[(r - 1) * ld + (r - 2)];
       tau[r - 2] = 0.f;
     }
-    if (r >= 1) { d[r - 1] = A[(r - 1) * r + (r - 1)]; e[r - 1] = 0.f; tau[r - 1] = 0.f; }
+    if (r >= 1) { d[r - 1] = A[(r - 1) * ld + (r - 1)]; e[r - 1] = 0.f; tau[r - 1] = 0.f; }
   }
   __syncthreads();
   // --- Gershgorin interval
@@ -645,19 +688,25 @@ eig32_kernel(int n, DW w) {
   for (int q = 1; q < nwarps; ++q) { lo = fminf(lo, slo[q]); hi = fmaxf(hi, shi[q]); }
   const float span = fmaxf(fmaxf(fabsf(lo), fabsf(hi)), 1e-30f);
   const float pivmin = 1e-30f * fmaxf(span * span, 1.f);
-  // --- eigenvalues by multisection of the Sturm count: a group of 8 lanes brackets
-  // one eigenvalue; each lane counts the eigenvalues below one of 8 interior points
-  // of the group's interval, which splits it into 9 parts.  8 rounds shrink the
-  // Gershgorin interval by 9^8 = 4.3e7, to the FP32 resolution of the spectrum
-  // (eigenvalues near 0 need no more: the refinement takes them to FP64).
+  // --- eigenvalues by multisection of the Sturm count: a group of G lanes brackets
+  // one eigenvalue; each lane counts the eigenvalues below one of G interior points
+  // of the group's interval, which splits it into G + 1 parts.  All eigenvalues are
+  // bracketed at once: G = 8 (8 rounds, 9^8 = 4.3e7) up to 128 of them, else G = 4
+  // (11 rounds, 5^11 = 4.9e7).  Either shrinks the Gershgorin interval to the FP32
+  // resolution of the spectrum (eigenvalues near 0 need no more: the refinement takes
+  // them to FP64).  Warps whose groups hold no eigenvalue skip the counts.
   {
-    const int grp = tid >> 3, sl = tid & 7;
-    const int gsh = lane & 24;
-    const float frac = (float)(sl + 1) * (1.0f / 9.0f);
-    for (int i0 = 0; i0 < r; i0 += kBig / 8) {
-      const int i = i0 + grp;
+    const int G = (r <= kBig / 8) ? 8 : 4;
+    const int rounds = (G == 8) ? 8 : 11;
+    const float inv = 1.f / (float)(G + 1);
+    const int grp = tid / G, sl = tid % G;
+    const int gsh = lane & ~(G - 1);
+    const unsigned gmask = (1u << G) - 1u;
+    const float frac = (float)(sl + 1) * inv;
+    if ((wid * 32) / G < r) {                           // warp-uniform
+      const int i = min(grp, r - 1);
       float a = lo - 1e-6f * span, b = hi + 1e-6f * span;
-      for (int round = 0; round < 8; ++round) {
+      for (int round = 0; round < rounds; ++round) {
         const float wd = b - a;
         const float x = fmaf(wd, frac, a);
         int cnt = 0;
@@ -670,14 +719,14 @@ eig32_kernel(int n, DW w) {
           cnt += q < 0.f;
         }
         // counts grow with x: the first point with more than i eigenvalues below it
-        const unsigned m = (__ballot_sync(0xffffffffu, cnt > i) >> gsh) & 0xffu;
-        const int first = m ? __ffs(m) - 1 : 8;
-        const float na = (first == 0) ? a : fmaf(wd, (float)first * (1.0f / 9.0f), a);
-        const float nb = (first == 8) ? b : fmaf(wd, (float)(first + 1) * (1.0f / 9.0f), a);
+        const unsigned m = (__ballot_sync(0xffffffffu, cnt > i) >> gsh) & gmask;
+        const int first = m ? __ffs(m) - 1 : G;
+        const float na = (first == 0) ? a : fmaf(wd, (float)first * inv, a);
+        const float nb = (first == G) ? b : fmaf(wd, (float)(first + 1) * inv, a);
         a = na;
         b = nb;
       }
-      if (sl == 0 && i < r) lam[i] = 0.5f * (a + b);
+      if (sl == 0 && grp < r) lam[i] = 0.5f * (a + b);
     }
   }
   __syncthreads();
@@ -724,7 +773,7 @@ eig32_kernel(int n, DW w) {
   for (int q = tid; q < r * r; q += kBig) {
     const int j = q / r, a = q % r;
     float v = 0.f;
-    if (j + 2 < r && tau[j] != 0.f) v = (a == j + 1) ? 1.f : ((a > j + 1) ? A[a * r + j] : 0.f);
+    if (j + 2 < r && tau[j] != 0.f) v = (a == j + 1) ? 1.f : ((a > j + 1) ? A[a * ld + j] : 0.f);
     V[q] = v;
   }
   for (int j = tid; j < r; j += kBig) V[r * r + j] = (j + 2 < r) ? tau[j] : 0.f;
@@ -1587,6 +1636,14 @@ void trsm(const double* Ahat, const double* Mhat, int n, double sigma, int pass,
     default: trsm_ns<kRowsPerLane>(Ahat, Mhat, n, sigma, pass, w, s); break;
   }
 }
+// FP32 eigensolve launch: T (n rows of stride 32 NS + 1 floats) in dynamic shared memory.
+template <int NS>
+void eig32(int n, const DW& w, cudaStream_t s) {
+  const size_t esm = (size_t)n * (32 * NS + 1) * sizeof(float);
+  BMG_CUDA(cudaFuncSetAttribute(eig32_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+  eig32_kernel<NS><<<1, kBig, esm, s>>>(n, w);
+  check_launch("eig32_kernel");
+}
 void backsub(int n, int k, const DW& w, double* Y, cudaStream_t s) {
   switch ((n + 31) / 32) {
     case 1: backsub_ns<1>(n, k, w, Y, s); break;
@@ -1646,10 +1703,15 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
   trsm(Ahat, Mhat, n, sigma, 1, w, s);
   // 3. FP32 start: tridiagonalisation and eigenvalues (T in shared memory), inverse
   //    iteration (one CTA per cluster), back-transformation
-  const size_t esm = (size_t)n * n * sizeof(float);
-  BMG_CUDA(cudaFuncSetAttribute(eig32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
-  eig32_kernel<<<1, kBig, esm, s>>>(n, w);
-  check_launch("eig32_kernel");
+  switch ((n + 31) / 32) {
+    case 1: eig32<1>(n, w, s); break;
+    case 2: eig32<2>(n, w, s); break;
+    case 3: eig32<3>(n, w, s); break;
+    case 4: eig32<4>(n, w, s); break;
+    case 5: eig32<5>(n, w, s); break;
+    case 6: eig32<6>(n, w, s); break;
+    default: eig32<7>(n, w, s); break;
+  }
   const size_t ism = sizeof(float) * ((size_t)n * kInvSmemMembers + kInvLuFloats);
   BMG_CUDA(cudaFuncSetAttribute(invit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism));
   invit_kernel<<<n, kInvThreads, ism, s>>>(n, w);
