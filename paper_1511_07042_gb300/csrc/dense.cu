@@ -575,9 +575,12 @@ eig32_kernel(int n, DW w) {
     const float a0 = A[j1 * ld + j];
     float beta = a0, t = 0.f, scale = 0.f;
     if (xn2 > 0.f) {
-      beta = -copysignf(sqrtf(a0 * a0 + xn2), a0);
-      t = (beta - a0) / beta;
-      scale = 1.f / (a0 - beta);
+      // hardware approximations (a few ulps): the reflector stays orthogonal to FP32
+      // accuracy, which is all the start needs, and the IEEE forms cost most of a step
+      const float nn = fmaf(a0, a0, xn2);
+      beta = -copysignf(nn * rsqrtf(nn), a0);
+      t = __fdividef(beta - a0, beta);
+      scale = __fdividef(1.f, a0 - beta);
     }
     if (tid == 0) { d[j] = A[j * ld + j]; e[j] = beta; tau[j] = t; }
     float vc[NS], vr[NS];
