@@ -9,7 +9,7 @@
 //      diagonal and factored by Cholesky with diagonal pivoting; pivots below the drop
 //      tolerance mark basis vectors already in the span of the others, which are
 //      dropped (rank r).  basis_kernel [1 CTA] factors the whole of Mhat; the block
-//      form (qfactor_kernel, xsolve_kernel, schur_kernel, xfactor_kernel) keeps the
+//      form (qfactor_kernel, xsolve_kernel, schur_kernel, xfactor_cl_kernel) keeps the
 //      factor of a repeating leading block and factors the Schur complement of the
 //      new columns.
 //   2. trsm_kernel     [multi-CTA, FP64]  reduced standard matrix
@@ -31,6 +31,8 @@
 //   5. select / backsub  the k smallest |theta|; Y = D P L^{-T} W_sel.
 #include <algorithm>
 #include <cmath>
+
+#include <cooperative_groups.h>
 
 #include "common.cuh"
 
@@ -383,48 +385,167 @@ schur_kernel(const double* __restrict__ Mhat, int n, int nq, int kx, DW w) {
 
 // Pivoted Cholesky of S_X and assembly of the factor of the whole of M-hat in the
 // layout basis_kernel writes (L, Lt, rl, perm, d, rank).  A deficient M_Q gives rank 0.
-template <int NW>
-__global__ void __launch_bounds__(NW * 32, 1)
-xfactor_kernel(int n, int nq, int kx, DW w, int smemS, double drop_tol) {
-  extern __shared__ double dsm[];
-  double* S = smemS ? dsm : w.S;
-  __shared__ unsigned long long wk[32];
-  __shared__ int wi[32];
-  __shared__ int perm[kMaxN];
-  __shared__ double lcol[kMaxN], rls[kMaxN];
-  __shared__ int s_go;
+// The same factorisation spread over a cluster of kXC CTAs, one per SM: the update, the
+// bulk of the FP64 work, then runs on kXC SMs at once (a warp's FP64 instruction holds
+// its scheduler's FP64 unit for about 64 cycles on this GPU, so one SM's update is the
+// bound of the one-CTA form).  CTA c holds the full rows a = c + kXC la of S_X and the
+// factor entries of those rows.  Pivoting is logical: an eliminated index keeps its
+// row and is only marked, and the pivot order is assembled at the end.  A step: each
+// CTA's largest remaining diagonal into its candidate slot (double-buffered by step
+// parity, so that a CTA a step ahead never overwrites a slot still being read); one
+// cluster barrier; every CTA reads the kXC candidates through distributed shared memory
+// and takes the same pivot p (largest key, then smallest index), stages row p of its
+// owner while warp 0 forms 1/sqrt(piv), and updates its own remaining rows with the
+// same fused multiply-adds as the one-CTA form.  Row p is never written again once
+// chosen, so the other CTAs may read it while its owner moves on.
+constexpr int kXC = 8;
+constexpr int kXThreads = 256;
+__global__ void __cluster_dims__(kXC, 1, 1) __launch_bounds__(kXThreads)
+xfactor_cl_kernel(int n, int nq, int kx, DW w, double drop_tol) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double xsm[];
+  __shared__ double lrow[kMaxN], rls[kMaxN];
+  __shared__ int perm[kMaxN], pos[kMaxN];
+  __shared__ unsigned char done[kMaxN];
+  __shared__ unsigned long long candk[2];
+  __shared__ int candi[2];
+  __shared__ int s_p, s_go;
+  __shared__ double s_piv, s_rl;
+  const int c = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int nwarps = NW, NT = NW * 32;
-  if (w.qflag[0] != 1) {
-    if (tid == 0) *w.rank = 0;
+  constexpr int nwarps = kXThreads / 32;
+  const int nr = (kx + kXC - 1) / kXC;               // row slots of a CTA
+  double* Srow = xsm;                                 // nr x kx
+  double* Lmine = xsm + (size_t)nr * kx;              // nr x kx: L[a][q] of this CTA's rows
+  if (w.qflag[0] != 1) {                              // the same decision in every CTA
+    if (c == 0 && tid == 0) *w.rank = 0;
     return;
   }
-  if (smemS)
-    for (int q = tid; q < kx * kx; q += NT) S[q] = w.S[q];
-  for (int i = tid; i < kx; i += NT) perm[i] = i;
+  for (int q = tid; q < nr * kx; q += kXThreads) {
+    const int la = q / kx, a = c + kXC * la;
+    Srow[q] = (a < kx) ? __ldcg(w.S + a * kx + (q - la * kx)) : 0.0;
+    Lmine[q] = 0.0;
+  }
+  for (int i = tid; i < kx; i += kXThreads) done[i] = 0;
   __syncthreads();
-  const int rx = pchol<NW>(S, kx, kx, drop_tol, perm, lcol, rls, wk, wi, &s_go);
+  int rx = kx;
+  for (int j = 0; j < kx; ++j) {
+    const int par = j & 1;
+    if (wid == 0) {                                   // this CTA's candidate
+      unsigned long long best = 0ull;
+      int bi = kx;
+      for (int la = lane; la < nr; la += 32) {
+        const int a = c + kXC * la;
+        if (a < kx && !done[a]) {
+          const unsigned long long key = pivot_key(Srow[la * kx + a]);
+          if (key > best || (key == best && a < bi)) { best = key; bi = a; }
+        }
+      }
+      warp_argmax(best, bi);
+      if (lane == 0) { candk[par] = best; candi[par] = bi; }
+    }
+    cl.sync();
+    if (wid == 0) {                                   // the cluster's pivot
+      unsigned long long best = 0ull;
+      int bi = kx;
+      if (lane < kXC) {
+        best = *cl.map_shared_rank(&candk[par], lane);
+        bi = *cl.map_shared_rank(&candi[par], lane);
+      }
+      warp_argmax(best, bi);
+      if (lane == 0) {
+        const double piv = __longlong_as_double((long long)best);
+        s_go = piv > drop_tol && bi < kx;
+        s_p = bi;
+        s_piv = piv;
+      }
+    }
+    __syncthreads();
+    if (!s_go) { rx = j; break; }
+    const int p = s_p;
+    if (wid == 0) {                                   // 1/sqrt(piv), while the others stage row p
+      if (lane == 0) {
+        const double rl = rsqrt_nr(s_piv);
+        s_rl = rl;
+        perm[j] = p;
+        pos[p] = j;
+        rls[j] = rl;
+      }
+    } else {
+      const double* prow = cl.map_shared_rank(Srow, p % kXC) + (size_t)(p / kXC) * kx;
+      for (int b = tid - 32; b < kx; b += kXThreads - 32) lrow[b] = (done[b] || b == p) ? 0.0 : prow[b];
+    }
+    __syncthreads();
+    const double rl = s_rl;
+    for (int b = tid; b < kx; b += kXThreads) lrow[b] *= rl;   // column j of L (0 at eliminated indices)
+    __syncthreads();
+    // rank-1 update of this CTA's remaining rows (full rows: S stays exactly symmetric)
+    for (int la = wid; la < nr; la += nwarps) {
+      const int a = c + kXC * la;
+      if (a >= kx) continue;                          // warp-uniform
+      if (a == p) {
+        if (lane == 0) Lmine[la * kx + j] = s_piv * rl;
+        continue;
+      }
+      if (done[a]) continue;
+      const double l = lrow[a];
+      if (lane == 0) Lmine[la * kx + j] = l;
+      double* Sa = Srow + la * kx;
+      for (int b = lane; b < kx; b += 32) Sa[b] = fma(-l, lrow[b], Sa[b]);
+    }
+    if (tid == 0) done[p] = 1;
+    __syncthreads();
+  }
+  cl.sync();                                          // no distributed shared-memory access after this
+  // pivot order: the chosen indices, then the remaining ones in index order (one warp,
+  // ballot prefix counts)
+  if (wid == 0) {
+    int base = rx;
+    for (int i0 = 0; i0 < kx; i0 += 32) {
+      const int i = i0 + lane;
+      const bool rem = i < kx && !done[i];
+      const unsigned bal = __ballot_sync(0xffffffffu, rem);
+      if (rem) {
+        const int q = base + __popc(bal & ((1u << lane) - 1u));
+        perm[q] = i;
+        pos[i] = q;
+      }
+      base += __popc(bal);
+    }
+  }
+  __syncthreads();
+  // this CTA's rows of the factor, in pivot order, into w.S (every CTA read its rows
+  // of S_X before the first cluster barrier)
+  for (int la = wid; la < nr; la += nwarps) {
+    const int a = c + kXC * la;
+    if (a >= kx) continue;
+    const int pa = pos[a];
+    for (int q = lane; q < kx; q += 32)
+      w.S[pa * kx + q] = (q < rx && q <= pa) ? Lmine[la * kx + q] : 0.0;
+  }
+  cl.sync();                                          // w.S complete and visible in the cluster
   const int rank = nq + rx;
   // L[i][q]: the cached L_Q (i, q < nq); W^T in X pivot order (i >= nq, q < nq);
-  // L_X (i, q >= nq, q - nq < rx)
+  // L_X (i, q >= nq, q - nq < rx); rows dealt to the CTAs
   auto entry = [&](int i, int q) -> double {
     if (q > i) return 0.0;
     if (i < nq) return w.qL[i * nq + q];
     const int a = i - nq;
     if (q < nq) return w.Z[q * kx + perm[a]];
     const int b = q - nq;
-    return (b < rx) ? S[a * kx + b] : 0.0;
+    return (b < rx) ? __ldcg(w.S + a * kx + b) : 0.0;   // written by the other CTAs
   };
-  for (int i = wid; i < n; i += nwarps)
+  for (int i = c * nwarps + wid; i < n; i += kXC * nwarps)
     for (int q = lane; q < n; q += 32) w.L[i * n + q] = entry(i, q);
-  for (int q = wid; q < n; q += nwarps)
+  for (int q = c * nwarps + wid; q < n; q += kXC * nwarps)
     for (int i = lane; i < n; i += 32) w.Lt[q * n + i] = entry(i, q);
-  for (int i = tid; i < n; i += NT) {
+  for (int i = c * kXThreads + tid; i < n; i += kXC * kXThreads) {
     w.perm[i] = (i < nq) ? w.qperm[i] : nq + perm[i - nq];
     if (i < nq) w.d[i] = w.qd[i];
     if (i < rank) w.rl[i] = (i < nq) ? w.qrl[i] : rls[i - nq];
   }
-  if (tid == 0) *w.rank = rank;
+  if (c == 0 && tid == 0) *w.rank = rank;
 }
 
 // ---------------------------------------- 2. T = L^{-1} C L^{-T} (FP64, warps) --
@@ -1690,10 +1811,10 @@ void dense_eig(const double* Ahat, const double* Mhat, int n, double sigma, int 
     const int nt = (kx + 7) / 8;
     schur_kernel<<<dim3(nt, nt), 64, 0, s>>>(Mhat, n, nq, kx, w);
     check_launch("schur_kernel");
-    const size_t xfs = (size_t)kx * kx * sizeof(double);
-    BMG_CUDA(cudaFuncSetAttribute(xfactor_kernel<kFactorWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xfs));
-    xfactor_kernel<kFactorWarps><<<1, kFactorWarps * 32, xfs, s>>>(n, nq, kx, w, 1, drop_tol);
-    check_launch("xfactor_kernel");
+    const size_t xfs = 2 * (size_t)((kx + kXC - 1) / kXC) * kx * sizeof(double);
+    BMG_CUDA(cudaFuncSetAttribute(xfactor_cl_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xfs));
+    xfactor_cl_kernel<<<kXC, kXThreads, xfs, s>>>(n, nq, kx, w, drop_tol);
+    check_launch("xfactor_cl_kernel");
   } else {
     const size_t smemS = (size_t)n * n * sizeof(double);
     const bool useS = smemS <= 200 * 1024;
