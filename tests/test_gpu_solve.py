@@ -52,6 +52,27 @@ def test_bumpy_interior_cluster_matches_dense(gpu_bmg, kw):
     assert err.max() <= 1e-10 and ang.max() <= 1e-8
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_duplicate_start_columns_drop_from_the_block_factor(gpu_bmg, precision):
+    """Two identical start columns stay bitwise identical through the smoother, so the
+    Schur complement S_X of the first cycle's enriched mass matrix is singular and the
+    block factorisation (the cluster kernel on the Schur complement) must drop one of
+    them (Alg. 2 step 3).  The solve then goes on with k - 1 independent columns and
+    still finds the 16 lowest pairs of the 642-vertex sphere."""
+    v, t = inputs.icosahedron()
+    prob = gpu_bmg.Problem(v, t, 3)
+    prob.hierarchy(3)
+    X0 = inputs.gaussian_block(inputs.n_vertices(2), 20, 1001)
+    X0[:, 7] = X0[:, 3]
+    ev, U, rs, info = prob.solve(X0, 20, 16, 0.0, 1e-10, gpu_bmg.options(precision=precision))
+    assert info.converged == 1
+    H = obmg.build_hierarchy(v, t, 3, 0.0, None)
+    A, M = H.A[3], H.M[3]
+    w, V = certify.dense_pencil_eigs(A, M)
+    err, ang = certify.compare_to_reference(M, ev, U, w[:16], V[:, :16])
+    assert err.max() <= 1e-10 and ang.max() <= 1e-8
+
+
 def test_ragged_block_and_no_guard(gpu_bmg):
     ev, U, rs, info, H = solve(gpu_bmg, 3, 17, 16, 0.0, 1e-10, smoother="jacobi")
     assert info.converged == 1
