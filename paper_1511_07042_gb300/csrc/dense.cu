@@ -15,8 +15,8 @@
 //   2. trsm_kernel     [multi-CTA, FP64]  reduced standard matrix
 //      T = L^{-1} D P^T (Ahat - sigma Mhat) P D L^{-T}: two forward substitutions, one
 //      warp per column, L staged in shared memory.
-//   3. FP32 start: eig32_kernel [1 CTA] Householder tridiagonalisation of sym(T) and
-//      multisection on Sturm counts for all eigenvalues; invit_kernel [one CTA per
+//   3. FP32 start: eig32_cl_kernel [8-CTA cluster] Householder tridiagonalisation of
+//      sym(T) and multisection on Sturm counts for all eigenvalues; invit_kernel [one CTA per
 //      cluster] inverse iteration with Gram-Schmidt inside clusters of close
 //      eigenvalues; backtr_kernel [multi-CTA] the back-transformation.
 //   4. refinement      [multi-CTA, FP64]  the eigenvectors W are refined to FP64
@@ -46,7 +46,6 @@ constexpr int kMaxDense = 224;           // the FP32 stage keeps T (n^2 floats) 
 constexpr int kBig = 1024;               // threads of the single-CTA kernels
 constexpr int kFactorWarps = 32;         // warps of the pivoted Cholesky kernels (block form)
 constexpr int kBasisWarps = 32;          // warps of the whole-matrix pivoted Cholesky
-constexpr int kTriDiagWarps = 32;        // warps of the FP32 tridiagonal reduction
 constexpr int kMaxCluster = 40;          // larger clusters keep the orthonormalising step only
 constexpr int kTile = 8;                 // output tile of the refinement products
 
@@ -385,19 +384,20 @@ schur_kernel(const double* __restrict__ Mhat, int n, int nq, int kx, DW w) {
 
 // Pivoted Cholesky of S_X and assembly of the factor of the whole of M-hat in the
 // layout basis_kernel writes (L, Lt, rl, perm, d, rank).  A deficient M_Q gives rank 0.
-// The same factorisation spread over a cluster of kXC CTAs, one per SM: the update, the
-// bulk of the FP64 work, then runs on kXC SMs at once (a warp's FP64 instruction holds
-// its scheduler's FP64 unit for about 64 cycles on this GPU, so one SM's update is the
-// bound of the one-CTA form).  CTA c holds the full rows a = c + kXC la of S_X and the
+// The factorisation runs on a cluster of kXC CTAs, one per SM: the update, the bulk of
+// the FP64 work, then runs on kXC SMs at once (a warp's FP64 instruction holds its
+// scheduler's FP64 unit for about 64 cycles on this GPU, so one SM's update bounds a
+// one-CTA factorisation).  CTA c holds the full rows a = c + kXC la of S_X and the
 // factor entries of those rows.  Pivoting is logical: an eliminated index keeps its
 // row and is only marked, and the pivot order is assembled at the end.  A step: each
 // CTA's largest remaining diagonal into its candidate slot (double-buffered by step
 // parity, so that a CTA a step ahead never overwrites a slot still being read); one
 // cluster barrier; every CTA reads the kXC candidates through distributed shared memory
 // and takes the same pivot p (largest key, then smallest index), stages row p of its
-// owner while warp 0 forms 1/sqrt(piv), and updates its own remaining rows with the
-// same fused multiply-adds as the one-CTA form.  Row p is never written again once
-// chosen, so the other CTAs may read it while its owner moves on.
+// owner while warp 0 forms 1/sqrt(piv), and updates its own remaining rows (each
+// element gets the fused multiply-adds of the unblocked right-looking algorithm, in
+// pivot order).  Row p is never written again once chosen, so the other CTAs may read
+// it while its owner moves on.
 constexpr int kXC = 8;
 constexpr int kXThreads = 256;
 __global__ void __cluster_dims__(kXC, 1, 1) __launch_bounds__(kXThreads)
@@ -618,11 +618,7 @@ trsm_kernel(const double* __restrict__ Ahat, const double* __restrict__ Mhat, in
   for (int q = lane; q < r; q += 32) out[q * n + c] = zs[q] * w.rl[q];
 }
 
-// ---------------------------------------------- 3. FP32 eigensolve (1 CTA) -----
-// Barrier among the first kTriDiagWarps warps of the block (named barrier 1).
-__device__ __forceinline__ void tridiag_sync() {
-  asm volatile("bar.sync 1, %0;" ::"r"(kTriDiagWarps * 32) : "memory");
-}
+// --------------------------------------------------------- 3. FP32 eigensolve --
 // Start vectors of the inverse iteration: zero-mean pseudo-random values in [-1, 1)
 // from an integer hash of (row, column).  Vectors with a common positive component
 // project almost parallel onto a near-degenerate group, and the last member of the
@@ -638,62 +634,78 @@ __device__ __forceinline__ float start_value(int a, int j) {
 }
 // Solves per eigenvector (each followed by orthonormalisation inside the clusters).
 constexpr int kInvIters = 3;
-// NS = ceil(n / 32): row and column slots per thread of the tridiagonalisation.
+// Householder tridiagonalisation of sym(T), eigenvalues by multisection of the Sturm
+// count, and the clusters and shifts of the inverse iteration, on a cluster of kEC
+// CTAs (one per SM), so that each Householder step touches kEC times fewer rows per
+// SM: a one-CTA form is bound by the work every warp repeats and by the two passes of
+// the trailing block through one SM's shared memory (about 5400 cycles a step at
+// n = 170).
+// CTA c holds the rows g = c + kEC la of sym(T) (stride ld = 32 NS + 1, columns from r
+// on zero), one warp per row.  The update keeps A exactly symmetric (the two products
+// rounded separately, then added, the same for (g, b) and (b, g)), so row j is column
+// j bit for bit and is read contiguously from its owner.  A step:
+//   every CTA gathers row j from its owner through distributed shared memory and forms
+//   the reflector's scalars and v (all CTAs compute the same values); CTA 0 writes v_j
+//   as row j of the back-transformation's reflector block;
+//   p = t A22 v on the CTA's rows, and the CTA's part of p.v;  cluster barrier;
+//   every CTA gathers p and the kEC parts, forms K and w = p - K v, and updates its
+//   rows;  cluster barrier.
+// Then every CTA brackets its share of the eigenvalues by multisection (a warp of 32
+// points per eigenvalue), and CTA 0 gathers them, forms the clusters and shifts of the
+// inverse iteration and writes the tridiagonal matrix.  A CTA's shared memory is read
+// by the others only between barriers that every thread of every CTA passes the same
+// number of times (no branch around a barrier depends on anything but n, r and data
+// that all CTAs hold identically).
+constexpr int kEC = 8;
+constexpr int kEThreads = 1024;
 template <int NS>
-__global__ void __launch_bounds__(kBig)
-eig32_kernel(int n, DW w) {
+__global__ void __cluster_dims__(kEC, 1, 1) __launch_bounds__(kEThreads)
+eig32_cl_kernel(int n, DW w) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  constexpr int ld = 32 * NS + 1;
+  constexpr int RW = (32 * NS + kEC - 1) / kEC;       // row slots of a CTA (<= 32)
+  static_assert(RW <= kEThreads / 32, "one warp per row");
   extern __shared__ float fsm[];
-  __shared__ float d[kMaxN], e[kMaxN], e2[kMaxN], tau[kMaxN], vb[kMaxN], pv[kMaxN], lam[kMaxN];
-  __shared__ float slo[32], shi[32];
+  float* A = fsm;                                     // RW x ld: rows c + kEC la
+  __shared__ float d[kMaxN], e[kMaxN], e2[kMaxN], tau[kMaxN], xv[kMaxN], vb[kMaxN], pv[kMaxN], wv[kMaxN],
+      lam[kMaxN];
+  __shared__ float wpart[32], s_pd, slo[32], shi[32];
+  const int c = (int)cl.block_rank();
   const int r = *w.rank;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int nwarps = kBig / 32;
-  float* A = fsm;                                   // r x r, row stride ld (odd)
-  constexpr int ld = 32 * NS + 1;
-  // T is symmetric in exact arithmetic; its two triangular solves leave rounding
-  // asymmetry.  Symmetrise it in place (each pair i <= j by one thread) for the FP64
-  // refinement, whose symmetric products assume it, and take its FP32 copy.
-  for (int q = tid; q < r * r; q += kBig) {
-    const int i = q / r, j = q - (q / r) * r;
-    if (i <= j) {
-      const double v = 0.5 * (w.T[i * n + j] + w.T[j * n + i]);
-      w.T[i * n + j] = v;
-      w.T[j * n + i] = v;
-      A[i * ld + j] = (float)v;
-      A[j * ld + i] = (float)v;
+  constexpr int nwarps = kEThreads / 32;
+  // this CTA's rows of sym(T) in FP32, read before any CTA writes sym(T) back
+  for (int q = tid; q < RW * ld; q += kEThreads) {
+    const int la = q / ld, b = q - la * ld, g = c + kEC * la;
+    A[q] = (g < r && b < r) ? (float)(0.5 * (w.T[g * n + b] + w.T[b * n + g])) : 0.f;
+  }
+  for (int b = tid; b < kMaxN; b += kEThreads) pv[b] = 0.f;
+  cl.sync();
+  // sym(T) back into T for the FP64 refinement: the pairs b >= g of this CTA's rows
+  // (each pair read and written by its one owner)
+  for (int la = wid; la < RW; la += nwarps) {
+    const int g = c + kEC * la;
+    if (g >= r) continue;
+    for (int b = g + lane; b < r; b += 32) {
+      const double v = 0.5 * (w.T[g * n + b] + w.T[b * n + g]);
+      w.T[g * n + b] = v;
+      w.T[b * n + g] = v;
     }
   }
-  for (int q = tid; q < r * (ld - r); q += kBig) A[(q / (ld - r)) * ld + r + q % (ld - r)] = 0.f;
-  __syncthreads();
-  // --- Householder tridiagonalisation, v_j stored in column j below the subdiagonal.
-  // Ownership is 2-D cyclic and fixed for the whole reduction: warp w holds the rows
-  // w + 32 q and lane l the columns l + 32 i (q, i < NS) of A.  Rows have the stride
-  // ld = 32 NS + 1: every lane's column slots exist in every row (the columns from r
-  // on are zero), so a step touches the thread's whole slot set at fixed offsets from
-  // a row base with no per-element test; the columns left of the trailing block enter
-  // with v = w = 0 and keep their values.  The odd stride keeps the column reads of v
-  // conflict-free.  A step has two barriers.  Every warp forms the reflector's scalars
-  // itself, from the per-warp sums of the column's squares that the previous step left
-  // in colsq (double-buffered), then:
-  //   p = t A22 v: per live row of the warp, NS products per lane, and the row sums of
-  //   the warp in one transposing reduction (9 shuffles for up to 8 rows);
-  //   barrier;  K = (t/2) p.v,  A22 -= v w^T + w v^T (w = p - K v) on the thread's
-  //   elements, v_j into column j, the next column's squares by its owner lane;
-  //   barrier.
-  static_assert(kTriDiagWarps == 32 && kBig == 1024, "rows are dealt to 32 warps");
-  static_assert(NS <= 8, "the row sums are reduced as eight slots");
-  __shared__ float colsq[2][32];
+  float* V = w.A32;                                   // reflector rows for backtr_kernel
+  __shared__ float pdv[kEC];
   for (int j = 0; j + 2 < r; ++j) {
     const int j1 = j + 1;
-    float xn2;
-    if (j == 0) {
-      float part = 0.f;
-      for (int g = 2 + lane; g < r; g += 32) part = fmaf(A[g * ld], A[g * ld], part);
-      xn2 = warp_sumf(part);
-    } else {
-      xn2 = warp_sumf(colsq[j & 1][lane]);
+    {                                                   // row j (= column j) from its owner
+      const float* rowj = cl.map_shared_rank(A, j % kEC) + (j / kEC) * ld;
+      for (int b = tid; b < r; b += kEThreads) xv[b] = rowj[b];
     }
-    const float a0 = A[j1 * ld + j];
+    __syncthreads();
+    float part = 0.f;
+    for (int b = j + 2 + lane; b < r; b += 32) part = fmaf(xv[b], xv[b], part);
+    const float xn2 = warp_sumf(part);
+    const float a0 = xv[j1];
     float beta = a0, t = 0.f, scale = 0.f;
     if (xn2 > 0.f) {
       // hardware approximations (a few ulps): the reflector stays orthogonal to FP32
@@ -703,99 +715,84 @@ eig32_kernel(int n, DW w) {
       t = __fdividef(beta - a0, beta);
       scale = __fdividef(1.f, a0 - beta);
     }
-    if (tid == 0) { d[j] = A[j * ld + j]; e[j] = beta; tau[j] = t; }
-    float vc[NS], vr[NS];
+    if (tid == 0) { d[j] = xv[j]; e[j] = beta; tau[j] = t; }
+    for (int b = tid; b < 32 * NS; b += kEThreads)
+      vb[b] = (b == j1) ? 1.f : ((b > j1 && b < r) ? xv[b] * scale : 0.f);
+    __syncthreads();
+    if (c == 0)                                         // v_j (1 at j + 1, 0 above; 0 when t = 0)
+      for (int b = tid; b < r; b += kEThreads) V[j * r + b] = (t != 0.f) ? vb[b] : 0.f;
+    // p = t A22 v on this CTA's rows, and the CTA's part of p.v
+    float pd = 0.f;
+    if (wid < RW && t != 0.f) {
+      const int g = c + kEC * wid;
+      if (g >= j1 && g < r) {                           // warp-uniform
+        const float* Ar = A + wid * ld + lane;
+        float s = 0.f;
 #pragma unroll
-    for (int i = 0; i < NS; ++i) {
-      const int c = lane + 32 * i, g = wid + 32 * i;
-      vc[i] = (c == j1) ? 1.f : ((c > j1 && c < r) ? A[c * ld + j] * scale : 0.f);
-      vr[i] = (g == j1) ? 1.f : ((g > j1 && g < r) ? A[g * ld + j] * scale : 0.f);
+        for (int i = 0; i < NS; ++i) s = fmaf(Ar[32 * i], vb[lane + 32 * i], s);
+        s = warp_sumf(s);
+        const float p = t * s;
+        if (lane == 0) pv[g] = p;
+        pd = p * vb[g];
+      }
     }
-    if (t != 0.f) {
-      float s[8];
+    if (lane == 0) wpart[wid] = pd;
+    __syncthreads();
+    if (wid == 0) {
+      const float q = warp_sumf(wpart[lane]);
+      if (lane == 0) s_pd = q;
+    }
+    cl.sync();                                          // p and the parts of p.v complete
+    if (tid < kEC) pdv[tid] = *cl.map_shared_rank(&s_pd, tid);
+    __syncthreads();
+    float kk = 0.f;                                     // K = (t/2) p.v, parts in CTA order
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        s[q] = 0.f;
-        const int g = wid + 32 * q;
-        if (q < NS && g >= j1 && g < r) {               // warp-uniform
-          const float* Ar = A + g * ld + lane;
+    for (int q = 0; q < kEC; ++q) kk += pdv[q];
+    kk *= 0.5f * t;
+    for (int b = tid; b < 32 * NS; b += kEThreads) {
+      const float pb = (t != 0.f && b >= j1 && b < r) ? *cl.map_shared_rank(&pv[b], b % kEC) : 0.f;
+      wv[b] = fmaf(-kk, vb[b], pb);                     // w = p - K v (0 outside the trailing block)
+    }
+    __syncthreads();
+    // A22 -= v w^T + w v^T on this CTA's rows; the two products rounded alone and then
+    // added, so that (g, b) and (b, g) get the same value
+    if (wid < RW && t != 0.f) {
+      const int g = c + kEC * wid;
+      if (g >= j1 && g < r) {
+        float* Ar = A + wid * ld + lane;
+        const float vg = vb[g], wg = wv[g];
 #pragma unroll
-          for (int i = 0; i < NS; ++i) s[q] = fmaf(Ar[32 * i], vc[i], s[q]);
+        for (int i = 0; i < NS; ++i) {
+          const int b = lane + 32 * i;
+          Ar[32 * i] = Ar[32 * i] - __fadd_rn(__fmul_rn(vg, wv[b]), __fmul_rn(wg, vb[b]));
         }
       }
-      // transposing reduction: after it, lane l holds the warp sum of row slot
-      // 4 b4 + 2 b3 + b2 (b = the bits of l)
-      const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-      float u[4], x2[2];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float keep = b4 ? s[k + 4] : s[k], send = b4 ? s[k] : s[k + 4];
-        u[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-      }
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const float keep = b3 ? u[k + 2] : u[k], send = b3 ? u[k] : u[k + 2];
-        x2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-      }
-      float sum;
-      {
-        const float keep = b2 ? x2[1] : x2[0], send = b2 ? x2[0] : x2[1];
-        sum = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-      }
-      sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-      sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-      const int qs = (lane >> 2) & 7;
-      const int gs = wid + 32 * qs;
-      if ((lane & 3) == 0 && qs < NS && gs >= j1 && gs < r) pv[gs] = t * sum;
     }
-    tridiag_sync();
-    const int own = j1 & 31;                            // owner lane of column j + 1
-    float sq = 0.f;
-    if (t != 0.f) {
-      float kk = 0.f;                                   // K = (t/2) p.v, per warp
-      float wc[NS];
-#pragma unroll
-      for (int i = 0; i < NS; ++i) {
-        const int c = lane + 32 * i;
-        const float pc = (c >= j1 && c < r) ? pv[c] : 0.f;
-        kk = fmaf(pc, vc[i], kk);
-        wc[i] = pc;
-      }
-      kk = 0.5f * t * warp_sumf(kk);
-#pragma unroll
-      for (int i = 0; i < NS; ++i) wc[i] = fmaf(-kk, vc[i], wc[i]);
-#pragma unroll
-      for (int q = 0; q < NS; ++q) {
-        const int g = wid + 32 * q;
-        if (g >= j1 && g < r) {                         // warp-uniform
-          float* Ar = A + g * ld + lane;
-          const float va = vr[q], wa = fmaf(-kk, va, pv[g]);
-#pragma unroll
-          for (int i = 0; i < NS; ++i) Ar[32 * i] = fmaf(-va, wc[i], fmaf(-wa, vc[i], Ar[32 * i]));
-          if (lane == (j & 31) && g > j1) A[g * ld + j] = va;   // v_j into column j (its owner lane)
-          if (lane == own && g >= j + 3) sq = fmaf(A[g * ld + j1], A[g * ld + j1], sq);
-        }
-      }
-    } else if (lane == own) {
-      for (int g = wid; g < r; g += 32)
-        if (g >= j + 3) sq = fmaf(A[g * ld + j1], A[g * ld + j1], sq);
-    }
-    if (lane == own) colsq[j1 & 1][wid] = sq;
-    tridiag_sync();
+    cl.sync();                                          // rows updated before the next gather
   }
-  __syncthreads();
   if (tid == 0) {
     if (r >= 2) {
-      d[r - 2] = A[(r - 2) * ld + (r - 2)];
-      e[r - 2] = A[(r - 1) * ld + (r - 2)];
+      const float* ra = cl.map_shared_rank(A, (r - 2) % kEC) + ((r - 2) / kEC) * ld;
+      const float* rb = cl.map_shared_rank(A, (r - 1) % kEC) + ((r - 1) / kEC) * ld;
+      d[r - 2] = ra[r - 2];
+      e[r - 2] = rb[r - 2];
       tau[r - 2] = 0.f;
     }
-    if (r >= 1) { d[r - 1] = A[(r - 1) * ld + (r - 1)]; e[r - 1] = 0.f; tau[r - 1] = 0.f; }
+    if (r >= 1) {
+      const float* rb = cl.map_shared_rank(A, (r - 1) % kEC) + ((r - 1) / kEC) * ld;
+      d[r - 1] = rb[r - 1];
+      e[r - 1] = 0.f;
+      tau[r - 1] = 0.f;
+    }
+  }
+  if (c == 0) {                                         // the rows without a reflector, and tau
+    for (int q = max(0, r - 2) * r + tid; q < r * r; q += kEThreads) V[q] = 0.f;
+    for (int j = tid; j < r; j += kEThreads) V[r * r + j] = (j + 2 < r) ? tau[j] : 0.f;
   }
   __syncthreads();
-  // --- Gershgorin interval
+  // --- Gershgorin interval (every CTA, the same values)
   float lo = 3.4e38f, hi = -3.4e38f;
-  for (int i = tid; i < r; i += kBig) {
+  for (int i = tid; i < r; i += kEThreads) {
     const float rad = fabsf(e[i]) + (i > 0 ? fabsf(e[i - 1]) : 0.f);
     lo = fminf(lo, d[i] - rad);
     hi = fmaxf(hi, d[i] + rad);
@@ -812,25 +809,21 @@ eig32_kernel(int n, DW w) {
   for (int q = 1; q < nwarps; ++q) { lo = fminf(lo, slo[q]); hi = fmaxf(hi, shi[q]); }
   const float span = fmaxf(fmaxf(fabsf(lo), fabsf(hi)), 1e-30f);
   const float pivmin = 1e-30f * fmaxf(span * span, 1.f);
-  // --- eigenvalues by multisection of the Sturm count: a group of G lanes brackets
-  // one eigenvalue; each lane counts the eigenvalues below one of G interior points
-  // of the group's interval, which splits it into G + 1 parts.  All eigenvalues are
-  // bracketed at once: G = 8 (8 rounds, 9^8 = 4.3e7) up to 128 of them, else G = 4
-  // (11 rounds, 5^11 = 4.9e7).  Either shrinks the Gershgorin interval to the FP32
-  // resolution of the spectrum (eigenvalues near 0 need no more: the refinement takes
-  // them to FP64).  Warps whose groups hold no eigenvalue skip the counts.
+  // --- eigenvalues by multisection of the Sturm count, CTA c taking the eigenvalues
+  // [c qn, (c + 1) qn): a group of 8 lanes brackets one eigenvalue; each lane counts
+  // the eigenvalues below one of 8 interior points of the group's interval, which
+  // splits it into 9 parts; 8 rounds shrink the Gershgorin interval by 9^8 = 4.3e7, to
+  // the FP32 resolution of the spectrum (eigenvalues near 0 need no more: the
+  // refinement takes them to FP64).
+  const int qn = (r + kEC - 1) / kEC, i0 = c * qn, i1 = min(r, i0 + qn);
   {
-    const int G = (r <= kBig / 8) ? 8 : 4;
-    const int rounds = (G == 8) ? 8 : 11;
-    const float inv = 1.f / (float)(G + 1);
-    const int grp = tid / G, sl = tid % G;
-    const int gsh = lane & ~(G - 1);
-    const unsigned gmask = (1u << G) - 1u;
-    const float frac = (float)(sl + 1) * inv;
-    if ((wid * 32) / G < r) {                           // warp-uniform
-      const int i = min(grp, r - 1);
+    const int grp = tid >> 3, sl = tid & 7;
+    const int gsh = lane & 24;
+    const float frac = (float)(sl + 1) * (1.0f / 9.0f);
+    if (i0 + 4 * wid < i1) {                            // warp-uniform
+      const int i = min(i0 + grp, i1 - 1);
       float a = lo - 1e-6f * span, b = hi + 1e-6f * span;
-      for (int round = 0; round < rounds; ++round) {
+      for (int round = 0; round < 8; ++round) {
         const float wd = b - a;
         const float x = fmaf(wd, frac, a);
         int cnt = 0;
@@ -843,25 +836,30 @@ eig32_kernel(int n, DW w) {
           cnt += q < 0.f;
         }
         // counts grow with x: the first point with more than i eigenvalues below it
-        const unsigned m = (__ballot_sync(0xffffffffu, cnt > i) >> gsh) & gmask;
-        const int first = m ? __ffs(m) - 1 : G;
-        const float na = (first == 0) ? a : fmaf(wd, (float)first * inv, a);
-        const float nb = (first == G) ? b : fmaf(wd, (float)(first + 1) * inv, a);
+        const unsigned m = (__ballot_sync(0xffffffffu, cnt > i) >> gsh) & 0xffu;
+        const int first = m ? __ffs(m) - 1 : 8;
+        const float na = (first == 0) ? a : fmaf(wd, (float)first * (1.0f / 9.0f), a);
+        const float nb = (first == 8) ? b : fmaf(wd, (float)(first + 1) * (1.0f / 9.0f), a);
         a = na;
         b = nb;
       }
-      if (sl == 0 && grp < r) lam[i] = 0.5f * (a + b);
+      if (sl == 0 && i0 + grp < i1) lam[i] = 0.5f * (a + b);
     }
   }
-  __syncthreads();
-  // --- clusters and shifts for the inverse iteration (invit_kernel): clusters are
-  // chains of eigenvalues closer than 1e-4 span; members of a cluster get shifts at
-  // least 10 ulps apart.
+  cl.sync();                                            // every CTA's eigenvalues bracketed
+  if (c == 0)
+    for (int i = tid; i < r; i += kEThreads)
+      if (i >= qn) lam[i] = *cl.map_shared_rank(&lam[i], i / qn);
+  cl.sync();                                            // CTA 0 has read the others' eigenvalues
+  if (c != 0) return;
+  // --- CTA 0: clusters and shifts for the inverse iteration (invit_kernel): clusters
+  // are chains of eigenvalues closer than 1e-4 span; members of a cluster get shifts
+  // at least 10 ulps apart.
   __shared__ int cst[kMaxN + 1];
   __shared__ int s_ncl;
   const float ortol = 1e-4f * span;
   const float tiny = fmaxf(1.2e-9f * span, pivmin);
-  float* shift = vb;   // the tridiagonalisation is done with vb
+  float* shift = vb;
   if (tid == 0) {
     int nc = 0;
     cst[0] = 0;
@@ -881,7 +879,7 @@ eig32_kernel(int n, DW w) {
     s_ncl = nc;
   }
   __syncthreads();
-  for (int i = tid; i < r; i += kBig) {
+  for (int i = tid; i < r; i += kEThreads) {
     w.T3[i] = d[i];
     w.T3[n + i] = e[i];
     w.T3[2 * n + i] = shift[i];
@@ -890,17 +888,7 @@ eig32_kernel(int n, DW w) {
     w.T3[3 * n] = tiny;
     w.cls[0] = s_ncl;
   }
-  for (int c = tid; c <= s_ncl; c += kBig) w.cls[1 + c] = cst[c];
-  // --- hand the back-transformation to backtr_kernel: the reflectors v_j as rows of
-  // A32 (row j = v_j, with the implicit 1 at j + 1 and zeros above), tau_j after them.
-  float* V = w.A32;
-  for (int q = tid; q < r * r; q += kBig) {
-    const int j = q / r, a = q % r;
-    float v = 0.f;
-    if (j + 2 < r && tau[j] != 0.f) v = (a == j + 1) ? 1.f : ((a > j + 1) ? A[a * ld + j] : 0.f);
-    V[q] = v;
-  }
-  for (int j = tid; j < r; j += kBig) V[r * r + j] = (j + 2 < r) ? tau[j] : 0.f;
+  for (int q = tid; q <= s_ncl; q += kEThreads) w.cls[1 + q] = cst[q];
 }
 
 // ------------------------------------- 3a. inverse iteration (one CTA per cluster) --
@@ -1760,13 +1748,13 @@ void trsm(const double* Ahat, const double* Mhat, int n, double sigma, int pass,
     default: trsm_ns<kRowsPerLane>(Ahat, Mhat, n, sigma, pass, w, s); break;
   }
 }
-// FP32 eigensolve launch: T (n rows of stride 32 NS + 1 floats) in dynamic shared memory.
+// FP32 eigensolve launch: each CTA of the cluster holds its rows of T (stride 32 NS + 1).
 template <int NS>
 void eig32(int n, const DW& w, cudaStream_t s) {
-  const size_t esm = (size_t)n * (32 * NS + 1) * sizeof(float);
-  BMG_CUDA(cudaFuncSetAttribute(eig32_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
-  eig32_kernel<NS><<<1, kBig, esm, s>>>(n, w);
-  check_launch("eig32_kernel");
+  const size_t esm = (size_t)((32 * NS + kEC - 1) / kEC) * (32 * NS + 1) * sizeof(float);
+  BMG_CUDA(cudaFuncSetAttribute(eig32_cl_kernel<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esm));
+  eig32_cl_kernel<NS><<<kEC, kEThreads, esm, s>>>(n, w);
+  check_launch("eig32_cl_kernel");
 }
 void backsub(int n, int k, const DW& w, double* Y, cudaStream_t s) {
   switch ((n + 31) / 32) {
