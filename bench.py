@@ -208,14 +208,25 @@ def class_table(prof, hbm_peak):
     return out
 
 
+# The source file that defines each kernel whose DRAM traffic is recorded.
+TRAFFIC_SOURCE = {"row_update_kernel": "ops.cu", "spmm_am_kernel": "ops.cu",
+                  "gram_tc_kernel": "tc.cu", "expand_tc_kernel": "tc.cu"}
+
+
+def traffic_stamp(name):
+    """Stamp of a kernel's code: its source file, every library header, the public
+    header and the compile flags (the stamp the traffic lines carry)."""
+    from paper_1511_07042_gb300 import build as B
+    return B._stamp([os.path.join(B.CSRC, TRAFFIC_SOURCE[name])])[:16]
+
+
 def read_traffic(name):
-    """DRAM bytes per launch of a kernel class from the committed ncu summary
-    (profiles/traffic_sphere655362_k128.txt: lines 'class bytes_per_launch stamp'),
-    valid only while the library sources match the stamp the counters were taken on."""
+    """DRAM bytes per launch of a kernel from the committed ncu summary
+    (profiles/traffic_sphere655362_k128.txt: lines 'kernel bytes_per_launch stamp'),
+    valid only while the kernel's code matches the stamp the counters were taken on."""
     path = os.path.join(ROOT, "profiles", "traffic_sphere655362_k128.txt")
     try:
-        from paper_1511_07042_gb300 import build as B
-        stamp = B._stamp(B._sources())[:16]
+        stamp = traffic_stamp(name)
         with open(path) as fh:
             for line in fh:
                 f = line.split()
