@@ -26,6 +26,7 @@ scaling, no collective on the data path.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -214,10 +215,20 @@ TRAFFIC_SOURCE = {"row_update_kernel": "ops.cu", "spmm_am_kernel": "ops.cu",
 
 
 def traffic_stamp(name):
-    """Stamp of a kernel's code: its source file, every library header, the public
-    header and the compile flags (the stamp the traffic lines carry)."""
+    """Stamp of a kernel's code: the names and contents of its source file, every
+    library header and the public header, and the compile flags (the stamp the
+    traffic lines carry; independent of where the tree sits)."""
     from paper_1511_07042_gb300 import build as B
-    return B._stamp([os.path.join(B.CSRC, TRAFFIC_SOURCE[name])])[:16]
+    files = [os.path.join(B.CSRC, TRAFFIC_SOURCE[name])]
+    files += sorted(os.path.join(B.CSRC, f) for f in os.listdir(B.CSRC) if f.endswith((".cuh", ".h")))
+    files += [os.path.join(B.INCLUDE, "bmg.h")]
+    h = hashlib.sha256()
+    for p in files:
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(B.ARCH + B.FLAGS).encode())
+    return h.hexdigest()[:16]
 
 
 def read_traffic(name):
